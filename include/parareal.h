@@ -1,0 +1,248 @@
+/*
+ * parareal.h - C ABI of the GB300 (sm_103a) hot path of the MOR-based adaptive parareal
+ * method of arXiv 2601.10981 for  u_t + b.grad(u) = eps Lap(u) + f  on a periodic cube.
+ *
+ * Plain C: every argument is a pointer, a size or a scalar.  "host" pointers are CPU
+ * memory owned by the caller and only read (or written) during the call; "device"
+ * pointers are CUDA global memory on the current device, owned by the caller unless
+ * stated otherwise.  Grid functions are n^3 doubles laid out [z][y][x] (x fastest).
+ * Every call returns a pr_status; on failure pr_last_error() describes it.  Phase calls
+ * are asynchronous on the stream set by pr_set_stream (default: the legacy stream);
+ * calls documented as "synchronises" wait for that stream.  A context is used by one
+ * host thread at a time.
+ */
+#ifndef PARAREAL_H
+#define PARAREAL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_ctx pr_ctx;
+
+typedef enum pr_status {
+    PR_OK = 0,
+    PR_ERR_INVALID_ARG = 1,    /* bad size, pointer or option                          */
+    PR_ERR_OOM = 2,            /* device memory could not be allocated / bound buffer too small */
+    PR_ERR_CUDA = 3,           /* a CUDA runtime call failed                           */
+    PR_ERR_NOT_CONVERGED = 4,  /* BiCGStab hit lin_maxit in some fine step             */
+    PR_ERR_BREAKDOWN = 5,      /* BiCGStab breakdown, or a non-positive Cholesky pivot */
+    PR_ERR_TIMEOUT = 6,        /* an in-kernel barrier exceeded its spin limit          */
+    PR_ERR_NONFINITE = 7,      /* NaN/Inf in the initial data or in an iterate          */
+    PR_ERR_STATE = 8,          /* phase called out of order                            */
+    PR_ERR_UNSUPPORTED = 9     /* valid request this build does not implement          */
+} pr_status;
+
+/* Velocity fields b(x).  Each component is a sum of 1-D functions of the two other
+ * coordinates (b_x(y,z), b_y(x,z), b_z(x,y)), which is what makes central advection
+ * exactly skew-symmetric on the periodic grid. */
+enum pr_flow_kind {
+    PR_FLOW_ABC = 0,        /* (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x) */
+    PR_FLOW_KOLMOGOROV = 1, /* (sin(k y), 0, 0)                                          */
+    PR_FLOW_CONST = 2       /* (b[0], b[1], b[2])                                        */
+};
+
+/* Arithmetic of the fine Krylov solves, snapshots and POD bases.  Interface states U^k_n,
+ * fine end states, reduced (Galerkin) systems and eigenproblems are FP64 in both. */
+enum pr_precision {
+    PR_FP64 = 0,            /* everything FP64                                           */
+    PR_FP32 = 1             /* FP64 state + FP32 increment solve ("delta form"); FP32
+                               snapshots and bases; Gram/projection accumulate in FP64  */
+};
+
+typedef struct pr_grid {
+    int n;                  /* points per direction, 4 <= n <= 1024                      */
+    double L;               /* cube edge; <= 0 means 2*pi                               */
+} pr_grid;
+
+typedef struct pr_flow {
+    int kind;               /* enum pr_flow_kind                                        */
+    double A, B, C;         /* ABC coefficients                                         */
+    int k;                  /* Kolmogorov wave number                                   */
+    double b[3];            /* constant velocity                                        */
+} pr_flow;
+
+/* Options; pr_opts_init fills the defaults.  Values marked "0: derive" are computed from
+ * the problem in pr_create following the paper's parameter ratios (Sec. 4). */
+typedef struct pr_opts {
+    double T0;              /* Case-I window [0,T0] (Sec. 2.3); 0: derive = DeltaT        */
+    double dT;              /* coarse step; 0: derive = DeltaT/10 (ratio of Sec. 4.1)     */
+    int n_snap;             /* snapshots per window; 0: one every delta_M = 5 fine steps,
+                               n_s = floor(S/delta_M)+1 (Case I); else delta_M =
+                               floor(S/(n_snap-1))                                       */
+    int m_cap;              /* cap on every POD dimension; 0: none                       */
+    int m_l, p;             /* left neighbours / previous iterations in W^k_n, eq. (W^k_n);
+                               each 0 or 1; default 1, 1                                  */
+    double pod_tol3;        /* gamma3 = 1 - pod_tol3; 0: derive = pod_tol * 4e-3          */
+    double rank_tau;        /* eigenvalues <= rank_tau*lambda_1 count as zero (Alg. 1);
+                               0: derive = 1e-13 (FP64) or 1e-6 (FP32)                   */
+    int precision;          /* enum pr_precision; default PR_FP64                        */
+    double lin_tol;         /* BiCGStab stops at ||r|| <= lin_tol ||rhs||;
+                               0: derive = 1e-14 (FP64) or 1e-9 (FP32)                   */
+    int lin_maxit;          /* BiCGStab iteration cap per fine step; default 200         */
+    double aug_tol;         /* no augmentation if ||d~|| <= aug_tol ||U||; default 1e-12  */
+    int group_ctas;         /* CTAs cooperating on one subinterval in the fine sweep;
+                               0: chosen from the SM count                               */
+    int ctas_per_sm;        /* resident CTAs per SM for the fine sweep; 0: occupancy max  */
+    long long spin_limit;   /* polls of an in-kernel barrier before PR_ERR_TIMEOUT
+                               (default 1<<22, about a second)                            */
+} pr_opts;
+
+/* Per-solve report (pr_solve).  Times are seconds measured with CUDA events. */
+typedef struct pr_report {
+    int k;                  /* parareal iterations performed (k >= 1)                    */
+    int converged;          /* criterion met                                             */
+    double max_inc;         /* max_n ||U^k_n - U^{k-1}_n|| / ||U^k_n|| at the last k      */
+    double max_err;         /* max_n error of eq. (error) against the reference; -1 if none */
+    double t_iter0, t_fine, t_pod, t_coarse, t_check, t_total;
+    double fine_dof_steps;  /* grid points x fine steps propagated by F (all iterations) */
+    double lin_iters_mean;  /* BiCGStab iterations per fine step, mean                   */
+    int lin_iters_max;
+    int m0;                 /* dimension of V0 (iteration 0)                              */
+    int m1_max, m2_max;     /* largest level-1 / level-2 POD dimension at the last k     */
+} pr_report;
+
+/* Fill *opts with defaults. */
+void pr_opts_init(pr_opts* opts);
+
+/* Create a solver for Algorithm 2 on [0, T0 + T]: the fine propagator on [0, T0] (Case I)
+ * and parareal with n_sub subintervals of length DeltaT = T / n_sub on [T0, T0 + T].
+ *   grid, flow: problem (host structs, copied).   eps > 0: diffusion.   T > 0.
+ *   dt_fine: requested fine step; the step used is DeltaT / S, S = ceil(DeltaT/dt_fine)
+ *            (ratios within 1e-9 of an integer are rounded).
+ *   pod_tol: gamma1 = gamma2 = 1 - pod_tol (Algorithm 1); the paper uses 5e-6.
+ *   opts: NULL for defaults.   *out receives the context (free with pr_destroy).
+ * Selects the current CUDA device; allocates nothing on it yet. */
+pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double T,
+                    int n_sub, double dt_fine, double pod_tol, const pr_opts* opts,
+                    pr_ctx** out);
+void pr_destroy(pr_ctx* ctx);
+
+/* Derived sizes: fine steps per subinterval S, steps on [0,T0] S0, snapshot stride and
+ * counts, coarse steps per subinterval; any pointer may be NULL. */
+pr_status pr_get_sizes(const pr_ctx* ctx, int* S, int* S0, int* dM, int* n_s, int* n_s0,
+                       int* Lc, double* dt_eff, double* DeltaT);
+
+/* Device bytes the context needs.  pr_bind_workspace hands it a caller-owned device
+ * buffer of at least that size (e.g. a torch tensor); otherwise the first phase call
+ * allocates it with cudaMalloc and pr_destroy frees it. */
+size_t pr_workspace_bytes(const pr_ctx* ctx);
+pr_status pr_bind_workspace(pr_ctx* ctx, void* device_ptr, size_t bytes);
+
+/* Stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream) for all work. */
+pr_status pr_set_stream(pr_ctx* ctx, void* cuda_stream);
+
+/* Initial state u0 and forcing f (n^3 host doubles each, copied; f may be NULL for 0).
+ * Resets the iteration state.  PR_ERR_NONFINITE if u0 or f holds NaN/Inf. */
+pr_status pr_set_initial(pr_ctx* ctx, const double* u0, const double* f);
+
+/* Iteration 0 (Case I, Algorithm 2): fine propagator on [0,T0] with snapshots,
+ * V0 = POD_Mode(W, gamma1), U^0_0 = u_hat0, U^0_{n+1} = G_0(P_{V0} U^0_n). */
+pr_status pr_iteration0(pr_ctx* ctx);
+
+/* Parareal iteration k >= 1, three phases that must run in this order:
+ *  pr_fine_sweep:   F_n = F(t_n, t_{n+1}, U^{k-1}_n) and snapshots W^k_{n,0} for
+ *                   n = k-1..N-1, all subintervals in one persistent launch.
+ *  pr_pod_update:   R^k_{n,0} = POD_Mode(W^k_{n,0}, gamma2) for n = k-1..N-1, the level-2
+ *                   basis R^k_n = POD_Mode(W^k_n, gamma3) of eq. (W^k_n) and its Galerkin
+ *                   matrices for n = k..N-1.
+ *  pr_coarse_sweep: sequential over n = k..N-1: augmentation (eqs. (eqaug), (eq12)), the
+ *                   bordered reduced system (eq13) and the update of eq. (formula4),
+ *                   U^k_{n+1} = G(U^k_n) + F_n - G(P U^{k-1}_n); U^k_n = U^{k-1}_n (n<k),
+ *                   U^k_k = F_{k-1}. */
+pr_status pr_fine_sweep(pr_ctx* ctx, int k);
+pr_status pr_pod_update(pr_ctx* ctx, int k);
+pr_status pr_coarse_sweep(pr_ctx* ctx, int k);
+
+/* Convergence after pr_coarse_sweep(k): max increment max_n ||U^k_n-U^{k-1}_n||/||U^k_n||
+ * and, if a reference is set, the max error of eq. (error).  Synchronises; also returns
+ * any error a kernel recorded since the last check. */
+pr_status pr_check(pr_ctx* ctx, int k, double* max_inc, double* max_err);
+
+/* Whole Algorithm 2: iteration 0 (if not yet done), then k = 1, 2, ... until the
+ * criterion holds (error against the reference <= tol if ref or a set reference exists,
+ * else increment <= tol), k = n_sub or k = k_max (<= 0: n_sub).  ref: NULL or host
+ * (n_sub+1) x n^3 doubles U_0..U_N of the sequential fine solution.  Synchronises. */
+pr_status pr_solve(pr_ctx* ctx, double tol, int k_max, const double* ref, pr_report* out);
+
+/* Sequential fine solution U_n = F(0, t_n, u0), n = 0..N, one subinterval after another
+ * on the GPU (the cost_seq form of Sec. 3.3); kept as the context's reference.
+ * fp64: 1 computes it with FP64 Krylov solves whatever the context precision. */
+pr_status pr_compute_reference(pr_ctx* ctx, int fp64);
+/* Reference from the caller: (N+1) x n^3 doubles, host (on_device = 0) or device (1). */
+pr_status pr_set_reference(pr_ctx* ctx, const double* U, int on_device);
+
+/* Interface states of the latest iteration (U^k after pr_coarse_sweep(k), U^0 after
+ * pr_iteration0).  pr_get_interface copies U_n, pr_get_interfaces all N+1 of them, to
+ * host memory.  Synchronise. */
+pr_status pr_get_interface(pr_ctx* ctx, int n, double* host_out);
+pr_status pr_get_interfaces(pr_ctx* ctx, double* host_out);
+/* Replace the latest iterate by host (N+1) x n^3 doubles and declare it iteration k_done
+ * (0 <= k_done < N): the next phase is pr_fine_sweep(k_done+1).  Needs iteration 0 done
+ * (V0 is part of the state). */
+pr_status pr_set_interfaces(pr_ctx* ctx, const double* host_U, int k_done);
+
+/* Undo the latest completed iteration k >= 1 (its predecessor U^{k-1} and the level-1
+ * bases of iteration k-1 are still resident): the next phase is pr_fine_sweep(k) again.
+ * One level deep; used to repeat an iteration on identical inputs. */
+pr_status pr_rewind(pr_ctx* ctx);
+
+/* Read back, to host memory, what the latest phases produced for subinterval n:
+ * F_n of the last fine sweep (n^3 doubles); its snapshots W^k_{n,0} (n_s x n^3 in the
+ * context precision; slot 0 holds the Case-I window after pr_iteration0); and a basis:
+ * level 0 = V0 (n ignored), 1 = R^k_{n,0}, 2 = R^k_n, m_out receives its dimension and
+ * host_out (may be NULL) m x n^3 values in the context precision.  Synchronise. */
+pr_status pr_get_fine_end(pr_ctx* ctx, int n, double* host_out);
+pr_status pr_get_snapshots(pr_ctx* ctx, int n, void* host_out);
+pr_status pr_get_basis(pr_ctx* ctx, int level, int n, void* host_out, int* m_out);
+
+/* Per-subinterval diagnostics of the last pr_check: increments and errors (N+1 each,
+ * host, may be NULL), and POD dimensions m0 / m^k_{n,0} / m^k_n (N each, may be NULL).
+ * Synchronise. */
+pr_status pr_get_diagnostics(pr_ctx* ctx, double* inc, double* err, int* m0, int* m1,
+                             int* m2);
+/* BiCGStab iteration counts of the last fine sweep: total and max over steps, per
+ * subinterval n (N each, host; entries of inactive subintervals are 0).  Synchronises. */
+pr_status pr_get_lin_stats(pr_ctx* ctx, int* total, int* max_per_step);
+
+/* Wait for the stream; return the first error any kernel recorded. */
+pr_status pr_sync(pr_ctx* ctx);
+const char* pr_last_error(const pr_ctx* ctx);
+const char* pr_status_string(pr_status s);
+/* Number of kernels this library has launched in this process. */
+long long pr_launch_count(void);
+
+/* ---- single steps on caller data (device pointers), same kernels as the phases ---- */
+
+/* out = L_h u (transpose = 0) or L_h^T u (1) for `count` grid functions, the FD operator
+ * of eq. (eq1) (central advection, 7-point Laplacian).  d_in, d_out: count x n^3. */
+pr_status pr_op_apply_L(pr_ctx* ctx, const double* d_in, double* d_out, int count,
+                        int transpose);
+
+/* Fine propagator on B independent states: d_out[b] = F(t0, t0 + steps*dt, d_in[b]) with
+ * snapshots of the states at steps 0, dM, ... (n_snap of them; d_snap may be NULL when
+ * n_snap = 0).  d_in, d_out: B x n^3 doubles.  d_snap: B x n_snap x n^3 in the context
+ * precision (double for PR_FP64, float for PR_FP32).  1 <= B <= n_sub. */
+pr_status pr_op_fine(pr_ctx* ctx, const double* d_in, double* d_out, void* d_snap, int B,
+                     double t0, int steps, int dM, int n_snap);
+
+/* POD_Mode (Algorithm 1) with CholQR2 re-orthonormalisation on B snapshot matrices:
+ * d_W: B x n_cols x n^3, d_R: B x m_max x n^3, both in the context precision; gamma in
+ * (0,1]; cap 0 = none; m_out: host, B ints.  n_cols <= the largest window the context
+ * was built for (max(n_s, n_s0, (m_l+1+p) * level-1 cap)); B <= n_sub. */
+pr_status pr_op_pod(pr_ctx* ctx, const void* d_W, int n_cols, int B, double gamma, int cap,
+                    void* d_R, int* m_out);
+
+/* One coarse update of eq. (formula4) on subinterval [t, t+DeltaT] with the augmented
+ * space [R, d(U)]:  d_out = G(U) + F - G(P U_prev).  d_R: m x n^3 in the context
+ * precision (orthonormal columns), d_U, d_Uprev, d_F, d_out: n^3 doubles. */
+pr_status pr_op_coarse_update(pr_ctx* ctx, const void* d_R, int m, const double* d_U,
+                              const double* d_Uprev, const double* d_F, double* d_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARAREAL_H */

@@ -1,0 +1,1218 @@
+// Context and C ABI of the adaptive-parareal library (include/parareal.h).
+//
+// The host side only orchestrates: every step of Algorithm 2 runs in the kernels of
+// fine.cu, pod.cu and coarse.cu, enqueued on one stream without host round trips inside
+// a phase.  The host reads device results only in pr_check / pr_sync / pr_get_*.
+#include "pr_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace pr {
+long long g_launch_count = 0;
+}
+
+using namespace pr;
+
+namespace {
+
+int steps_for(double span, double dt) {
+    const double q = span / dt;
+    const double r = std::nearbyint(q);
+    if (std::fabs(q - r) < 1e-9 * std::max(1.0, q)) return (int)r;
+    return (int)std::ceil(q);
+}
+
+struct Bump {
+    size_t off = 0;
+    char* base = nullptr;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) / 256 * 256;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+struct pr_ctx {
+    // problem
+    int n = 0;
+    double L = 0, h = 0;
+    long long Ng = 0;
+    pr_flow flow{};
+    double eps = 0, T = 0;
+    int N = 0;
+    double pod_tol = 0;
+    pr_opts o{};
+    // derived
+    double DeltaT = 0, dt = 0, T0 = 0, dT = 0;
+    int S = 0, S0 = 0, Lc = 0, dM = 0, ns = 0, ns0 = 0, nsmax = 0;
+    double gamma1 = 0, gamma3 = 0, tau = 0, lin_tol = 0;
+    bool fp32 = false;
+    int esz = 8;
+    int mcap0 = 0, mcap1 = 0, w2 = 0, mcap2 = 0, mscr = 0, maxK = 0, ldcols = 0;
+    int groups_max = 1;
+    int max_ctas = 1;
+    bool has_f = false;
+    // device
+    cudaStream_t st = nullptr;
+    bool own_ws = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_ready = false;
+    double* tab = nullptr;
+    double* u0 = nullptr;
+    double* f = nullptr;
+    double* Ubuf[2] = {nullptr, nullptr};
+    int cur = 0;  // Ubuf[cur] holds the latest iterate
+    double* Fend = nullptr;
+    char* snap = nullptr;
+    char* R1[2] = {nullptr, nullptr};
+    int* m1[2] = {nullptr, nullptr};
+    int r1cur = 0;  // R1[r1cur]: level-1 bases of the latest pod update
+    char* V0 = nullptr;
+    int* m0 = nullptr;
+    char* R2 = nullptr;
+    int* m2 = nullptr;
+    int* mop = nullptr;            // POD dimensions of pr_op_pod
+    char* LR = nullptr;
+    char* scr[2] = {nullptr, nullptr};
+    double* Mr = nullptr;
+    double* Lr = nullptr;
+    double* M0 = nullptr;
+    double* L0 = nullptr;
+    double* p0 = nullptr;
+    double* q0 = nullptr;
+    double* beta = nullptr;
+    double* gout = nullptr;
+    double* lam = nullptr;
+    double* Cm = nullptr;
+    double* X = nullptr;
+    double* gpart = nullptr;
+    size_t gpart_n = 0;
+    unsigned* counters = nullptr;  // [N + 64]
+    const void** colsA = nullptr;
+    const void** colsB = nullptr;
+    const void** bases = nullptr;  // [N][4]
+    const int** cntp = nullptr;    // [N][4]
+    int* KA = nullptr;
+    int* KB = nullptr;
+    int* ones = nullptr;           // [N+1] = 1
+    int* cnst = nullptr;           // [0] = ns, [1] = ns0, [2] = op m, [3] = 1
+    void* fws = nullptr;
+    size_t fws_bytes = 0;
+    double* ust = nullptr;
+    double* fpart = nullptr;
+    unsigned* fbar = nullptr;
+    int* fstatus = nullptr;
+    int* fits = nullptr;
+    int* fitsmax = nullptr;
+    int* derr = nullptr;
+    int* nonfin = nullptr;
+    double* cd = nullptr;
+    double* cLd = nullptr;
+    double* cLtd = nullptr;
+    double* cdots = nullptr;
+    double* cpart = nullptr;
+    double* coef = nullptr;
+    double* npart = nullptr;
+    double* nout = nullptr;
+    double* ref = nullptr;        // owned cudaMalloc
+    // state
+    int k_done = -1;   // -1: nothing, 0: iteration 0, k: iteration k complete
+    int phase = 0;     // for k_done+1: 0 none, 1 fine done, 2 pod done
+    bool initial_set = false;
+    bool checked = true;
+    std::vector<double> last_inc, last_err;
+    std::string err;
+    cudaEvent_t ev[8] = {};
+    bool ev_ready = false;
+};
+
+namespace {
+
+pr_status fail(pr_ctx* c, pr_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+pr_status cuda_fail(pr_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, PR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PR_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+// Assign (base != null) or size (base == null) the workspace.
+size_t plan(pr_ctx* c, char* base) {
+    Bump b;
+    b.base = base;
+    const long long Ng = c->Ng;
+    const int N = c->N;
+    c->tab = b.take<double>(6 * (size_t)c->n);
+    c->u0 = b.take<double>(Ng);
+    c->f = b.take<double>(Ng);
+    c->Ubuf[0] = b.take<double>((size_t)(N + 1) * Ng);
+    c->Ubuf[1] = b.take<double>((size_t)(N + 1) * Ng);
+    c->Fend = b.take<double>((size_t)N * Ng);
+    c->snap = b.take<char>((size_t)N * c->nsmax * Ng * c->esz);
+    for (int i = 0; i < 2; ++i) {
+        c->R1[i] = b.take<char>((size_t)N * c->mcap1 * Ng * c->esz);
+        c->m1[i] = b.take<int>(N);
+    }
+    c->V0 = b.take<char>((size_t)c->mcap0 * Ng * c->esz);
+    c->m0 = b.take<int>(1);
+    c->R2 = b.take<char>((size_t)N * c->mcap2 * Ng * c->esz);
+    c->m2 = b.take<int>(N + 1);
+    c->mop = b.take<int>(N + 1);
+    c->LR = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
+    c->scr[0] = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
+    c->scr[1] = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
+    c->Mr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
+    c->Lr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
+    c->M0 = b.take<double>((size_t)c->mcap0 * c->mcap0);
+    c->L0 = b.take<double>((size_t)c->mcap0 * c->mcap0);
+    c->p0 = b.take<double>(c->mcap0);
+    c->q0 = b.take<double>(c->mcap0);
+    c->beta = b.take<double>((size_t)N * c->mcap0);
+    c->gout = b.take<double>((size_t)N * c->maxK * c->maxK);
+    c->lam = b.take<double>((size_t)N * c->maxK);
+    c->Cm = b.take<double>((size_t)N * c->maxK * c->maxK);
+    c->X = b.take<double>((size_t)N * c->mscr * c->mscr);
+    c->gpart_n = gram_part_doubles(Ng, N + 1, c->maxK, c->maxK);
+    c->gpart = b.take<double>(c->gpart_n);
+    c->counters = b.take<unsigned>((size_t)N + 64);
+    c->colsA = b.take<const void*>((size_t)(N + 1) * c->ldcols);
+    c->colsB = b.take<const void*>((size_t)(N + 1) * c->ldcols);
+    c->bases = b.take<const void*>((size_t)(N + 1) * 4);
+    c->cntp = b.take<const int*>((size_t)(N + 1) * 4);
+    c->KA = b.take<int>(N + 1);
+    c->KB = b.take<int>(N + 1);
+    c->ones = b.take<int>(N + 1);
+    c->cnst = b.take<int>(8);
+    c->fws_bytes = std::max((size_t)c->groups_max * FINE_NVEC * Ng * c->esz,
+                            (size_t)FINE_NVEC * Ng * sizeof(double));
+    c->fws = b.take<char>(c->fws_bytes);
+    c->ust = b.take<double>((size_t)c->groups_max * 2 * Ng);
+    c->fpart = b.take<double>((size_t)8 * c->max_ctas);
+    c->fbar = b.take<unsigned>((size_t)2 * c->groups_max);
+    c->fstatus = b.take<int>(N + 1);
+    c->fits = b.take<int>(N + 1);
+    c->fitsmax = b.take<int>(N + 1);
+    c->derr = b.take<int>(1);
+    c->nonfin = b.take<int>(1);
+    c->cd = b.take<double>(Ng);
+    c->cLd = b.take<double>(Ng);
+    c->cLtd = b.take<double>(Ng);
+    c->cdots = b.take<double>(1024);
+    c->cpart = b.take<double>(coarse_part_doubles(Ng, c->mcap2));
+    c->coef = b.take<double>(64);
+    c->npart = b.take<double>(norms_part_doubles(Ng, N + 1));
+    c->nout = b.take<double>((size_t)4 * (N + 1));
+    return b.off + 256;
+}
+
+Grid grid_of(const pr_ctx* c) {
+    Grid g;
+    g.n = c->n;
+    g.Ng = c->Ng;
+    g.h = c->h;
+    g.eps = c->eps;
+    g.tab = c->tab;
+    return g;
+}
+
+pr_status init_ws(pr_ctx* c) {
+    plan(c, c->ws);
+    cudaStream_t st = c->st;
+    PR_CUDA(cudaMemsetAsync(c->counters, 0, sizeof(unsigned) * ((size_t)c->N + 64), st));
+    PR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), st));
+    PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, st));
+    std::vector<int> ones(c->N + 1, 1);
+    PR_CUDA(cudaMemcpy(c->ones, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice));
+    int cn[8] = {c->ns, c->ns0, 0, 1, 0, 0, 0, 0};
+    PR_CUDA(cudaMemcpy(c->cnst, cn, sizeof(cn), cudaMemcpyHostToDevice));
+    PR_CUDA(launch_tables(c->flow, c->n, c->L, c->tab, st));
+    if (!c->ev_ready) {
+        for (auto& e : c->ev) PR_CUDA(cudaEventCreate(&e));
+        c->ev_ready = true;
+    }
+    c->ws_ready = true;
+    return PR_OK;
+}
+
+pr_status ensure_ws(pr_ctx* c) {
+    if (c->ws_ready) return PR_OK;
+    if (!c->ws) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, c->ws_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PR_ERR_OOM, "cudaMalloc of " + std::to_string(c->ws_bytes) +
+                                           " bytes failed: " + cudaGetErrorString(e));
+        }
+        c->ws = (char*)p;
+        c->own_ws = true;
+    }
+    return init_ws(c);
+}
+
+// Host-built block descriptors (bases/counts) for B batch items, nb blocks each, uploaded
+// and expanded on the device into column pointer arrays.
+pr_status upload_blocks(pr_ctx* c, const std::vector<const void*>& bases,
+                        const std::vector<const int*>& cnts, int nb, int B, const void** cols,
+                        int* K) {
+    PR_CUDA(cudaMemcpyAsync(c->bases, bases.data(), sizeof(void*) * bases.size(),
+                            cudaMemcpyHostToDevice, c->st));
+    PR_CUDA(cudaMemcpyAsync(c->cntp, cnts.data(), sizeof(int*) * cnts.size(),
+                            cudaMemcpyHostToDevice, c->st));
+    // pageable async copies are staged before returning and stream-ordered, so the host
+    // vectors may go out of scope and the next upload cannot overtake this expansion
+    PR_CUDA(launch_assemble_cols(c->bases, c->cntp, nb, B, c->Ng, c->esz, cols, c->ldcols, K, c->st));
+    return PR_OK;
+}
+
+// Column pointer arrays for B contiguous blocks base + b*bstride (count cnt[b] or the
+// same device int for all when cnt_stride = 0).
+pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const int* cnt, int cnt_stride,
+                      int B, const void** cols, int* K) {
+    std::vector<const void*> bs(B);
+    std::vector<const int*> cs(B);
+    for (int b = 0; b < B; ++b) {
+        bs[b] = base + (size_t)b * bstride_bytes;
+        cs[b] = cnt + (size_t)b * cnt_stride;
+    }
+    return upload_blocks(c, bs, cs, 1, B, cols, K);
+}
+
+// POD_Mode + CholQR2 on B batch items whose snapshot columns are already in
+// (c->colsA, c->KA).  Result: dest + b*dest_bstride (columns of Ng), dims m_dest[b].
+pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, int cap, int mmax, char* dest,
+                       size_t dest_bstride_elems, int* m_dest) {
+    const bool f32 = c->fp32;
+    cudaStream_t st = c->st;
+    // Gram W^T W
+    GramArgs ga{};
+    ga.colsA = c->colsA;
+    ga.colsB = c->colsA;
+    ga.KA = c->KA;
+    ga.KB = c->KA;
+    ga.ldcols = c->ldcols;
+    ga.Ng = c->Ng;
+    ga.B = B;
+    ga.maxKA = maxK;
+    ga.maxKB = maxK;
+    ga.sym = true;
+    ga.part = c->gpart;
+    ga.counter = c->counters;
+    ga.G = c->gout;
+    ga.ldG = maxK;
+    ga.ldG_b = (long long)maxK * maxK;
+    PR_CUDA(launch_gram(ga, f32, f32, st));
+    // eigenpairs + dimension + C = Y_m Lambda_m^{-1/2}
+    EigArgs ea{};
+    ea.G = c->gout;
+    ea.ldG = maxK;
+    ea.ldG_b = (long long)maxK * maxK;
+    ea.K = c->KA;
+    ea.maxK = maxK;
+    ea.B = B;
+    ea.gamma = gamma;
+    ea.tau = c->tau;
+    ea.cap = cap > 0 ? std::min(cap, mmax) : mmax;
+    ea.lam = c->lam;
+    ea.m = m_dest;
+    ea.C = c->Cm;
+    ea.ldC = mmax;
+    ea.ldC_b = (long long)maxK * mmax;
+    ea.err = c->derr;
+    PR_CUDA(launch_eig_pod(ea, st));
+    // R0 = W C -> scr[0]
+    TsmmArgs ta{};
+    ta.colsIn = c->colsA;
+    ta.KIN = c->KA;
+    ta.KOUT = m_dest;
+    ta.ldcols = c->ldcols;
+    ta.C = c->Cm;
+    ta.ldC = mmax;
+    ta.ldC_b = (long long)maxK * mmax;
+    ta.out = c->scr[0];
+    ta.ld_out_b = (long long)mmax * c->Ng;
+    ta.Ng = c->Ng;
+    ta.B = B;
+    ta.maxKIN = maxK;
+    ta.maxKOUT = mmax;
+    PR_CUDA(launch_tsmm(ta, f32, f32, st));
+    // CholQR twice: scr[0] -> scr[1] -> dest
+    for (int pass = 0; pass < 2; ++pass) {
+        char* src = c->scr[pass];
+        pr_status s = cols_contig(c, src, (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB);
+        if (s != PR_OK) return s;
+        GramArgs gb = ga;
+        gb.colsA = c->colsB;
+        gb.colsB = c->colsB;
+        gb.KA = c->KB;
+        gb.KB = c->KB;
+        gb.maxKA = mmax;
+        gb.maxKB = mmax;
+        gb.ldG = mmax;
+        gb.ldG_b = (long long)mmax * mmax;
+        PR_CUDA(launch_gram(gb, f32, f32, st));
+        PR_CUDA(launch_chol_inv(c->gout, mmax, (long long)mmax * mmax, m_dest, mmax, B, c->X, mmax,
+                                (long long)mmax * mmax, c->derr, st));
+        TsmmArgs tb = ta;
+        tb.colsIn = c->colsB;
+        tb.KIN = c->KB;
+        tb.KOUT = m_dest;
+        tb.C = c->X;
+        tb.ldC = mmax;
+        tb.ldC_b = (long long)mmax * mmax;
+        tb.maxKIN = mmax;
+        if (pass == 0) {
+            tb.out = c->scr[1];
+            tb.ld_out_b = (long long)mmax * c->Ng;
+        } else {
+            tb.out = dest;
+            tb.ld_out_b = (long long)dest_bstride_elems;
+        }
+        PR_CUDA(launch_tsmm(tb, f32, f32, st));
+    }
+    return PR_OK;
+}
+
+// Galerkin blocks of B bases (dest columns, counts m[b]): M = R^T R, L = R^T L_h R
+// into Mo/Lo + b*mmax*mmax (ld mmax).
+pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B, int mmax, double* Mo,
+                   double* Lo) {
+    const bool f32 = c->fp32;
+    pr_status s = cols_contig(c, R, bstride_elems * c->esz, m, 1, B, c->colsA, c->KA);
+    if (s != PR_OK) return s;
+    s = cols_contig(c, c->LR, (size_t)mmax * c->Ng * c->esz, m, 1, B, c->colsB, c->KB);
+    if (s != PR_OK) return s;
+    Grid g = grid_of(c);
+    PR_CUDA(launch_apply_L(g, c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, f32, f32,
+                           false, c->st));
+    GramArgs ga{};
+    ga.colsA = c->colsA;
+    ga.colsB = c->colsA;
+    ga.KA = c->KA;
+    ga.KB = c->KA;
+    ga.ldcols = c->ldcols;
+    ga.Ng = c->Ng;
+    ga.B = B;
+    ga.maxKA = mmax;
+    ga.maxKB = mmax;
+    ga.sym = true;
+    ga.part = c->gpart;
+    ga.counter = c->counters;
+    ga.G = Mo;
+    ga.ldG = mmax;
+    ga.ldG_b = (long long)mmax * mmax;
+    PR_CUDA(launch_gram(ga, f32, f32, c->st));
+    ga.sym = false;
+    ga.colsB = c->colsB;
+    ga.KB = c->KB;
+    ga.G = Lo;
+    PR_CUDA(launch_gram(ga, f32, f32, c->st));
+    return PR_OK;
+}
+
+pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int B, int steps,
+                   int n_snap, int stat_off, bool force_fp64) {
+    const bool f32 = c->fp32 && !force_fp64;
+    FineArgs a{};
+    a.g = grid_of(c);
+    a.S = steps;
+    a.dM = c->dM;
+    a.n_snap = snap ? n_snap : 0;
+    a.dt = c->dt;
+    a.f = c->has_f ? c->f : nullptr;
+    a.B = B;
+    a.u_in = u_in;
+    a.u_out = u_out;
+    a.snap = snap;
+    a.ws = c->fws;
+    a.ust = c->ust;
+    a.part = c->fpart;
+    a.bar = c->fbar;
+    a.G = c->o.group_ctas;
+    a.tol = force_fp64 ? std::min(c->lin_tol, 1e-14) : c->lin_tol;
+    a.maxit = c->o.lin_maxit;
+    a.spin_limit = c->o.spin_limit;
+    a.status = c->fstatus + stat_off;
+    a.its_total = c->fits + stat_off;
+    a.its_max = c->fitsmax + stat_off;
+    a.err = c->derr;
+    int max_groups = force_fp64 && c->fp32 ? 1 : c->groups_max;
+    PR_CUDA(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned) * 2 * c->groups_max, c->st));
+    PR_CUDA(launch_fine(a, f32, c->o.ctas_per_sm, max_groups, c->st));
+    return PR_OK;
+}
+
+pr_status read_device_errors(pr_ctx* c) {
+    int e = 0;
+    PR_CUDA(cudaMemcpyAsync(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    std::vector<int> stat(c->N + 1);
+    PR_CUDA(cudaMemcpyAsync(stat.data(), c->fstatus, sizeof(int) * (c->N + 1), cudaMemcpyDeviceToHost,
+                            c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    if (e != 0) {
+        PR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
+        return fail(c, (pr_status)e,
+                    e == PR_ERR_TIMEOUT ? "in-kernel barrier exceeded its spin limit"
+                                        : "a kernel recorded an error (Cholesky pivot or eigen size)");
+    }
+    for (int n = 0; n <= c->N; ++n) {
+        if (stat[n] != 0) {
+            PR_CUDA(cudaMemsetAsync(c->fstatus, 0, sizeof(int) * (c->N + 1), c->st));
+            return fail(c, (pr_status)stat[n],
+                        "fine propagator on subinterval " + std::to_string(n) + ": " +
+                            pr_status_string((pr_status)stat[n]));
+        }
+    }
+    return PR_OK;
+}
+
+pr_status check_finite_host(const double* x, long long n) {
+    for (long long i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return PR_ERR_NONFINITE;
+    return PR_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+void pr_opts_init(pr_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->m_l = 1;
+    o->p = 1;
+    o->precision = PR_FP64;
+    o->lin_maxit = 200;
+    o->aug_tol = 1e-12;
+    o->spin_limit = 1LL << 22;
+}
+
+const char* pr_status_string(pr_status s) {
+    switch (s) {
+        case PR_OK: return "ok";
+        case PR_ERR_INVALID_ARG: return "invalid argument";
+        case PR_ERR_OOM: return "out of device memory";
+        case PR_ERR_CUDA: return "CUDA error";
+        case PR_ERR_NOT_CONVERGED: return "BiCGStab did not converge";
+        case PR_ERR_BREAKDOWN: return "breakdown";
+        case PR_ERR_TIMEOUT: return "in-kernel barrier timed out";
+        case PR_ERR_NONFINITE: return "non-finite value";
+        case PR_ERR_STATE: return "phase called out of order";
+        case PR_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* pr_last_error(const pr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+long long pr_launch_count(void) { return g_launch_count; }
+
+pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double T, int n_sub,
+                    double dt_fine, double pod_tol, const pr_opts* opts, pr_ctx** out) {
+    if (!out) return PR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || !flow) return PR_ERR_INVALID_ARG;
+    if (grid->n < 4 || grid->n > 256) return PR_ERR_UNSUPPORTED;
+    if (!(eps > 0) || !(T > 0) || n_sub < 1 || !(dt_fine > 0) || !(pod_tol >= 0 && pod_tol < 1))
+        return PR_ERR_INVALID_ARG;
+    if (flow->kind < PR_FLOW_ABC || flow->kind > PR_FLOW_CONST) return PR_ERR_INVALID_ARG;
+    pr_opts o;
+    if (opts) o = *opts; else pr_opts_init(&o);
+    if (o.m_l < 0 || o.m_l > 1 || o.p < 0 || o.p > 1) return PR_ERR_UNSUPPORTED;
+    if (o.precision != PR_FP64 && o.precision != PR_FP32) return PR_ERR_INVALID_ARG;
+    if (o.lin_maxit <= 0) o.lin_maxit = 200;
+    if (o.spin_limit < 0) o.spin_limit = 1LL << 22;
+    if (o.aug_tol <= 0) o.aug_tol = 1e-12;
+    pr_ctx* c = new pr_ctx();
+    c->n = grid->n;
+    c->L = grid->L > 0 ? grid->L : 2.0 * M_PI;
+    c->h = c->L / c->n;
+    c->Ng = (long long)c->n * c->n * c->n;
+    c->flow = *flow;
+    c->eps = eps;
+    c->T = T;
+    c->N = n_sub;
+    c->pod_tol = pod_tol;
+    c->o = o;
+    c->fp32 = o.precision == PR_FP32;
+    c->esz = c->fp32 ? 4 : 8;
+    c->DeltaT = T / n_sub;
+    c->S = steps_for(c->DeltaT, dt_fine);
+    c->dt = c->DeltaT / c->S;
+    c->T0 = o.T0 > 0 ? o.T0 : c->DeltaT;
+    c->S0 = steps_for(c->T0, c->dt);
+    const double dT = o.dT > 0 ? o.dT : c->DeltaT / 10.0;
+    c->Lc = steps_for(c->DeltaT, dT);
+    c->dT = c->DeltaT / c->Lc;
+    if (o.n_snap > 0) {
+        if (o.n_snap < 2) { delete c; return PR_ERR_INVALID_ARG; }
+        c->dM = std::max(1, c->S / (o.n_snap - 1));
+    } else {
+        c->dM = 5;
+    }
+    c->ns = c->S / c->dM + 1;
+    c->ns0 = c->S0 / c->dM + 1;
+    if (o.n_snap > 0) {
+        c->ns = std::min(c->ns, o.n_snap);
+        c->ns0 = std::min(c->ns0, o.n_snap);
+    }
+    c->nsmax = std::max(c->ns, c->ns0);
+    c->gamma1 = 1.0 - pod_tol;
+    c->gamma3 = 1.0 - (o.pod_tol3 > 0 ? o.pod_tol3 : pod_tol * 4e-3);
+    c->tau = o.rank_tau > 0 ? o.rank_tau : (c->fp32 ? 1e-6 : 1e-13);
+    c->lin_tol = o.lin_tol > 0 ? o.lin_tol : (c->fp32 ? 1e-9 : 1e-14);
+    const int cap = o.m_cap;
+    c->mcap0 = cap > 0 ? std::min(cap, c->ns0) : c->ns0;
+    c->mcap1 = cap > 0 ? std::min(cap, c->ns) : c->ns;
+    c->w2 = (o.m_l + 1) * c->mcap1 + o.p * std::max(c->mcap1, c->mcap0);
+    c->mcap2 = cap > 0 ? std::min(cap, c->w2) : c->w2;
+    c->mscr = std::max(c->mcap0, std::max(c->mcap1, c->mcap2));
+    c->maxK = std::max(c->nsmax, c->w2);
+    c->ldcols = c->maxK + 2;
+    c->has_f = false;
+    if (c->mcap2 > 32 || c->mcap0 > 33) {
+        delete c;
+        return PR_ERR_UNSUPPORTED;  // reduced systems are solved in one CTA (<= 33 unknowns)
+    }
+    if (c->maxK > 96) {
+        delete c;
+        return PR_ERR_UNSUPPORTED;  // Gram eigenproblems up to 96 x 96 (one CTA each)
+    }
+    c->max_ctas = fine_max_ctas(c->n, c->fp32, o.ctas_per_sm);
+    c->max_ctas = std::max(c->max_ctas, fine_max_ctas(c->n, false, o.ctas_per_sm));
+    c->groups_max = std::max(1, std::min(c->N, c->max_ctas));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        delete c;
+        return PR_ERR_CUDA;
+    }
+    c->ws_bytes = plan(c, nullptr);
+    *out = c;
+    return PR_OK;
+}
+
+void pr_destroy(pr_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->ref) cudaFree(c->ref);
+    if (c->ev_ready)
+        for (auto& e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+pr_status pr_get_sizes(const pr_ctx* c, int* S, int* S0, int* dM, int* n_s, int* n_s0, int* Lc,
+                       double* dt_eff, double* DeltaT) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (S) *S = c->S;
+    if (S0) *S0 = c->S0;
+    if (dM) *dM = c->dM;
+    if (n_s) *n_s = c->ns;
+    if (n_s0) *n_s0 = c->ns0;
+    if (Lc) *Lc = c->Lc;
+    if (dt_eff) *dt_eff = c->dt;
+    if (DeltaT) *DeltaT = c->DeltaT;
+    return PR_OK;
+}
+
+size_t pr_workspace_bytes(const pr_ctx* c) { return c ? c->ws_bytes : 0; }
+
+pr_status pr_bind_workspace(pr_ctx* c, void* p, size_t bytes) {
+    if (!c || !p) return PR_ERR_INVALID_ARG;
+    if (bytes < c->ws_bytes) return fail(c, PR_ERR_OOM, "bound workspace smaller than pr_workspace_bytes");
+    if ((reinterpret_cast<uintptr_t>(p) & 255) != 0) return fail(c, PR_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    c->own_ws = false;
+    c->ws = (char*)p;
+    c->ws_ready = false;
+    c->k_done = -1;
+    c->phase = 0;
+    c->initial_set = false;
+    return init_ws(c);
+}
+
+pr_status pr_set_stream(pr_ctx* c, void* s) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    c->st = (cudaStream_t)s;
+    return PR_OK;
+}
+
+pr_status pr_set_initial(pr_ctx* c, const double* u0, const double* f) {
+    if (!c || !u0) return PR_ERR_INVALID_ARG;
+    if (check_finite_host(u0, c->Ng) != PR_OK || (f && check_finite_host(f, c->Ng) != PR_OK))
+        return fail(c, PR_ERR_NONFINITE, "initial state or forcing holds NaN/Inf");
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    PR_CUDA(cudaMemcpyAsync(c->u0, u0, sizeof(double) * c->Ng, cudaMemcpyHostToDevice, c->st));
+    if (f) PR_CUDA(cudaMemcpyAsync(c->f, f, sizeof(double) * c->Ng, cudaMemcpyHostToDevice, c->st));
+    else PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    c->has_f = f != nullptr;
+    c->initial_set = true;
+    c->k_done = -1;
+    c->phase = 0;
+    return PR_OK;
+}
+
+pr_status pr_iteration0(pr_ctx* c) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (!c->initial_set) return fail(c, PR_ERR_STATE, "pr_set_initial first");
+    pr_status s;
+    const long long Ng = c->Ng;
+    double* U = c->Ubuf[0];
+    c->cur = 0;
+    // fine propagator on [0, T0] with snapshots (slot 0 of the snapshot store)
+    s = run_fine(c, c->u0, U, c->snap, 1, c->S0, c->ns0, 0, false);
+    if (s != PR_OK) return s;
+    // V0 = POD_Mode(W, gamma1)
+    s = cols_contig(c, c->snap, 0, c->cnst + 1, 0, 1, c->colsA, c->KA);
+    if (s != PR_OK) return s;
+    s = pod_pipeline(c, 1, c->ns0, c->gamma1, c->o.m_cap, c->mcap0, c->V0, (size_t)c->mcap0 * Ng, c->m0);
+    if (s != PR_OK) return s;
+    // Galerkin matrices of V0 and projections of u_hat0, f
+    s = galerkin(c, c->V0, (size_t)c->mcap0 * Ng, c->m0, 1, c->mcap0, c->M0, c->L0);
+    if (s != PR_OK) return s;
+    {
+        // p0 = V0^T u_hat0, q0 = V0^T f : gram of V0 columns against [u_hat0, f]
+        std::vector<const void*> bs = {U, c->f};
+        PR_CUDA(cudaMemcpyAsync(c->colsB, bs.data(), sizeof(void*) * 2, cudaMemcpyHostToDevice, c->st));
+        PR_CUDA(cudaStreamSynchronize(c->st));
+        GramArgs ga{};
+        ga.colsA = c->colsA;  // V0 columns from galerkin()
+        ga.colsB = c->colsB;
+        ga.KA = c->KA;
+        ga.KB = c->cnst + 3;  // 1 column
+        ga.ldcols = 0;
+        ga.Ng = Ng;
+        ga.B = 1;
+        ga.maxKA = c->mcap0;
+        ga.maxKB = 1;
+        ga.part = c->gpart;
+        ga.counter = c->counters;
+        ga.G = c->p0;
+        ga.ldG = 1;
+        ga.ldG_b = 0;
+        PR_CUDA(launch_gram(ga, c->fp32, false, c->st));
+        if (c->has_f) {
+            ga.colsB = c->colsB + 1;
+            ga.G = c->q0;
+            PR_CUDA(launch_gram(ga, c->fp32, false, c->st));
+        }
+    }
+    PR_CUDA(launch_g0(c->M0, c->L0, c->p0, c->has_f ? c->q0 : nullptr, c->m0, c->mcap0, c->N, c->Lc, c->dT,
+                      c->beta, c->mcap0, c->derr, c->st));
+    // U^0_{n+1} = V0 beta_n
+    s = cols_contig(c, c->V0, 0, c->m0, 0, c->N, c->colsA, c->KA);
+    if (s != PR_OK) return s;
+    TsmmArgs ta{};
+    ta.colsIn = c->colsA;
+    ta.KIN = c->KA;
+    ta.KOUT = c->ones;
+    ta.ldcols = c->ldcols;
+    ta.C = c->beta;
+    ta.ldC = 1;
+    ta.ldC_b = c->mcap0;
+    ta.out = U + Ng;
+    ta.ld_out_b = Ng;
+    ta.Ng = Ng;
+    ta.B = c->N;
+    ta.maxKIN = c->mcap0;
+    ta.maxKOUT = 1;
+    PR_CUDA(launch_tsmm(ta, c->fp32, false, c->st));
+    c->r1cur = 0;
+    c->k_done = 0;
+    c->phase = 0;
+    c->checked = true;
+    return PR_OK;
+}
+
+pr_status pr_fine_sweep(pr_ctx* c, int k) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (k < 1 || k > c->N) return fail(c, PR_ERR_INVALID_ARG, "k out of range");
+    if (c->k_done != k - 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "pr_fine_sweep out of order");
+    const long long Ng = c->Ng;
+    const int B = c->N - k + 1;
+    const double* Uprev = c->Ubuf[c->cur];
+    pr_status s = run_fine(c, Uprev + (size_t)(k - 1) * Ng, c->Fend + (size_t)(k - 1) * Ng,
+                           c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S, c->ns, k - 1, false);
+    if (s != PR_OK) return s;
+    c->phase = 1;
+    return PR_OK;
+}
+
+pr_status pr_pod_update(pr_ctx* c, int k) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (c->k_done != k - 1 || c->phase != 1) return fail(c, PR_ERR_STATE, "pr_pod_update out of order");
+    const long long Ng = c->Ng;
+    const int N = c->N;
+    pr_status s;
+    // level 1: n = k-1 .. N-1 into R1[nw] (the other buffer)
+    const int nw = 1 - c->r1cur;
+    const int B1 = N - k + 1;
+    {
+        s = cols_contig(c, c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, (size_t)c->ns * Ng * c->esz,
+                        c->cnst + 0, 0, B1, c->colsA, c->KA);
+        if (s != PR_OK) return s;
+        s = pod_pipeline(c, B1, c->ns, c->gamma1, c->o.m_cap, c->mcap1,
+                         c->R1[nw] + (size_t)(k - 1) * c->mcap1 * Ng * c->esz, (size_t)c->mcap1 * Ng,
+                         c->m1[nw] + (k - 1));
+        if (s != PR_OK) return s;
+    }
+    // level 2: n = k .. N-1
+    const int B2 = N - k;
+    if (B2 > 0) {
+        std::vector<const void*> bs;
+        std::vector<const int*> cs;
+        const int nb = 3;
+        const size_t colstride = (size_t)c->mcap1 * Ng * c->esz;
+        for (int n = k; n < N; ++n) {
+            // left neighbour(s), this subinterval, previous iteration (V0 at k = 1)
+            if (c->o.m_l >= 1) {
+                bs.push_back(c->R1[nw] + (size_t)(n - 1) * colstride);
+                cs.push_back(c->m1[nw] + (n - 1));
+            } else {
+                bs.push_back(nullptr);
+                cs.push_back(nullptr);
+            }
+            bs.push_back(c->R1[nw] + (size_t)n * colstride);
+            cs.push_back(c->m1[nw] + n);
+            if (c->o.p >= 1) {
+                if (k == 1) {
+                    bs.push_back(c->V0);
+                    cs.push_back(c->m0);
+                } else {
+                    bs.push_back(c->R1[1 - nw] + (size_t)n * colstride);
+                    cs.push_back(c->m1[1 - nw] + n);
+                }
+            } else {
+                bs.push_back(nullptr);
+                cs.push_back(nullptr);
+            }
+        }
+        s = upload_blocks(c, bs, cs, nb, B2, c->colsA, c->KA);
+        if (s != PR_OK) return s;
+        s = pod_pipeline(c, B2, c->w2, c->gamma3, c->o.m_cap, c->mcap2,
+                         c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k);
+        if (s != PR_OK) return s;
+        s = galerkin(c, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k, B2,
+                     c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * c->mcap2 * c->mcap2);
+        if (s != PR_OK) return s;
+    }
+    c->r1cur = nw;
+    c->phase = 2;
+    return PR_OK;
+}
+
+static CoarseArgs coarse_args(pr_ctx* c) {
+    CoarseArgs a{};
+    a.g = grid_of(c);
+    a.maxm = c->mcap2;
+    a.dT = c->dT;
+    a.Lc = c->Lc;
+    a.aug_tol = c->o.aug_tol;
+    a.d = c->cd;
+    a.Ld = c->cLd;
+    a.Ltd = c->cLtd;
+    a.dots = c->cdots;
+    a.part = c->cpart;
+    a.counter = c->counters + c->N + 16;
+    a.coef = c->coef;
+    a.err = c->derr;
+    return a;
+}
+
+pr_status pr_coarse_sweep(pr_ctx* c, int k) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (c->k_done != k - 1 || c->phase != 2) return fail(c, PR_ERR_STATE, "pr_coarse_sweep out of order");
+    const long long Ng = c->Ng;
+    const double* Uold = c->Ubuf[c->cur];
+    double* Unew = c->Ubuf[1 - c->cur];
+    PR_CUDA(cudaMemcpyAsync(Unew, Uold, sizeof(double) * (size_t)k * Ng, cudaMemcpyDeviceToDevice, c->st));
+    PR_CUDA(cudaMemcpyAsync(Unew + (size_t)k * Ng, c->Fend + (size_t)(k - 1) * Ng, sizeof(double) * Ng,
+                            cudaMemcpyDeviceToDevice, c->st));
+    CoarseArgs a = coarse_args(c);
+    for (int n = k; n < c->N; ++n) {
+        a.R = c->R2 + (size_t)n * c->mcap2 * Ng * c->esz;
+        a.m_ptr = c->m2 + n;
+        a.U = Unew + (size_t)n * Ng;
+        a.Up = Uold + (size_t)n * Ng;
+        a.F = c->Fend + (size_t)n * Ng;
+        a.out = Unew + (size_t)(n + 1) * Ng;
+        a.Mr = c->Mr + (size_t)n * c->mcap2 * c->mcap2;
+        a.Lr = c->Lr + (size_t)n * c->mcap2 * c->mcap2;
+        PR_CUDA(launch_coarse_update(a, c->fp32, c->st));
+    }
+    c->cur = 1 - c->cur;
+    c->k_done = k;
+    c->phase = 0;
+    c->checked = false;
+    return PR_OK;
+}
+
+pr_status pr_check(pr_ctx* c, int k, double* max_inc, double* max_err) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (c->k_done != k || k < 1) return fail(c, PR_ERR_STATE, "pr_check needs pr_coarse_sweep(k) first");
+    const long long Ng = c->Ng;
+    const int cnt = c->N + 1;
+    PR_CUDA(launch_norms(c->Ubuf[c->cur], c->Ubuf[1 - c->cur], c->ref, Ng, cnt, c->npart, c->counters + 0,
+                         c->nout, c->st));
+    std::vector<double> h(4 * cnt);
+    PR_CUDA(cudaMemcpyAsync(h.data(), c->nout, sizeof(double) * 4 * cnt, cudaMemcpyDeviceToHost, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    pr_status s = read_device_errors(c);
+    if (s != PR_OK) return s;
+    c->last_inc.assign(cnt, 0.0);
+    c->last_err.assign(cnt, -1.0);
+    double mi = 0.0, me = c->ref ? 0.0 : -1.0;
+    bool finite = true;
+    for (int n = 0; n < cnt; ++n) {
+        const double d2 = h[4 * n], a2 = h[4 * n + 1];
+        const double inc = a2 > 0 ? std::sqrt(d2 / a2) : std::sqrt(d2);
+        c->last_inc[n] = inc;
+        mi = std::max(mi, inc);
+        if (!std::isfinite(inc)) finite = false;
+        if (c->ref) {
+            const double e2 = h[4 * n + 2], r2 = h[4 * n + 3];
+            const double err = r2 > 0 ? std::sqrt(e2 / r2) : std::sqrt(e2);
+            c->last_err[n] = err;
+            me = std::max(me, err);
+        }
+    }
+    c->checked = true;
+    if (max_inc) *max_inc = mi;
+    if (max_err) *max_err = me;
+    if (!finite) return fail(c, PR_ERR_NONFINITE, "non-finite interface state");
+    return PR_OK;
+}
+
+pr_status pr_sync(pr_ctx* c) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    if (!c->ws_ready) return PR_OK;
+    return read_device_errors(c);
+}
+
+static pr_status alloc_ref(pr_ctx* c) {
+    if (c->ref) return PR_OK;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(double) * (size_t)(c->N + 1) * c->Ng);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PR_ERR_OOM, "reference allocation failed");
+    }
+    c->ref = (double*)p;
+    return PR_OK;
+}
+
+pr_status pr_set_reference(pr_ctx* c, const double* U, int on_device) {
+    if (!c || !U) return PR_ERR_INVALID_ARG;
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    s = alloc_ref(c);
+    if (s != PR_OK) return s;
+    PR_CUDA(cudaMemcpyAsync(c->ref, U, sizeof(double) * (size_t)(c->N + 1) * c->Ng,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    return PR_OK;
+}
+
+pr_status pr_compute_reference(pr_ctx* c, int fp64) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (!c->initial_set) return fail(c, PR_ERR_STATE, "pr_set_initial first");
+    pr_status s = alloc_ref(c);
+    if (s != PR_OK) return s;
+    const long long Ng = c->Ng;
+    const bool force = fp64 != 0;
+    s = run_fine(c, c->u0, c->ref, nullptr, 1, c->S0, 0, c->N, force);
+    if (s != PR_OK) return s;
+    for (int n = 0; n < c->N; ++n) {
+        s = run_fine(c, c->ref + (size_t)n * Ng, c->ref + (size_t)(n + 1) * Ng, nullptr, 1, c->S, 0, c->N,
+                     force);
+        if (s != PR_OK) return s;
+    }
+    return pr_sync(c);
+}
+
+pr_status pr_solve(pr_ctx* c, double tol, int k_max, const double* ref, pr_report* rep) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (!c->initial_set) return fail(c, PR_ERR_STATE, "pr_set_initial first");
+    pr_status s;
+    if (ref) {
+        s = pr_set_reference(c, ref, 0);
+        if (s != PR_OK) return s;
+    }
+    pr_report R;
+    std::memset(&R, 0, sizeof(R));
+    R.max_err = -1.0;
+    const int kmax = (k_max <= 0) ? c->N : std::min(k_max, c->N);
+    cudaEvent_t* ev = c->ev;
+    PR_CUDA(cudaEventRecord(ev[0], c->st));
+    if (c->k_done < 0) {
+        s = pr_iteration0(c);
+        if (s != PR_OK) return s;
+    }
+    PR_CUDA(cudaEventRecord(ev[1], c->st));
+    PR_CUDA(cudaEventSynchronize(ev[1]));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    R.t_iter0 = ms * 1e-3;
+    R.t_total = R.t_iter0;
+    long long its_sum = 0, steps_sum = 0;
+    for (int k = c->k_done + 1; k <= kmax; ++k) {
+        PR_CUDA(cudaEventRecord(ev[2], c->st));
+        if ((s = pr_fine_sweep(c, k)) != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(ev[3], c->st));
+        if ((s = pr_pod_update(c, k)) != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(ev[4], c->st));
+        if ((s = pr_coarse_sweep(c, k)) != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(ev[5], c->st));
+        double mi = 0, me = -1;
+        if ((s = pr_check(c, k, &mi, &me)) != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(ev[6], c->st));
+        PR_CUDA(cudaEventSynchronize(ev[6]));
+        float a, b2, d, e2;
+        cudaEventElapsedTime(&a, ev[2], ev[3]);
+        cudaEventElapsedTime(&b2, ev[3], ev[4]);
+        cudaEventElapsedTime(&d, ev[4], ev[5]);
+        cudaEventElapsedTime(&e2, ev[5], ev[6]);
+        R.t_fine += a * 1e-3;
+        R.t_pod += b2 * 1e-3;
+        R.t_coarse += d * 1e-3;
+        R.t_check += e2 * 1e-3;
+        R.t_total += (a + b2 + d + e2) * 1e-3;
+        R.k = k;
+        R.max_inc = mi;
+        R.max_err = me;
+        const int B = c->N - k + 1;
+        R.fine_dof_steps += (double)B * c->S * (double)c->Ng;
+        std::vector<int> tot(c->N + 1), mx(c->N + 1);
+        PR_CUDA(cudaMemcpy(tot.data(), c->fits, sizeof(int) * (c->N + 1), cudaMemcpyDeviceToHost));
+        PR_CUDA(cudaMemcpy(mx.data(), c->fitsmax, sizeof(int) * (c->N + 1), cudaMemcpyDeviceToHost));
+        for (int n = k - 1; n < c->N; ++n) {
+            its_sum += tot[n];
+            R.lin_iters_max = std::max(R.lin_iters_max, mx[n]);
+        }
+        steps_sum += (long long)B * c->S;
+        const double crit = c->ref ? me : mi;
+        if (crit <= tol) {
+            R.converged = 1;
+            break;
+        }
+    }
+    R.lin_iters_mean = steps_sum ? (double)its_sum / steps_sum : 0.0;
+    {
+        int m0 = 0;
+        std::vector<int> m1(c->N), m2(c->N);
+        PR_CUDA(cudaMemcpy(&m0, c->m0, sizeof(int), cudaMemcpyDeviceToHost));
+        PR_CUDA(cudaMemcpy(m1.data(), c->m1[c->r1cur], sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+        PR_CUDA(cudaMemcpy(m2.data(), c->m2, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+        R.m0 = m0;
+        for (int n = std::max(0, R.k - 1); n < c->N; ++n) R.m1_max = std::max(R.m1_max, m1[n]);
+        for (int n = std::max(1, R.k); n < c->N; ++n) R.m2_max = std::max(R.m2_max, m2[n]);
+    }
+    if (rep) *rep = R;
+    return PR_OK;
+}
+
+pr_status pr_get_interface(pr_ctx* c, int n, double* out) {
+    if (!c || !out || n < 0 || n > c->N) return PR_ERR_INVALID_ARG;
+    if (c->k_done < 0) return fail(c, PR_ERR_STATE, "no iterate yet");
+    PR_CUDA(cudaMemcpyAsync(out, c->Ubuf[c->cur] + (size_t)n * c->Ng, sizeof(double) * c->Ng,
+                            cudaMemcpyDeviceToHost, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    return PR_OK;
+}
+
+pr_status pr_get_interfaces(pr_ctx* c, double* out) {
+    if (!c || !out) return PR_ERR_INVALID_ARG;
+    if (c->k_done < 0) return fail(c, PR_ERR_STATE, "no iterate yet");
+    PR_CUDA(cudaMemcpyAsync(out, c->Ubuf[c->cur], sizeof(double) * (size_t)(c->N + 1) * c->Ng,
+                            cudaMemcpyDeviceToHost, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    return PR_OK;
+}
+
+pr_status pr_set_interfaces(pr_ctx* c, const double* U, int k_done) {
+    if (!c || !U || k_done < 0 || k_done >= c->N) return PR_ERR_INVALID_ARG;
+    if (c->k_done < 0) return fail(c, PR_ERR_STATE, "iteration 0 must have run (V0 is part of the state)");
+    if (k_done >= 1 && c->k_done < 1)
+        return fail(c, PR_ERR_STATE, "level-1 bases of iteration k_done are not available");
+    PR_CUDA(cudaMemcpyAsync(c->Ubuf[c->cur], U, sizeof(double) * (size_t)(c->N + 1) * c->Ng,
+                            cudaMemcpyHostToDevice, c->st));
+    c->k_done = k_done;
+    c->phase = 0;
+    return PR_OK;
+}
+
+pr_status pr_get_diagnostics(pr_ctx* c, double* inc, double* err, int* m0, int* m1, int* m2) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    const int cnt = c->N + 1;
+    if (inc) for (int n = 0; n < cnt; ++n) inc[n] = n < (int)c->last_inc.size() ? c->last_inc[n] : 0.0;
+    if (err) for (int n = 0; n < cnt; ++n) err[n] = n < (int)c->last_err.size() ? c->last_err[n] : -1.0;
+    if (!c->ws_ready) return PR_OK;
+    if (m0) PR_CUDA(cudaMemcpy(m0, c->m0, sizeof(int), cudaMemcpyDeviceToHost));
+    if (m1) PR_CUDA(cudaMemcpy(m1, c->m1[c->r1cur], sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    if (m2) PR_CUDA(cudaMemcpy(m2, c->m2, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    return PR_OK;
+}
+
+pr_status pr_get_lin_stats(pr_ctx* c, int* total, int* mx) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    if (total) PR_CUDA(cudaMemcpy(total, c->fits, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    if (mx) PR_CUDA(cudaMemcpy(mx, c->fitsmax, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    return PR_OK;
+}
+
+pr_status pr_rewind(pr_ctx* c) {
+    if (!c) return PR_ERR_INVALID_ARG;
+    if (c->k_done < 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "no completed iteration to undo");
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    c->cur = 1 - c->cur;
+    c->r1cur = 1 - c->r1cur;
+    c->k_done -= 1;
+    c->phase = 0;
+    return PR_OK;
+}
+
+pr_status pr_get_fine_end(pr_ctx* c, int n, double* out) {
+    if (!c || !out || n < 0 || n >= c->N) return PR_ERR_INVALID_ARG;
+    if (!c->ws_ready) return fail(c, PR_ERR_STATE, "no workspace");
+    PR_CUDA(cudaMemcpyAsync(out, c->Fend + (size_t)n * c->Ng, sizeof(double) * c->Ng,
+                            cudaMemcpyDeviceToHost, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    return PR_OK;
+}
+
+pr_status pr_get_snapshots(pr_ctx* c, int n, void* out) {
+    if (!c || !out || n < 0 || n >= c->N) return PR_ERR_INVALID_ARG;
+    if (!c->ws_ready) return fail(c, PR_ERR_STATE, "no workspace");
+    const size_t per = (size_t)c->ns * c->Ng * c->esz;
+    PR_CUDA(cudaMemcpyAsync(out, c->snap + (size_t)n * per, per, cudaMemcpyDeviceToHost, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    return PR_OK;
+}
+
+pr_status pr_get_basis(pr_ctx* c, int level, int n, void* out, int* m_out) {
+    if (!c || !m_out || level < 0 || level > 2) return PR_ERR_INVALID_ARG;
+    if (level > 0 && (n < 0 || n >= c->N)) return PR_ERR_INVALID_ARG;
+    if (!c->ws_ready) return fail(c, PR_ERR_STATE, "no workspace");
+    const size_t col = (size_t)c->Ng * c->esz;
+    const char* base;
+    const int* mp;
+    if (level == 0) { base = c->V0; mp = c->m0; }
+    else if (level == 1) { base = c->R1[c->r1cur] + (size_t)n * c->mcap1 * col; mp = c->m1[c->r1cur] + n; }
+    else { base = c->R2 + (size_t)n * c->mcap2 * col; mp = c->m2 + n; }
+    int m = 0;
+    PR_CUDA(cudaMemcpyAsync(&m, mp, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    *m_out = m;
+    if (out && m > 0) {
+        PR_CUDA(cudaMemcpyAsync(out, base, (size_t)m * col, cudaMemcpyDeviceToHost, c->st));
+        PR_CUDA(cudaStreamSynchronize(c->st));
+    }
+    return PR_OK;
+}
+
+// ---------------------------------------------------------------------------------
+pr_status pr_op_apply_L(pr_ctx* c, const double* d_in, double* d_out, int count, int transpose) {
+    if (!c || !d_in || !d_out || count < 0) return PR_ERR_INVALID_ARG;
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    Grid g = grid_of(c);
+    for (int c0 = 0; c0 < count; c0 += c->N + 1) {
+        const int B = std::min(count - c0, c->N + 1);
+        std::vector<const void*> in(B), out(B);
+        for (int b = 0; b < B; ++b) {
+            in[b] = d_in + (size_t)(c0 + b) * c->Ng;
+            out[b] = d_out + (size_t)(c0 + b) * c->Ng;
+        }
+        PR_CUDA(cudaMemcpyAsync(c->colsA, in.data(), sizeof(void*) * B, cudaMemcpyHostToDevice, c->st));
+        PR_CUDA(cudaMemcpyAsync(c->colsB, out.data(), sizeof(void*) * B, cudaMemcpyHostToDevice, c->st));
+        PR_CUDA(launch_apply_L(g, c->colsA, (void* const*)c->colsB, c->ones, 1, 1, B, false, false,
+                               transpose != 0, c->st));
+        PR_CUDA(cudaStreamSynchronize(c->st));
+    }
+    return PR_OK;
+}
+
+pr_status pr_op_fine(pr_ctx* c, const double* d_in, double* d_out, void* d_snap, int B, double t0,
+                     int steps, int dM, int n_snap) {
+    (void)t0;  // time-independent flows
+    if (!c || !d_in || !d_out || B < 1 || B > c->N || steps < 1) return PR_ERR_INVALID_ARG;
+    if (n_snap < 0 || (n_snap > 0 && (!d_snap || dM < 1))) return PR_ERR_INVALID_ARG;
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    const int saved = c->dM;
+    c->dM = dM > 0 ? dM : 1;
+    s = run_fine(c, d_in, d_out, (char*)d_snap, B, steps, n_snap, 0, false);
+    c->dM = saved;
+    if (s != PR_OK) return s;
+    return pr_sync(c);
+}
+
+pr_status pr_op_pod(pr_ctx* c, const void* d_W, int n_cols, int B, double gamma, int cap, void* d_R,
+                    int* m_out) {
+    if (!c || !d_W || !d_R || !m_out || B < 1 || B > c->N || n_cols < 1) return PR_ERR_INVALID_ARG;
+    if (n_cols > c->maxK || !(gamma > 0 && gamma <= 1)) return PR_ERR_INVALID_ARG;
+    const int mmax = cap > 0 ? std::min(cap, n_cols) : n_cols;
+    if (mmax > c->mscr) return fail(c, PR_ERR_INVALID_ARG, "POD dimension above the context's cap");
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    int nc = n_cols;
+    PR_CUDA(cudaMemcpy(c->cnst + 2, &nc, sizeof(int), cudaMemcpyHostToDevice));
+    s = cols_contig(c, (const char*)d_W, (size_t)n_cols * c->Ng * c->esz, c->cnst + 2, 0, B, c->colsA, c->KA);
+    if (s != PR_OK) return s;
+    s = pod_pipeline(c, B, n_cols, gamma, cap, mmax, (char*)d_R, (size_t)mmax * c->Ng, c->mop);
+    if (s != PR_OK) return s;
+    PR_CUDA(cudaMemcpyAsync(m_out, c->mop, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st));
+    return pr_sync(c);
+}
+
+pr_status pr_op_coarse_update(pr_ctx* c, const void* d_R, int m, const double* d_U, const double* d_Uprev,
+                              const double* d_F, double* d_out) {
+    if (!c || !d_R || !d_U || !d_Uprev || !d_F || !d_out || m < 0) return PR_ERR_INVALID_ARG;
+    if (m > c->mcap2) return fail(c, PR_ERR_INVALID_ARG, "m above the context's level-2 cap");
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    PR_CUDA(cudaMemcpy(c->m2 + c->N, &m, sizeof(int), cudaMemcpyHostToDevice));
+    double* Mr = c->Mr + (size_t)c->N * c->mcap2 * c->mcap2;
+    double* Lr = c->Lr + (size_t)c->N * c->mcap2 * c->mcap2;
+    if (m > 0) {
+        s = galerkin(c, (char*)d_R, (size_t)c->mcap2 * c->Ng, c->m2 + c->N, 1, c->mcap2, Mr, Lr);
+        if (s != PR_OK) return s;
+    }
+    CoarseArgs a = coarse_args(c);
+    a.R = d_R;
+    a.m_ptr = c->m2 + c->N;
+    a.U = d_U;
+    a.Up = d_Uprev;
+    a.F = d_F;
+    a.out = d_out;
+    a.Mr = Mr;
+    a.Lr = Lr;
+    PR_CUDA(launch_coarse_update(a, c->fp32, c->st));
+    return pr_sync(c);
+}
+
+}  // extern "C"

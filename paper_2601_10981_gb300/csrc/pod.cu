@@ -1,0 +1,503 @@
+// POD of snapshot matrices (Algorithm 1, POD_Mode, and the two-level POD of Case II):
+//   Gram W^T M W (M = I)           -> gram_kernel     (batched, split over points)
+//   eigenpairs, rank r, dimension m -> eig_pod_kernel  (cyclic Jacobi, FP64, one CTA/matrix)
+//   R = W Y_m Lambda_m^{-1/2}       -> tsmm_kernel     (tall-skinny multiply)
+//   CholQR2 re-orthonormalisation   -> gram + chol_inv_kernel + tsmm, twice
+// The Gram and projection stream every snapshot once per use; the small dense steps stay
+// in FP64 because their stability needs it (Gram-based POD squares the conditioning).
+#include "pr_internal.cuh"
+
+#include <algorithm>
+#include <math.h>
+
+namespace pr {
+
+constexpr int GRAM_THREADS = 256;
+constexpr int GRAM_SUB = 32;
+
+int gram_chunks(long long Ng) {
+    long long ch = (Ng / 128 + 31) / 32 * 32;
+    ch = std::max<long long>(256, std::min<long long>(16384, ch));
+    return (int)((Ng + ch - 1) / ch);
+}
+static long long gram_chunk_len(long long Ng) {
+    const int c = gram_chunks(Ng);
+    long long ch = (Ng + c - 1) / c;
+    return (ch + GRAM_SUB - 1) / GRAM_SUB * GRAM_SUB;
+}
+size_t gram_part_doubles(long long Ng, int B, int maxKA, int maxKB) {
+    return (size_t)B * gram_chunks(Ng) * (size_t)maxKA * maxKB;
+}
+
+// Output o of a batch item -> (i, j).  Non-symmetric: row-major KA x KB.  Symmetric:
+// the upper triangle i <= j enumerated row by row.
+__device__ __forceinline__ void out_index(int o, int KA, int KB, bool sym, int& i, int& j) {
+    if (!sym) {
+        i = o / KB;
+        j = o - i * KB;
+        return;
+    }
+    // rows i have KA - i entries; find i with cumulative count
+    int rem = o, row = 0, len = KA;
+    while (rem >= len) { rem -= len; ++row; --len; }
+    i = row;
+    j = row + rem;
+}
+
+template <typename TA, typename TB, typename TACC, int MAXO>
+__global__ void __launch_bounds__(GRAM_THREADS) gram_kernel(GramArgs a, long long CH, int chunks) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.y, c = blockIdx.x;
+    const int KA = a.KA[b];
+    const int KB = a.sym ? KA : a.KB[b];
+    const int nout = a.sym ? KA * (KA + 1) / 2 : KA * KB;
+    const long long p_lo = (long long)c * CH;
+    const long long p_hi = min(a.Ng, p_lo + CH);
+    const int lda = KA + 1, ldb = KB + 1;
+    TACC* sA = reinterpret_cast<TACC*>(smem_raw);
+    TACC* sB = a.sym ? sA : sA + GRAM_SUB * lda;
+    const void* const* colsA = a.colsA + (size_t)b * a.ldcols;
+    const void* const* colsB = (a.sym ? a.colsA : a.colsB) + (size_t)b * a.ldcols;
+
+    int oi[MAXO], oj[MAXO];
+    double acc64[MAXO];
+    TACC acc[MAXO];
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+        const int o = threadIdx.x + k * GRAM_THREADS;
+        int i = 0, j = 0;
+        if (o < nout) out_index(o, KA, KB, a.sym, i, j);
+        oi[k] = (o < nout) ? i : -1;
+        oj[k] = j;
+        acc64[k] = 0.0;
+        acc[k] = (TACC)0;
+    }
+    for (long long p0 = p_lo; p0 < p_hi; p0 += GRAM_SUB) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < GRAM_SUB * KA; e += GRAM_THREADS) {
+            const int col = e / GRAM_SUB, pp = e - col * GRAM_SUB;
+            const long long p = p0 + pp;
+            sA[pp * lda + col] = (p < p_hi) ? (TACC)(reinterpret_cast<const TA*>(colsA[col])[p]) : (TACC)0;
+        }
+        if (!a.sym) {
+            for (int e = threadIdx.x; e < GRAM_SUB * KB; e += GRAM_THREADS) {
+                const int col = e / GRAM_SUB, pp = e - col * GRAM_SUB;
+                const long long p = p0 + pp;
+                sB[pp * ldb + col] = (p < p_hi) ? (TACC)(reinterpret_cast<const TB*>(colsB[col])[p]) : (TACC)0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < MAXO; ++k) {
+            if (oi[k] >= 0) {
+                const TACC* pa = sA + oi[k];
+                const TACC* pb = sB + oj[k];
+                TACC s = acc[k];
+#pragma unroll 8
+                for (int pp = 0; pp < GRAM_SUB; ++pp) s += pa[pp * lda] * pb[pp * ldb];
+                acc[k] = s;
+            }
+        }
+        if (sizeof(TACC) == 4) {
+#pragma unroll
+            for (int k = 0; k < MAXO; ++k) { acc64[k] += (double)acc[k]; acc[k] = (TACC)0; }
+        }
+    }
+    const size_t outsz = (size_t)a.maxKA * a.maxKB;
+    double* mypart = a.part + ((size_t)b * chunks + c) * outsz;
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+        if (oi[k] >= 0) {
+            const double v = (sizeof(TACC) == 4) ? acc64[k] : (double)acc[k];
+            mypart[(size_t)oi[k] * a.maxKB + oj[k]] = v;
+        }
+    }
+    // last CTA of this batch item reduces the chunk partials in chunk order
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atom_add_acq_rel_u32(a.counter + b, 1u);
+        s_last = (ticket == (unsigned)chunks - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double* bpart = a.part + (size_t)b * chunks * outsz;
+    double* Gb = a.G + (size_t)b * a.ldG_b;
+    for (int o = threadIdx.x; o < nout; o += GRAM_THREADS) {
+        int i, j;
+        out_index(o, KA, KB, a.sym, i, j);
+        double s = 0.0;
+        for (int cc = 0; cc < chunks; ++cc) s += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
+        Gb[(size_t)i * a.ldG + j] = s;
+        if (a.sym) Gb[(size_t)j * a.ldG + i] = s;
+    }
+    if (threadIdx.x == 0) st_relaxed_u32(a.counter + b, 0u);
+}
+
+template <typename TA, typename TB, typename TACC>
+static cudaError_t gram_dispatch(const GramArgs& a, cudaStream_t st) {
+    const int chunks = gram_chunks(a.Ng);
+    const long long CH = gram_chunk_len(a.Ng);
+    const int nout = a.sym ? a.maxKA * (a.maxKA + 1) / 2 : a.maxKA * a.maxKB;
+    const int need = (nout + GRAM_THREADS - 1) / GRAM_THREADS;
+    const size_t smem = (size_t)GRAM_SUB * ((a.maxKA + 1) + (a.sym ? 0 : a.maxKB + 1)) * sizeof(TACC);
+    dim3 grid(chunks, a.B);
+    if (need <= 2)
+        gram_kernel<TA, TB, TACC, 2><<<grid, GRAM_THREADS, smem, st>>>(a, CH, chunks);
+    else if (need <= 4)
+        gram_kernel<TA, TB, TACC, 4><<<grid, GRAM_THREADS, smem, st>>>(a, CH, chunks);
+    else if (need <= 10)
+        gram_kernel<TA, TB, TACC, 10><<<grid, GRAM_THREADS, smem, st>>>(a, CH, chunks);
+    else if (need <= 20)
+        gram_kernel<TA, TB, TACC, 20><<<grid, GRAM_THREADS, smem, st>>>(a, CH, chunks);
+    else if (need <= 40)
+        gram_kernel<TA, TB, TACC, 40><<<grid, GRAM_THREADS, smem, st>>>(a, CH, chunks);
+    else
+        return cudaErrorInvalidValue;
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t st) {
+    if (a.B <= 0 || a.maxKA <= 0 || (!a.sym && a.maxKB <= 0)) return cudaSuccess;
+    // FP32 accumulation only when both operands are FP32.
+    if (a_f32 && (b_f32 || a.sym)) return gram_dispatch<float, float, float>(a, st);
+    if (a_f32) return gram_dispatch<float, double, double>(a, st);
+    if (b_f32) return gram_dispatch<double, float, double>(a, st);
+    return gram_dispatch<double, double, double>(a, st);
+}
+
+// ------------------------------------------------------------------------------------
+// Out_b = In_b C_b.
+template <typename TI, typename TO, typename TC>
+__global__ void __launch_bounds__(256) tsmm_kernel(TsmmArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TC* sC = reinterpret_cast<TC*>(smem_raw);
+    const int b = blockIdx.y;
+    const int KIN = a.KIN[b], KOUT = a.KOUT[b];
+    if (KOUT <= 0) return;
+    const double* Cb = a.C + (size_t)b * a.ldC_b;
+    for (int e = threadIdx.x; e < KIN * KOUT; e += blockDim.x) {
+        const int i = e / KOUT, j = e - i * KOUT;
+        sC[e] = (TC)Cb[(size_t)i * a.ldC + j];
+    }
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.Ng) return;
+    const void* const* cols = a.colsIn + (size_t)b * a.ldcols;
+    TO* out = reinterpret_cast<TO*>(a.out) + (size_t)b * a.ld_out_b;
+    for (int j0 = 0; j0 < KOUT; j0 += 32) {
+        const int jn = min(32, KOUT - j0);
+        TC acc[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) acc[jj] = (TC)0;
+        for (int i = 0; i < KIN; ++i) {
+            const TC x = (TC)(reinterpret_cast<const TI*>(cols[i])[p]);
+            const TC* crow = sC + i * KOUT + j0;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+                if (jj < jn) acc[jj] += x * crow[jj];
+        }
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+            if (jj < jn) out[(size_t)(j0 + jj) * a.Ng + p] = (TO)acc[jj];
+    }
+}
+
+cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream_t st) {
+    if (a.B <= 0 || a.maxKOUT <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((a.Ng + 255) / 256), a.B);
+    if (in_f32 && out_f32) {
+        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(float);
+        tsmm_kernel<float, float, float><<<grid, 256, smem, st>>>(a);
+    } else if (!in_f32 && out_f32) {
+        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(float);
+        tsmm_kernel<double, float, float><<<grid, 256, smem, st>>>(a);
+    } else if (in_f32) {
+        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
+        tsmm_kernel<float, double, double><<<grid, 256, smem, st>>>(a);
+    } else {
+        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
+        tsmm_kernel<double, double, double><<<grid, 256, smem, st>>>(a);
+    }
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Batched symmetric eigensolver (parallel cyclic Jacobi, round-robin pairing) + POD
+// selection of Algorithm 1.
+constexpr int EIG_THREADS = 256;
+constexpr int EIG_MAX_SWEEPS = 40;
+
+__device__ __forceinline__ void rr_pair(int r, int i, int Kp, int& p, int& q) {
+    const int M = Kp - 1;
+    if (i == 0) {
+        p = M;
+        q = r;
+    } else {
+        p = (r + i) % M;
+        q = (r - i + M) % M;
+    }
+}
+
+__global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    const int K = a.K[b];
+    double* lam_out = a.lam + (size_t)b * a.maxK;
+    double* Cb = a.C + (size_t)b * a.ldC_b;
+    if (K <= 0) {
+        if (threadIdx.x == 0) a.m[b] = 0;
+        return;
+    }
+    const int Kp = K + (K & 1);
+    const int ld = Kp;
+    double* A = reinterpret_cast<double*>(smem_raw);
+    double* V = A + (size_t)Kp * ld;
+    double* cs = V + (size_t)Kp * ld;           // [Kp/2][2]
+    double* lam = cs + Kp;                       // [Kp]
+    int* perm = reinterpret_cast<int*>(lam + Kp);  // [Kp]
+    __shared__ double red[32];
+    __shared__ int s_stop;
+    const double* Gb = a.G + (size_t)b * a.ldG_b;
+    for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) {
+        const int i = e / Kp, j = e - i * Kp;
+        A[i * ld + j] = (i < K && j < K) ? Gb[(size_t)i * a.ldG + j] : 0.0;
+        V[i * ld + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int npair = Kp / 2;
+    for (int sweep = 0; sweep < EIG_MAX_SWEEPS; ++sweep) {
+        // convergence: off-diagonal Frobenius norm against the whole matrix
+        double off = 0.0, tot = 0.0;
+        for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+            const int i = e / K, j = e - i * K;
+            const double v = A[i * ld + j];
+            tot += v * v;
+            if (i != j) off += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_down_sync(0xffffffffu, off, o);
+            tot += __shfl_down_sync(0xffffffffu, tot, o);
+        }
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = off; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double so = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) so += red[w];
+            red[31] = so;
+        }
+        __syncthreads();
+        const double offsum = red[31];
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = tot; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double st = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) st += red[w];
+            s_stop = (offsum <= 1e-32 * st) || st == 0.0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        for (int r = 0; r < Kp - 1; ++r) {
+            for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+                int p, q;
+                rr_pair(r, i, Kp, p, q);
+                double c = 1.0, s = 0.0;
+                if (p < K && q < K) {
+                    const double apq = A[p * ld + q];
+                    const double app = A[p * ld + p], aqq = A[q * ld + q];
+                    if (apq != 0.0 && fabs(apq) > 1e-300) {
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        s = tt * c;
+                    }
+                }
+                cs[2 * i] = c;
+                cs[2 * i + 1] = s;
+            }
+            __syncthreads();
+            // A <- A J, V <- V J (columns p, q)
+            for (int w = threadIdx.x; w < Kp * npair; w += blockDim.x) {
+                const int i = w % npair, k = w / npair;
+                int p, q;
+                rr_pair(r, i, Kp, p, q);
+                const double c = cs[2 * i], s = cs[2 * i + 1];
+                if (s == 0.0) continue;
+                const double akp = A[k * ld + p], akq = A[k * ld + q];
+                A[k * ld + p] = c * akp - s * akq;
+                A[k * ld + q] = s * akp + c * akq;
+                const double vkp = V[k * ld + p], vkq = V[k * ld + q];
+                V[k * ld + p] = c * vkp - s * vkq;
+                V[k * ld + q] = s * vkp + c * vkq;
+            }
+            __syncthreads();
+            // A <- J^T A (rows p, q)
+            for (int w = threadIdx.x; w < Kp * npair; w += blockDim.x) {
+                const int i = w % npair, k = w / npair;
+                int p, q;
+                rr_pair(r, i, Kp, p, q);
+                const double c = cs[2 * i], s = cs[2 * i + 1];
+                if (s == 0.0) continue;
+                const double apk = A[p * ld + k], aqk = A[q * ld + k];
+                A[p * ld + k] = c * apk - s * aqk;
+                A[q * ld + k] = s * apk + c * aqk;
+            }
+            __syncthreads();
+        }
+    }
+    // eigenvalues, descending order (ties by index)
+    for (int i = threadIdx.x; i < K; i += blockDim.x) lam[i] = A[i * ld + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        int rank = 0;
+        const double li = lam[i];
+        for (int j = 0; j < K; ++j) {
+            const double lj = lam[j];
+            rank += (lj > li) || (lj == li && j < i);
+        }
+        perm[rank] = i;
+    }
+    __syncthreads();
+    __shared__ int s_m;
+    if (threadIdx.x == 0) {
+        const double l1 = lam[perm[0]];
+        int m = 0;
+        if (l1 > 0.0) {
+            int r = 0;
+            for (int i = 0; i < K; ++i) r += lam[perm[i]] > a.tau * l1;
+            double total = 0.0;
+            for (int i = 0; i < r; ++i) total += sqrt(lam[perm[i]]);
+            double cum = 0.0;
+            m = r;
+            for (int i = 0; i < r; ++i) {
+                cum += sqrt(lam[perm[i]]);
+                if (cum >= a.gamma * total) { m = i + 1; break; }
+            }
+            if (a.cap > 0) m = min(m, a.cap);
+            m = min(m, r);
+        }
+        s_m = m;
+        a.m[b] = m;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.maxK; i += blockDim.x) lam_out[i] = (i < K) ? lam[perm[i]] : 0.0;
+    const int m = s_m;
+    for (int e = threadIdx.x; e < K * m; e += blockDim.x) {
+        const int i = e / m, j = e - i * m;
+        const int src = perm[j];
+        Cb[(size_t)i * a.ldC + j] = V[i * ld + src] / sqrt(lam[src]);
+    }
+}
+
+cudaError_t launch_eig_pod(const EigArgs& a, cudaStream_t st) {
+    if (a.B <= 0) return cudaSuccess;
+    const int Kp = a.maxK + (a.maxK & 1);
+    const size_t smem = (size_t)2 * Kp * Kp * sizeof(double) + (size_t)2 * Kp * sizeof(double) +
+                        (size_t)Kp * sizeof(int) + 16;
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaFuncSetAttribute(eig_pod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    eig_pod_kernel<<<a.B, EIG_THREADS, smem, st>>>(a);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Cholesky G = L L^T (FP64) and X = L^{-T}, one CTA per matrix.
+__global__ void chol_inv_kernel(const double* G, int ldG, long long ldG_b, const int* mp, int maxm,
+                                double* X, int ldX, long long ldX_b, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    const int m = mp[b];
+    if (m <= 0) return;
+    double* L = reinterpret_cast<double*>(smem_raw);   // [maxm][maxm]
+    double* Li = L + (size_t)maxm * maxm;                // [maxm][maxm]
+    __shared__ int s_bad;
+    const double* Gb = G + (size_t)b * ldG_b;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e - i * m;
+        L[i * maxm + j] = (j <= i) ? Gb[(size_t)i * ldG + j] : 0.0;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        if (threadIdx.x == 0) {
+            double d = L[j * maxm + j];
+            for (int k = 0; k < j; ++k) d -= L[j * maxm + k] * L[j * maxm + k];
+            if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
+            L[j * maxm + j] = sqrt(d);
+        }
+        __syncthreads();
+        const double ljj = L[j * maxm + j];
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+            double s = L[i * maxm + j];
+            for (int k = 0; k < j; ++k) s -= L[i * maxm + k] * L[j * maxm + k];
+            L[i * maxm + j] = s / ljj;
+        }
+        __syncthreads();
+    }
+    // columns of L^{-1} by forward substitution
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        for (int i = 0; i < m; ++i) {
+            if (i < c) { Li[i * maxm + c] = 0.0; continue; }
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= L[i * maxm + k] * Li[k * maxm + c];
+            Li[i * maxm + c] = s / L[i * maxm + i];
+        }
+    }
+    __syncthreads();
+    double* Xb = X + (size_t)b * ldX_b;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e - i * m;
+        Xb[(size_t)i * ldX + j] = s_bad ? (i == j ? 1.0 : 0.0) : Li[j * maxm + i];
+    }
+    if (threadIdx.x == 0 && s_bad) record_error(err, DERR_BREAKDOWN);
+}
+
+cudaError_t launch_chol_inv(const double* G, int ldG, long long ldG_b, const int* m, int maxm,
+                            int B, double* X, int ldX, long long ldX_b, int* err,
+                            cudaStream_t st) {
+    if (B <= 0 || maxm <= 0) return cudaSuccess;
+    const size_t smem = (size_t)2 * maxm * maxm * sizeof(double);
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    chol_inv_kernel<<<B, 128, smem, st>>>(G, ldG, ldG_b, m, maxm, X, ldX, ldX_b, err);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+__global__ void assemble_cols_kernel(const void* const* bases, const int* const* cnt_ptrs, int nb,
+                                     long long Ng, int esize, const void** cols, int ld, int* K) {
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    int k = 0;
+    for (int j = 0; j < nb; ++j) {
+        const char* base = reinterpret_cast<const char*>(bases[(size_t)b * nb + j]);
+        const int* cp = cnt_ptrs[(size_t)b * nb + j];
+        const int c = (base && cp) ? *cp : 0;
+        for (int i = 0; i < c && k < ld; ++i) cols[(size_t)b * ld + k++] = base + (size_t)i * Ng * esize;
+    }
+    K[b] = k;
+}
+
+cudaError_t launch_assemble_cols(const void* const* bases, const int* const* cnt_ptrs, int nb, int B,
+                                 long long Ng, int esize, const void** cols, int ld, int* K,
+                                 cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    assemble_cols_kernel<<<B, 32, 0, st>>>(bases, cnt_ptrs, nb, Ng, esize, cols, ld, K);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+} // namespace pr

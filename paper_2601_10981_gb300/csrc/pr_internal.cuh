@@ -1,0 +1,292 @@
+// Internal declarations shared by the CUDA translation units of the parareal library.
+// Device utilities (bounded barriers, deterministic block reductions), kernel parameter
+// structs and the host-side launchers the context code calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/parareal.h"
+
+namespace pr {
+
+// ---------------------------------------------------------------------------------
+// Error codes recorded by kernels into a device int (first error wins).
+enum DevErr : int {
+    DERR_OK = 0,
+    DERR_NOT_CONVERGED = PR_ERR_NOT_CONVERGED,
+    DERR_BREAKDOWN = PR_ERR_BREAKDOWN,
+    DERR_TIMEOUT = PR_ERR_TIMEOUT,
+    DERR_NONFINITE = PR_ERR_NONFINITE,
+};
+
+extern long long g_launch_count;   // kernels launched by this library (host counter)
+
+// ---------------------------------------------------------------------------------
+// The FD operator of eq. (eq1): (L u)_i = sum_d b_d(i)(u_{i+e_d}-u_{i-e_d})/(2h)
+//                                        - eps sum_d (u_{i+e_d}-2u_i+u_{i-e_d})/h^2.
+// Velocity: b_x = tab[0][y] + tab[1][z], b_y = tab[2][x] + tab[3][z],
+//           b_z = tab[4][x] + tab[5][y]   (six 1-D tables of n doubles, device).
+struct Grid {
+    int n;
+    long long Ng;      // n^3
+    double h;
+    double eps;
+    const double* tab; // 6*n
+};
+
+enum TabIdx { TXY = 0, TXZ = 1, TYX = 2, TYZ = 3, TZX = 4, TZY = 5 };
+
+// ---------------------------------------------------------------------------------
+// Memory-model helpers (PTX acquire/release at gpu scope).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void record_error(int* err, int code) {
+    atomicCAS(err, 0, code);
+}
+
+// Barrier of `count` co-resident CTAs on bar[0] (arrivals) / bar[1] (generation).
+// Thread 0 arrives with release semantics and polls the generation with acquire
+// semantics at most `spin_limit` times; on time-out it records DERR_TIMEOUT and the
+// whole CTA gets `false` (the caller returns).  Every CTA of the group must call it the
+// same number of times.
+__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned count,
+                                              long long spin_limit, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(bar + 1);
+        unsigned arrived = atom_add_acq_rel_u32(bar, 1u);
+        if (arrived == count - 1) {
+            st_relaxed_u32(bar, 0u);
+            st_release_u32(bar + 1, gen + 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire_u32(bar + 1) == gen) {
+                if (spins >= spin_limit) {
+                    ok = 0;
+                    record_error(err, DERR_TIMEOUT);
+                    break;
+                }
+                ++spins;
+                __nanosleep(64);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Deterministic block sum of NQ doubles per thread; the result is valid in thread 0
+// (returned in-place in v[] of thread 0).  Fixed shuffle tree, then warp sums added in
+// warp order.  `red` must hold NQ * 32 doubles of shared memory.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[q * 32 + warp] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += red[q * 32 + w];
+            v[q] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Fine sweep (a batch of independent implicit-Euler runs, one per subinterval).
+struct FineArgs {
+    Grid g;
+    int S;              // fine steps
+    int dM, n_snap;     // snapshot stride / count (n_snap = 0: none)
+    double dt;          // fine step
+    const double* f;    // forcing [Ng] or nullptr
+    int B;              // subintervals in this launch
+    const double* u_in; // [B][Ng]
+    double* u_out;      // [B][Ng]
+    void* snap;         // [B][n_snap][Ng] of KT, or nullptr
+    void* ws;           // [numGroups][NVEC][Ng] of KT
+    double* ust;        // [numGroups][2][Ng]
+    double* part;       // [numGroups][2][4][n]
+    unsigned* bar;      // [numGroups][2]
+    int G;              // CTAs per group
+    int numGroups;
+    double tol;
+    int maxit;
+    long long spin_limit;
+    int* status;        // [B] per-subinterval error code
+    int* its_total;     // [B]
+    int* its_max;       // [B]
+    int* err;           // launch-wide error code
+};
+constexpr int FINE_NVEC = 8; // delta, r, rhat, p0, p1, v0, v1, t
+
+// Launch the persistent fine sweep.  Chooses numGroups = min(B, grid / G) and G from
+// the occupancy unless a.G > 0.  Returns the CUDA error of the launch.
+cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups,
+                        cudaStream_t st);
+// Largest number of co-resident CTAs of the fine kernel for this grid size.
+int fine_max_ctas(int n, bool fp32, int ctas_per_sm);
+int fine_block_threads(int n);
+
+cudaError_t launch_tables(const pr_flow& flow, int n, double L, double* tab,
+                          cudaStream_t st);
+// out[c] = L u[c] (transpose: L^T) for columns c < count[b] of each batch item b;
+// columns given as pointer arrays in_cols[b*ldcols + c], out_cols[...]; TI/TO = float
+// or double selected by the flags.
+cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols,
+                           void* const* out_cols, const int* count, int ldcols,
+                           int max_count, int B, bool in_f32, bool out_f32, bool transpose,
+                           cudaStream_t st);
+
+// ---------------------------------------------------------------------------------
+// Batched cross Gram  G[b] = A_b^T B_b  (A_b: KA[b] columns, B_b: KB[b] columns of Ng
+// points each, column pointer arrays), accumulated in FP64 (FP32 inputs: FP32 over
+// 32-point blocks, FP64 above).  sym: A_b == B_b and only the upper triangle is formed,
+// then mirrored.  Output G[b*ldG_b + i*ldG + j], i < KA, j < KB.  Chunk partials are
+// summed in a fixed order by the last CTA of each batch item (deterministic).
+struct GramArgs {
+    const void* const* colsA; // [B][ldcols]
+    const void* const* colsB;
+    const int* KA;            // [B] (device)
+    const int* KB;            // [B]
+    int ldcols;
+    long long Ng;
+    int B;
+    int maxKA, maxKB;
+    bool sym;
+    double* part;             // [B][chunks][maxKA*maxKB]
+    unsigned* counter;        // [B], zero on entry, left zero on exit
+    double* G;                // [B][ldG_b]
+    int ldG;                  // row stride
+    long long ldG_b;          // batch stride
+    double scaleB;            // unused (1.0)
+};
+int gram_chunks(long long Ng);
+size_t gram_part_doubles(long long Ng, int B, int maxKA, int maxKB);
+cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t st);
+
+// Tall-skinny multiply: Out_b[:, j] = sum_i In_b[:, i] C_b[i][j], i < KIN[b], j < KOUT[b];
+// inputs as column pointers, output contiguous columns out + b*ld_out_b + j*Ng.
+struct TsmmArgs {
+    const void* const* colsIn; // [B][ldcols]
+    const int* KIN;            // [B]
+    const int* KOUT;           // [B]
+    int ldcols;
+    const double* C;           // [B][ldC_b]: C[i*ldC + j]
+    int ldC;
+    long long ldC_b;
+    void* out;
+    long long ld_out_b;        // elements between batch items
+    long long Ng;
+    int B;
+    int maxKIN, maxKOUT;
+};
+cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream_t st);
+
+// Batched symmetric eigenproblem (cyclic Jacobi, FP64) + POD selection (Algorithm 1):
+// G[b] (K[b] x K[b], row stride ldG, batch stride ldG_b) -> lam[b][0..K) descending,
+// m[b] (criterion with gamma, tau, cap), C[b] = Y[:, :m] diag(lam^-1/2) stored
+// C[b*ldC_b + i*ldC + j].
+struct EigArgs {
+    const double* G; int ldG; long long ldG_b;
+    const int* K;
+    int maxK;
+    int B;
+    double gamma, tau;
+    int cap;
+    double* lam;               // [B][maxK]
+    int* m;                    // [B]
+    double* C; int ldC; long long ldC_b;
+    int* err;
+};
+cudaError_t launch_eig_pod(const EigArgs& a, cudaStream_t st);
+
+// Batched Cholesky of Gram matrices and X = L^{-T}: G[b] (m[b] x m[b]) -> X[b].
+cudaError_t launch_chol_inv(const double* G, int ldG, long long ldG_b, const int* m, int maxm,
+                            int B, double* X, int ldX, long long ldX_b, int* err,
+                            cudaStream_t st);
+
+// Fill column pointer arrays: for batch b, cols[b*ld + ...] = concatenation of nb blocks
+// (block j: base pointer bases[b*nb + j], count cnt[b*nb + j] read on the device,
+// column stride Ng elements of esize bytes); K[b] = total.
+cudaError_t launch_assemble_cols(const void* const* bases, const int* const* cnt_ptrs,
+                                 int nb, int B, long long Ng, int esize, const void** cols,
+                                 int ld, int* K, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------
+// Coarse sweep pieces (one subinterval, sequential in n).
+struct CoarseArgs {
+    Grid g;
+    const void* R;          // m columns (KT), contiguous, stride Ng
+    const int* m_ptr;       // device int: m
+    int maxm;
+    const double* U;        // U^k_n
+    const double* Up;       // U^{k-1}_n
+    const double* F;        // F_n
+    double* out;            // U^k_{n+1}
+    const double* Mr;       // m x m (ld maxm): R^T R
+    const double* Lr;       // m x m (ld maxm): R^T L R
+    double dT;
+    int Lc;
+    double aug_tol;
+    // scratch
+    double* d;              // [Ng]
+    double* Ld;             // [Ng]
+    double* Ltd;            // [Ng]
+    double* dots;           // small result vectors (see coarse.cu)
+    double* part;           // chunk partials
+    unsigned* counter;      // [8] zero
+    double* coef;           // [maxm+1]
+    int* err;
+};
+cudaError_t launch_coarse_update(const CoarseArgs& a, bool r_f32, cudaStream_t st);
+size_t coarse_part_doubles(long long Ng, int maxm);
+
+// Iteration 0: beta_n = reduced coordinates of U^0_n, n = 1..N (G_0 in V0), from
+// M0 = V0^T V0, L0 = V0^T L V0, p0 = V0^T u_hat0, q0 = V0^T f.
+cudaError_t launch_g0(const double* M0, const double* L0, const double* p0, const double* q0,
+                      const int* m0, int ld, int N, int Lc, double dT, double* beta, int ldb,
+                      int* err, cudaStream_t st);
+
+// Convergence: for n < cnt: out[n*4 + 0..3] = ||a_n-b_n||^2, ||a_n||^2, ||a_n-r_n||^2,
+// ||r_n||^2 (r may be null: last two zero).
+cudaError_t launch_norms(const double* a, const double* b, const double* r, long long Ng,
+                         int cnt, double* part, unsigned* counter, double* out,
+                         cudaStream_t st);
+size_t norms_part_doubles(long long Ng, int cnt);
+
+// Scan for NaN/Inf: sets *flag = 1 if any of the first `count` doubles is not finite.
+cudaError_t launch_nonfinite(const double* x, long long count, int* flag, cudaStream_t st);
+
+} // namespace pr
