@@ -44,12 +44,14 @@ enum pr_flow_kind {
     PR_FLOW_CONST = 2       /* (b[0], b[1], b[2])                                        */
 };
 
-/* Arithmetic of the fine Krylov solves, snapshots and POD bases.  Interface states U^k_n,
- * fine end states, reduced (Galerkin) systems and eigenproblems are FP64 in both. */
+/* Arithmetic of the fine Krylov solves.  Interface states U^k_n, fine states and end
+ * states, snapshots, POD bases, Grams, eigenproblems and reduced systems are FP64 in both
+ * modes: the augmentation of eq. (eqaug) resolves U^k_n against the POD space to
+ * ||d~||/||U|| ~ 1e-9, which a basis rounded to FP32 cannot. */
 enum pr_precision {
     PR_FP64 = 0,            /* everything FP64                                           */
-    PR_FP32 = 1             /* FP64 state + FP32 increment solve ("delta form"); FP32
-                               snapshots and bases; Gram/projection accumulate in FP64  */
+    PR_FP32 = 1             /* fine sweep: FP64 state, FP32 BiCGStab for the increment
+                               ("delta form"), FP64 residual of the state               */
 };
 
 typedef struct pr_grid {
@@ -77,7 +79,7 @@ typedef struct pr_opts {
                                each 0 or 1; default 1, 1                                  */
     double pod_tol3;        /* gamma3 = 1 - pod_tol3; 0: derive = pod_tol * 4e-3          */
     double rank_tau;        /* eigenvalues <= rank_tau*lambda_1 count as zero (Alg. 1);
-                               0: derive = 1e-13 (FP64) or 1e-6 (FP32)                   */
+                               0: derive = 1e-13                                         */
     int precision;          /* enum pr_precision; default PR_FP64                        */
     double lin_tol;         /* BiCGStab stops at ||r|| <= lin_tol ||rhs||;
                                0: derive = 1e-14 (FP64) or 1e-9 (FP32)                   */
@@ -190,10 +192,10 @@ pr_status pr_set_interfaces(pr_ctx* ctx, const double* host_U, int k_done);
 pr_status pr_rewind(pr_ctx* ctx);
 
 /* Read back, to host memory, what the latest phases produced for subinterval n:
- * F_n of the last fine sweep (n^3 doubles); its snapshots W^k_{n,0} (n_s x n^3 in the
- * context precision; slot 0 holds the Case-I window after pr_iteration0); and a basis:
+ * F_n of the last fine sweep (n^3 doubles); its snapshots W^k_{n,0} (n_s x n^3 doubles;
+ * slot 0 holds the Case-I window after pr_iteration0); and a basis:
  * level 0 = V0 (n ignored), 1 = R^k_{n,0}, 2 = R^k_n, m_out receives its dimension and
- * host_out (may be NULL) m x n^3 values in the context precision.  Synchronise. */
+ * host_out (may be NULL) m x n^3 doubles.  Synchronise. */
 pr_status pr_get_fine_end(pr_ctx* ctx, int n, double* host_out);
 pr_status pr_get_snapshots(pr_ctx* ctx, int n, void* host_out);
 pr_status pr_get_basis(pr_ctx* ctx, int level, int n, void* host_out, int* m_out);
@@ -223,21 +225,24 @@ pr_status pr_op_apply_L(pr_ctx* ctx, const double* d_in, double* d_out, int coun
 
 /* Fine propagator on B independent states: d_out[b] = F(t0, t0 + steps*dt, d_in[b]) with
  * snapshots of the states at steps 0, dM, ... (n_snap of them; d_snap may be NULL when
- * n_snap = 0).  d_in, d_out: B x n^3 doubles.  d_snap: B x n_snap x n^3 in the context
- * precision (double for PR_FP64, float for PR_FP32).  1 <= B <= n_sub. */
+ * n_snap = 0).  d_in, d_out: B x n^3 doubles.  d_snap: B x n_snap x n^3 doubles (snapshots
+ * are FP64 in both precision modes).  1 <= B <= n_sub.  The forcing is
+ * the one given to pr_set_initial (zero before the first call). */
 pr_status pr_op_fine(pr_ctx* ctx, const double* d_in, double* d_out, void* d_snap, int B,
                      double t0, int steps, int dM, int n_snap);
 
 /* POD_Mode (Algorithm 1) with CholQR2 re-orthonormalisation on B snapshot matrices:
- * d_W: B x n_cols x n^3, d_R: B x m_max x n^3, both in the context precision; gamma in
- * (0,1]; cap 0 = none; m_out: host, B ints.  n_cols <= the largest window the context
- * was built for (max(n_s, n_s0, (m_l+1+p) * level-1 cap)); B <= n_sub. */
-pr_status pr_op_pod(pr_ctx* ctx, const void* d_W, int n_cols, int B, double gamma, int cap,
-                    void* d_R, int* m_out);
+ * d_W: B x n_cols x n^3 doubles (w_f32 = 0; the level-1 path, numerical zero 1e-13) or
+ * floats (w_f32 = 1; Gram accumulated over 32-point blocks in FP32, numerical zero 1e-6);
+ * d_R: B x m_max x n^3 doubles, m_max = min(cap, n_cols) or
+ * n_cols when cap = 0; gamma in (0,1]; m_out: host, B ints.  n_cols <= the largest window
+ * the context was built for (max(n_s, n_s0, (m_l+1+p) * level-1 cap)); B <= n_sub. */
+pr_status pr_op_pod(pr_ctx* ctx, const void* d_W, int w_f32, int n_cols, int B, double gamma,
+                    int cap, void* d_R, int* m_out);
 
 /* One coarse update of eq. (formula4) on subinterval [t, t+DeltaT] with the augmented
- * space [R, d(U)]:  d_out = G(U) + F - G(P U_prev).  d_R: m x n^3 in the context
- * precision (orthonormal columns), d_U, d_Uprev, d_F, d_out: n^3 doubles. */
+ * space [R, d(U)]:  d_out = G(U) + F - G(P U_prev).  d_R: m x n^3 doubles (orthonormal
+ * columns), d_U, d_Uprev, d_F, d_out: n^3 doubles. */
 pr_status pr_op_coarse_update(pr_ctx* ctx, const void* d_R, int m, const double* d_U,
                               const double* d_Uprev, const double* d_F, double* d_out);
 

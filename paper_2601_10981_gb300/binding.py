@@ -88,7 +88,7 @@ _SIGS = {
     "pr_get_basis": (C.c_int, [_P, C.c_int, C.c_int, _P, _I]),
     "pr_op_apply_L": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "pr_op_fine": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int]),
-    "pr_op_pod": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_double, C.c_int, _P, _I]),
+    "pr_op_pod": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _P, _I]),
     "pr_op_coarse_update": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, _P]),
 }
 
@@ -293,19 +293,15 @@ class Parareal:
         self._check(self._lib.pr_get_fine_end(self.ctx, n, _dptr(out)))
         return out
 
-    @property
-    def kt(self):
-        return np.float32 if self.fp32 else np.float64
-
     def snapshots(self, n: int) -> np.ndarray:
-        out = np.empty((self.n_s, self.Ng), dtype=self.kt)
+        out = np.empty((self.n_s, self.Ng), dtype=np.float64)
         self._check(self._lib.pr_get_snapshots(self.ctx, n, out.ctypes.data_as(C.c_void_p)))
         return out
 
     def basis(self, level: int, n: int = 0) -> np.ndarray:
         m = C.c_int()
         self._check(self._lib.pr_get_basis(self.ctx, level, n, None, C.byref(m)))
-        out = np.empty((m.value, self.Ng), dtype=self.kt)
+        out = np.empty((m.value, self.Ng), dtype=np.float64)
         if m.value:
             self._check(self._lib.pr_get_basis(self.ctx, level, n, out.ctypes.data_as(C.c_void_p),
                                                C.byref(m)))
@@ -322,24 +318,27 @@ class Parareal:
         self._check(self._lib.pr_op_apply_L(self.ctx, _tptr(u), _tptr(out), count, int(transpose)))
         return out
 
-    def op_fine(self, u, steps: int, dM: int = 1, n_snap: int = 0, fp32: bool = False):
+    def op_fine(self, u, steps: int, dM: int = 1, n_snap: int = 0):
         B = u.shape[0]
         out = self.torch.empty_like(u)
         snap = None
         if n_snap > 0:
-            dt = self.torch.float32 if fp32 else self.torch.float64
-            snap = self.torch.zeros((B, n_snap) + tuple(u.shape[1:]), dtype=dt, device=u.device)
+            snap = self.torch.zeros((B, n_snap) + tuple(u.shape[1:]), dtype=self.torch.float64,
+                                    device=u.device)
         self._check(self._lib.pr_op_fine(self.ctx, _tptr(u), _tptr(out), _tptr(snap), B, 0.0,
                                          steps, dM, n_snap))
         return out, snap
 
     def op_pod(self, W, gamma: float, cap: int = 0):
-        """W: (B, n_cols, n, n, n) tensor in the context precision."""
+        """W: (B, n_cols, n, n, n) float64 or float32 tensor; returns the (float64) bases and
+        the POD dimensions."""
         B, ncol = W.shape[0], W.shape[1]
         mmax = min(cap, ncol) if cap > 0 else ncol
-        R = self.torch.zeros((B, mmax) + tuple(W.shape[2:]), dtype=W.dtype, device=W.device)
+        R = self.torch.zeros((B, mmax) + tuple(W.shape[2:]), dtype=self.torch.float64,
+                             device=W.device)
         m = np.zeros(B, dtype=np.int32)
-        self._check(self._lib.pr_op_pod(self.ctx, _tptr(W), ncol, B, gamma, cap, _tptr(R),
+        w32 = 1 if W.dtype == self.torch.float32 else 0
+        self._check(self._lib.pr_op_pod(self.ctx, _tptr(W), w32, ncol, B, gamma, cap, _tptr(R),
                                         m.ctypes.data_as(_I)))
         return R, m
 

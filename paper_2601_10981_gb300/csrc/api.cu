@@ -54,7 +54,7 @@ struct pr_ctx {
     // derived
     double DeltaT = 0, dt = 0, T0 = 0, dT = 0;
     int S = 0, S0 = 0, Lc = 0, dM = 0, ns = 0, ns0 = 0, nsmax = 0;
-    double gamma1 = 0, gamma3 = 0, tau = 0, lin_tol = 0;
+    double gamma1 = 0, gamma3 = 0, tau = 0, tau1 = 1e-13, lin_tol = 0;
     bool fp32 = false;
     int esz = 8;
     int mcap0 = 0, mcap1 = 0, w2 = 0, mcap2 = 0, mscr = 0, maxK = 0, ldcols = 0;
@@ -165,7 +165,7 @@ size_t plan(pr_ctx* c, char* base) {
     c->Ubuf[0] = b.take<double>((size_t)(N + 1) * Ng);
     c->Ubuf[1] = b.take<double>((size_t)(N + 1) * Ng);
     c->Fend = b.take<double>((size_t)N * Ng);
-    c->snap = b.take<char>((size_t)N * c->nsmax * Ng * c->esz);
+    c->snap = b.take<char>((size_t)N * c->nsmax * Ng * sizeof(double));
     for (int i = 0; i < 2; ++i) {
         c->R1[i] = b.take<char>((size_t)N * c->mcap1 * Ng * c->esz);
         c->m1[i] = b.take<int>(N);
@@ -200,7 +200,8 @@ size_t plan(pr_ctx* c, char* base) {
     c->KB = b.take<int>(N + 1);
     c->ones = b.take<int>(N + 1);
     c->cnst = b.take<int>(8);
-    c->fws_bytes = std::max((size_t)c->groups_max * FINE_NVEC * Ng * c->esz,
+    const size_t kesz = c->fp32 ? sizeof(float) : sizeof(double);  // Krylov vectors
+    c->fws_bytes = std::max((size_t)c->groups_max * FINE_NVEC * Ng * kesz,
                             (size_t)FINE_NVEC * Ng * sizeof(double));
     c->fws = b.take<char>(c->fws_bytes);
     c->ust = b.take<double>((size_t)c->groups_max * 2 * Ng);
@@ -237,6 +238,12 @@ pr_status init_ws(pr_ctx* c) {
     cudaStream_t st = c->st;
     PR_CUDA(cudaMemsetAsync(c->counters, 0, sizeof(unsigned) * ((size_t)c->N + 64), st));
     PR_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), st));
+    PR_CUDA(cudaMemsetAsync(c->fstatus, 0, sizeof(int) * ((size_t)c->N + 1), st));
+    PR_CUDA(cudaMemsetAsync(c->fits, 0, sizeof(int) * ((size_t)c->N + 1), st));
+    PR_CUDA(cudaMemsetAsync(c->fitsmax, 0, sizeof(int) * ((size_t)c->N + 1), st));
+    PR_CUDA(cudaMemsetAsync(c->m1[0], 0, sizeof(int) * c->N, st));
+    PR_CUDA(cudaMemsetAsync(c->m1[1], 0, sizeof(int) * c->N, st));
+    PR_CUDA(cudaMemsetAsync(c->m2, 0, sizeof(int) * ((size_t)c->N + 1), st));
     PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, st));
     std::vector<int> ones(c->N + 1, 1);
     PR_CUDA(cudaMemcpy(c->ones, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice));
@@ -271,35 +278,35 @@ pr_status ensure_ws(pr_ctx* c) {
 // and expanded on the device into column pointer arrays.
 pr_status upload_blocks(pr_ctx* c, const std::vector<const void*>& bases,
                         const std::vector<const int*>& cnts, int nb, int B, const void** cols,
-                        int* K) {
+                        int* K, int esize) {
     PR_CUDA(cudaMemcpyAsync(c->bases, bases.data(), sizeof(void*) * bases.size(),
                             cudaMemcpyHostToDevice, c->st));
     PR_CUDA(cudaMemcpyAsync(c->cntp, cnts.data(), sizeof(int*) * cnts.size(),
                             cudaMemcpyHostToDevice, c->st));
     // pageable async copies are staged before returning and stream-ordered, so the host
     // vectors may go out of scope and the next upload cannot overtake this expansion
-    PR_CUDA(launch_assemble_cols(c->bases, c->cntp, nb, B, c->Ng, c->esz, cols, c->ldcols, K, c->st));
+    PR_CUDA(launch_assemble_cols(c->bases, c->cntp, nb, B, c->Ng, esize, cols, c->ldcols, K, c->st));
     return PR_OK;
 }
 
 // Column pointer arrays for B contiguous blocks base + b*bstride (count cnt[b] or the
 // same device int for all when cnt_stride = 0).
 pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const int* cnt, int cnt_stride,
-                      int B, const void** cols, int* K) {
+                      int B, const void** cols, int* K, int esize) {
     std::vector<const void*> bs(B);
     std::vector<const int*> cs(B);
     for (int b = 0; b < B; ++b) {
         bs[b] = base + (size_t)b * bstride_bytes;
         cs[b] = cnt + (size_t)b * cnt_stride;
     }
-    return upload_blocks(c, bs, cs, 1, B, cols, K);
+    return upload_blocks(c, bs, cs, 1, B, cols, K, esize);
 }
 
 // POD_Mode + CholQR2 on B batch items whose snapshot columns are already in
 // (c->colsA, c->KA).  Result: dest + b*dest_bstride (columns of Ng), dims m_dest[b].
-pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, int cap, int mmax, char* dest,
-                       size_t dest_bstride_elems, int* m_dest) {
-    const bool f32 = c->fp32;
+pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, bool in_f32, int cap,
+                       int mmax, char* dest, size_t dest_bstride_elems, int* m_dest) {
+    const bool f32 = false;  // bases and their Grams are FP64
     cudaStream_t st = c->st;
     // Gram W^T W
     GramArgs ga{};
@@ -318,7 +325,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, int cap, int mm
     ga.G = c->gout;
     ga.ldG = maxK;
     ga.ldG_b = (long long)maxK * maxK;
-    PR_CUDA(launch_gram(ga, f32, f32, st));
+    PR_CUDA(launch_gram(ga, in_f32, in_f32, st));
     // eigenpairs + dimension + C = Y_m Lambda_m^{-1/2}
     EigArgs ea{};
     ea.G = c->gout;
@@ -328,7 +335,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, int cap, int mm
     ea.maxK = maxK;
     ea.B = B;
     ea.gamma = gamma;
-    ea.tau = c->tau;
+    ea.tau = tau;
     ea.cap = cap > 0 ? std::min(cap, mmax) : mmax;
     ea.lam = c->lam;
     ea.m = m_dest;
@@ -352,11 +359,11 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, int cap, int mm
     ta.B = B;
     ta.maxKIN = maxK;
     ta.maxKOUT = mmax;
-    PR_CUDA(launch_tsmm(ta, f32, f32, st));
+    PR_CUDA(launch_tsmm(ta, in_f32, f32, st));
     // CholQR twice: scr[0] -> scr[1] -> dest
     for (int pass = 0; pass < 2; ++pass) {
         char* src = c->scr[pass];
-        pr_status s = cols_contig(c, src, (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB);
+        pr_status s = cols_contig(c, src, (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB, c->esz);
         if (s != PR_OK) return s;
         GramArgs gb = ga;
         gb.colsA = c->colsB;
@@ -394,10 +401,10 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, int cap, int mm
 // into Mo/Lo + b*mmax*mmax (ld mmax).
 pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B, int mmax, double* Mo,
                    double* Lo) {
-    const bool f32 = c->fp32;
-    pr_status s = cols_contig(c, R, bstride_elems * c->esz, m, 1, B, c->colsA, c->KA);
+    const bool f32 = false;
+    pr_status s = cols_contig(c, R, bstride_elems * c->esz, m, 1, B, c->colsA, c->KA, c->esz);
     if (s != PR_OK) return s;
-    s = cols_contig(c, c->LR, (size_t)mmax * c->Ng * c->esz, m, 1, B, c->colsB, c->KB);
+    s = cols_contig(c, c->LR, (size_t)mmax * c->Ng * c->esz, m, 1, B, c->colsB, c->KB, c->esz);
     if (s != PR_OK) return s;
     Grid g = grid_of(c);
     PR_CUDA(launch_apply_L(g, c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, f32, f32,
@@ -553,7 +560,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     c->pod_tol = pod_tol;
     c->o = o;
     c->fp32 = o.precision == PR_FP32;
-    c->esz = c->fp32 ? 4 : 8;
+    c->esz = 8;  // POD bases are FP64 in both modes (the augmentation needs them exact)
     c->DeltaT = T / n_sub;
     c->S = steps_for(c->DeltaT, dt_fine);
     c->dt = c->DeltaT / c->S;
@@ -577,7 +584,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     c->nsmax = std::max(c->ns, c->ns0);
     c->gamma1 = 1.0 - pod_tol;
     c->gamma3 = 1.0 - (o.pod_tol3 > 0 ? o.pod_tol3 : pod_tol * 4e-3);
-    c->tau = o.rank_tau > 0 ? o.rank_tau : (c->fp32 ? 1e-6 : 1e-13);
+    c->tau = o.rank_tau > 0 ? o.rank_tau : 1e-13;
     c->lin_tol = o.lin_tol > 0 ? o.lin_tol : (c->fp32 ? 1e-9 : 1e-14);
     const int cap = o.m_cap;
     c->mcap0 = cap > 0 ? std::min(cap, c->ns0) : c->ns0;
@@ -684,9 +691,10 @@ pr_status pr_iteration0(pr_ctx* c) {
     s = run_fine(c, c->u0, U, c->snap, 1, c->S0, c->ns0, 0, false);
     if (s != PR_OK) return s;
     // V0 = POD_Mode(W, gamma1)
-    s = cols_contig(c, c->snap, 0, c->cnst + 1, 0, 1, c->colsA, c->KA);
+    s = cols_contig(c, c->snap, 0, c->cnst + 1, 0, 1, c->colsA, c->KA, sizeof(double));
     if (s != PR_OK) return s;
-    s = pod_pipeline(c, 1, c->ns0, c->gamma1, c->o.m_cap, c->mcap0, c->V0, (size_t)c->mcap0 * Ng, c->m0);
+    s = pod_pipeline(c, 1, c->ns0, c->gamma1, c->tau1, false, c->o.m_cap, c->mcap0, c->V0,
+                     (size_t)c->mcap0 * Ng, c->m0);
     if (s != PR_OK) return s;
     // Galerkin matrices of V0 and projections of u_hat0, f
     s = galerkin(c, c->V0, (size_t)c->mcap0 * Ng, c->m0, 1, c->mcap0, c->M0, c->L0);
@@ -711,17 +719,17 @@ pr_status pr_iteration0(pr_ctx* c) {
         ga.G = c->p0;
         ga.ldG = 1;
         ga.ldG_b = 0;
-        PR_CUDA(launch_gram(ga, c->fp32, false, c->st));
+        PR_CUDA(launch_gram(ga, false, false, c->st));
         if (c->has_f) {
             ga.colsB = c->colsB + 1;
             ga.G = c->q0;
-            PR_CUDA(launch_gram(ga, c->fp32, false, c->st));
+            PR_CUDA(launch_gram(ga, false, false, c->st));
         }
     }
     PR_CUDA(launch_g0(c->M0, c->L0, c->p0, c->has_f ? c->q0 : nullptr, c->m0, c->mcap0, c->N, c->Lc, c->dT,
                       c->beta, c->mcap0, c->derr, c->st));
     // U^0_{n+1} = V0 beta_n
-    s = cols_contig(c, c->V0, 0, c->m0, 0, c->N, c->colsA, c->KA);
+    s = cols_contig(c, c->V0, 0, c->m0, 0, c->N, c->colsA, c->KA, c->esz);
     if (s != PR_OK) return s;
     TsmmArgs ta{};
     ta.colsIn = c->colsA;
@@ -737,7 +745,7 @@ pr_status pr_iteration0(pr_ctx* c) {
     ta.B = c->N;
     ta.maxKIN = c->mcap0;
     ta.maxKOUT = 1;
-    PR_CUDA(launch_tsmm(ta, c->fp32, false, c->st));
+    PR_CUDA(launch_tsmm(ta, false, false, c->st));
     c->r1cur = 0;
     c->k_done = 0;
     c->phase = 0;
@@ -769,10 +777,11 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
     const int nw = 1 - c->r1cur;
     const int B1 = N - k + 1;
     {
-        s = cols_contig(c, c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, (size_t)c->ns * Ng * c->esz,
-                        c->cnst + 0, 0, B1, c->colsA, c->KA);
+        s = cols_contig(c, c->snap + (size_t)(k - 1) * c->ns * Ng * sizeof(double),
+                        (size_t)c->ns * Ng * sizeof(double), c->cnst + 0, 0, B1, c->colsA, c->KA,
+                        sizeof(double));
         if (s != PR_OK) return s;
-        s = pod_pipeline(c, B1, c->ns, c->gamma1, c->o.m_cap, c->mcap1,
+        s = pod_pipeline(c, B1, c->ns, c->gamma1, c->tau1, false, c->o.m_cap, c->mcap1,
                          c->R1[nw] + (size_t)(k - 1) * c->mcap1 * Ng * c->esz, (size_t)c->mcap1 * Ng,
                          c->m1[nw] + (k - 1));
         if (s != PR_OK) return s;
@@ -808,9 +817,9 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
                 cs.push_back(nullptr);
             }
         }
-        s = upload_blocks(c, bs, cs, nb, B2, c->colsA, c->KA);
+        s = upload_blocks(c, bs, cs, nb, B2, c->colsA, c->KA, c->esz);
         if (s != PR_OK) return s;
-        s = pod_pipeline(c, B2, c->w2, c->gamma3, c->o.m_cap, c->mcap2,
+        s = pod_pipeline(c, B2, c->w2, c->gamma3, c->tau, false, c->o.m_cap, c->mcap2,
                          c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k);
         if (s != PR_OK) return s;
         s = galerkin(c, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k, B2,
@@ -859,7 +868,7 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
         a.out = Unew + (size_t)(n + 1) * Ng;
         a.Mr = c->Mr + (size_t)n * c->mcap2 * c->mcap2;
         a.Lr = c->Lr + (size_t)n * c->mcap2 * c->mcap2;
-        PR_CUDA(launch_coarse_update(a, c->fp32, c->st));
+        PR_CUDA(launch_coarse_update(a, false, c->st));
     }
     c->cur = 1 - c->cur;
     c->k_done = k;
@@ -1107,7 +1116,7 @@ pr_status pr_get_fine_end(pr_ctx* c, int n, double* out) {
 pr_status pr_get_snapshots(pr_ctx* c, int n, void* out) {
     if (!c || !out || n < 0 || n >= c->N) return PR_ERR_INVALID_ARG;
     if (!c->ws_ready) return fail(c, PR_ERR_STATE, "no workspace");
-    const size_t per = (size_t)c->ns * c->Ng * c->esz;
+    const size_t per = (size_t)c->ns * c->Ng * sizeof(double);
     PR_CUDA(cudaMemcpyAsync(out, c->snap + (size_t)n * per, per, cudaMemcpyDeviceToHost, c->st));
     PR_CUDA(cudaStreamSynchronize(c->st));
     return PR_OK;
@@ -1171,8 +1180,8 @@ pr_status pr_op_fine(pr_ctx* c, const double* d_in, double* d_out, void* d_snap,
     return pr_sync(c);
 }
 
-pr_status pr_op_pod(pr_ctx* c, const void* d_W, int n_cols, int B, double gamma, int cap, void* d_R,
-                    int* m_out) {
+pr_status pr_op_pod(pr_ctx* c, const void* d_W, int w_f32, int n_cols, int B, double gamma, int cap,
+                    void* d_R, int* m_out) {
     if (!c || !d_W || !d_R || !m_out || B < 1 || B > c->N || n_cols < 1) return PR_ERR_INVALID_ARG;
     if (n_cols > c->maxK || !(gamma > 0 && gamma <= 1)) return PR_ERR_INVALID_ARG;
     const int mmax = cap > 0 ? std::min(cap, n_cols) : n_cols;
@@ -1181,9 +1190,11 @@ pr_status pr_op_pod(pr_ctx* c, const void* d_W, int n_cols, int B, double gamma,
     if (s != PR_OK) return s;
     int nc = n_cols;
     PR_CUDA(cudaMemcpy(c->cnst + 2, &nc, sizeof(int), cudaMemcpyHostToDevice));
-    s = cols_contig(c, (const char*)d_W, (size_t)n_cols * c->Ng * c->esz, c->cnst + 2, 0, B, c->colsA, c->KA);
+    const int wes = w_f32 ? 4 : 8;
+    s = cols_contig(c, (const char*)d_W, (size_t)n_cols * c->Ng * wes, c->cnst + 2, 0, B, c->colsA, c->KA, wes);
     if (s != PR_OK) return s;
-    s = pod_pipeline(c, B, n_cols, gamma, cap, mmax, (char*)d_R, (size_t)mmax * c->Ng, c->mop);
+    s = pod_pipeline(c, B, n_cols, gamma, w_f32 ? 1e-6 : c->tau1, w_f32 != 0, cap, mmax, (char*)d_R,
+                     (size_t)mmax * c->Ng, c->mop);
     if (s != PR_OK) return s;
     PR_CUDA(cudaMemcpyAsync(m_out, c->mop, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st));
     return pr_sync(c);
@@ -1211,7 +1222,7 @@ pr_status pr_op_coarse_update(pr_ctx* c, const void* d_R, int m, const double* d
     a.out = d_out;
     a.Mr = Mr;
     a.Lr = Lr;
-    PR_CUDA(launch_coarse_update(a, c->fp32, c->st));
+    PR_CUDA(launch_coarse_update(a, false, c->st));
     return pr_sync(c);
 }
 

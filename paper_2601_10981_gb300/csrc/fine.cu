@@ -15,6 +15,8 @@
 // which generates the same Krylov iterates as BiCGStab on the paper's system started
 // from u_{j-1}.  The state u stays FP64; delta and the Krylov vectors are KT (double in
 // the FP64 mode, float in the FP32 mode).  The residual of the state is formed in FP64.
+// Snapshots are written in FP64 in both modes: the POD criterion keeps modes down to
+// lambda/lambda_1 ~ 1e-12, which FP32-rounded snapshots cannot resolve.
 // Stopping rule: ||r|| <= tol ||u_{j-1} + dt f||.
 //
 // BiCGStab phases (van der Vorst 1992), each followed by a group barrier:
@@ -121,6 +123,14 @@ cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols, void* cons
 
 // ------------------------------------------------------------------------------------
 // Fine sweep kernel.
+//
+// Ownership: the n^3 points of a subinterval are cut into NY x NZ tiles of TY rows (y) by
+// a slab of planes (z); CTA q of a group owns a contiguous range of tiles.  Stencil
+// phases march a tile plane by plane through a 3-plane shared-memory ring: the operand
+// of the stencil (u, p or s) is computed once per plane, with one halo row on each side
+// in y, and the 6 neighbours of a point come from the ring (x +- 1 wraps inside the row,
+// z +- 1 from the adjacent slots).  Global traffic per point and phase is one load per
+// input vector (plus the 2/TY halo rows and 2/slab halo planes) and one store per output.
 
 // Per-thread partial sums: KT = float accumulates 16 points in float, then in double.
 template <typename KT, int NQ>
@@ -143,26 +153,6 @@ struct Acc {
     }
 };
 
-struct Nbr {
-    long long c, xp, xm, yp, ym, zp, zm;
-    int x, y, z;
-};
-
-__device__ __forceinline__ Nbr neighbours(int x, int y, int z, int n, long long n2) {
-    Nbr o;
-    o.x = x; o.y = y; o.z = z;
-    const long long row = (long long)z * n2 + (long long)y * n;
-    o.c = row + x;
-    o.xp = row + (x + 1 == n ? 0 : x + 1);
-    o.xm = row + (x == 0 ? n - 1 : x - 1);
-    o.yp = (long long)z * n2 + (long long)(y + 1 == n ? 0 : y + 1) * n + x;
-    o.ym = (long long)z * n2 + (long long)(y == 0 ? n - 1 : y - 1) * n + x;
-    o.zp = (long long)(z + 1 == n ? 0 : z + 1) * n2 + (long long)y * n + x;
-    o.zm = (long long)(z == 0 ? n - 1 : z - 1) * n2 + (long long)y * n + x;
-    return o;
-}
-
-template <typename KT>
 struct FineShared {
     double red[4 * 32];
     double sums[4];
@@ -185,27 +175,50 @@ __device__ __forceinline__ void group_sums(const double* part, int grid, int g0,
     __syncthreads();
 }
 
-template <typename KT>
-__global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
+struct TileGeom {
+    int n, TY, NY, NZ;
+    __device__ __forceinline__ void tile(int t, int& y0, int& zlo, int& zhi) const {
+        const int yb = t % NY, zs = t / NY;
+        y0 = yb * TY;
+        zlo = zs * n / NZ;
+        zhi = (zs + 1) * n / NZ;
+    }
+};
+
+// Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
+template <typename KT> struct RawSetup { double u; KT d; };
+template <typename KT> struct RawP { KT r, p, v; };
+template <typename KT> struct RawS { KT r, v; };
+
+// KF: ring rows each thread fills per plane (ceil((TY+2)/rows_pass)); KS: owned rows per
+// thread per plane (TY/rows_pass).  Both compile-time so the prefetch lives in registers.
+template <typename KT, int KF, int KS>
+__global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ FineShared<KT> sh;
+    __shared__ FineShared sh;
 
     const int G = a.G;
     const int g = blockIdx.x / G;
     const int q = blockIdx.x % G;
     const int grid = gridDim.x;
     const int n = a.g.n;
-    const long long n2 = (long long)n * n;
+    const int n2 = n * n;
     const long long Ng = a.g.Ng;
     const int rows_pass = blockDim.x / n;
     const int tx = threadIdx.x % n;
     const int ty = threadIdx.x / n;
-    const long long nrows = n2;
-    const long long r_lo = nrows * q / G, r_hi = nrows * (q + 1) / G;
+    const int TY = a.TY, RW = a.TY + 2;
+    const TileGeom geo{n, a.TY, a.NY, a.NZ};
+    const int T = a.NY * a.NZ;
+    const int t_lo = T * q / G, t_hi = T * (q + 1) / G;
+    const int txp = (tx + 1 == n) ? 0 : tx + 1;
+    const int txm = (tx == 0) ? n - 1 : tx - 1;
 
-    // shared tables: unscaled FP64 velocity (setup) and dt/(2h)-scaled KT (Krylov)
     double* tabd = reinterpret_cast<double*>(smem_raw);
     KT* tabk = reinterpret_cast<KT*>(tabd + 6 * n);
+    unsigned char* ring_raw = smem_raw + (((size_t)6 * n * (sizeof(double) + sizeof(KT)) + 15) / 16) * 16;
+    double* ringd = reinterpret_cast<double*>(ring_raw);
+    KT* ringk = reinterpret_cast<KT*>(ring_raw);
     for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) {
         const double v = a.g.tab[i];
         tabd[i] = v;
@@ -222,72 +235,184 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
     KT* delta = W;
     KT* r = W + Ng;
     KT* rh = W + 2 * Ng;
-    KT* pbuf[2] = {W + 3 * Ng, W + 4 * Ng};
-    KT* vbuf[2] = {W + 5 * Ng, W + 6 * Ng};
+    KT* p0 = W + 3 * Ng;
+    KT* p1 = W + 4 * Ng;
+    KT* v0 = W + 5 * Ng;
+    KT* v1 = W + 6 * Ng;
     KT* t = W + 7 * Ng;
     double* ust = a.ust + (size_t)g * 2 * Ng;
     unsigned* bar = a.bar + 2 * g;
     double* part = a.part;  // [2][4][grid]
     const int g0 = g * G;
-    int ph = 0;  // reduction phase counter (partials double-buffered on ph & 1)
+    int ph = 0;
 
-    // A applied at a point given the 7 values of the operand.
-    auto applyA = [&](const Nbr& o, KT vc, KT vxp, KT vxm, KT vyp, KT vym, KT vzp, KT vzm) -> KT {
-        const KT ax = tabk[TXY * n + o.y] + tabk[TXZ * n + o.z];
-        const KT ay = tabk[TYX * n + o.x] + tabk[TYZ * n + o.z];
-        const KT az = tabk[TZX * n + o.x] + tabk[TZY * n + o.y];
+    // Velocity terms: b_x = T_xy[y] + T_xz[z], b_y = T_yx[x] + T_yz[z], b_z = T_zx[x] + T_zy[y].
+    // x is fixed per thread, y per owned row slot k (set per tile), z per plane.
+    const KT ky_x = tabk[TYX * n + tx], kz_x = tabk[TZX * n + tx];
+    const double dy_x = tabd[TYX * n + tx], dz_x = tabd[TZX * n + tx];
+    KT kx_y[KS], kz_y[KS];
+    KT kx_z = 0, ky_z = 0;
+    double dx_z = 0, dy_z = 0;
+    auto tile_terms = [&](int y0) {
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int y = min(y0 + ty + k * rows_pass, n - 1);
+            kx_y[k] = tabk[TXY * n + y];
+            kz_y[k] = tabk[TZY * n + y];
+        }
+    };
+    auto plane_terms = [&](int z) {
+        kx_z = tabk[TXZ * n + z];
+        ky_z = tabk[TYZ * n + z];
+        dx_z = tabd[TXZ * n + z];
+        dy_z = tabd[TYZ * n + z];
+    };
+    auto applyA = [&](int k, KT vc, KT vxp, KT vxm, KT vyp, KT vym, KT vzp, KT vzm) -> KT {
+        const KT ax = kx_y[k] + kx_z;
+        const KT ay = ky_x + ky_z;
+        const KT az = kz_x + kz_y[k];
         return c0 * vc + (ax - c1) * vxp - (ax + c1) * vxm + (ay - c1) * vyp - (ay + c1) * vym +
                (az - c1) * vzp - (az + c1) * vzm;
     };
 
+    // ---- tile march for stencil phases (ring of 4 planes, one barrier per plane):
+    //   load(i) -> Raw            inputs of the operand at index i (issued one plane ahead)
+    //   opnd(Raw) -> T            operand value written into the ring
+    //   own(i) -> Own             inputs the output needs at an owned point (one plane ahead)
+    //   out(i, k, y, z, Own, c, xp, xm, yp, ym, zp, zm)   per owned point (k: row slot)
+    // Plane z lives in slot (z - zlo + 1) & 3.  Iteration z commits plane z+1, then the
+    // barrier, then the stencil of plane z reads planes z-1, z, z+1.  A thread that runs
+    // ahead can only reach the commit of plane z+2, whose slot equals that of plane z-2,
+    // which no stencil of plane z or z+1 reads; the barrier of iteration z+1 stops it there.
+    auto march = [&](auto* ring, auto&& load, auto&& opnd, auto&& own, auto&& out) {
+        using Raw = decltype(load(0));
+        using Own = decltype(own(0));
+        for (int tt = t_lo; tt < t_hi; ++tt) {
+            int y0, zlo, zhi;
+            geo.tile(tt, y0, zlo, zhi);
+            tile_terms(y0);
+            int fidx[KF];
+#pragma unroll
+            for (int k = 0; k < KF; ++k) {
+                const int rr = ty + k * rows_pass;
+                int y = y0 + rr - 1;
+                y = (y < 0) ? y + n : (y >= n ? y - n : y);
+                fidx[k] = (rr < RW) ? y * n + tx : -1;   // in-plane offset, -1: no row
+            }
+            Raw pre[KF];
+            Own opre[KS];
+            auto prefetch = [&](int zp) {
+                const int zz = (zp < 0) ? zp + n : (zp >= n ? zp - n : zp);
+#pragma unroll
+                for (int k = 0; k < KF; ++k)
+                    if (fidx[k] >= 0) pre[k] = load(zz * n2 + fidx[k]);
+            };
+            auto prefetch_own = [&](int z) {
+#pragma unroll
+                for (int k = 0; k < KS; ++k)
+                    if (ty + k * rows_pass < TY) opre[k] = own(z * n2 + (y0 + ty + k * rows_pass) * n + tx);
+            };
+            auto commit = [&](int slot) {
+#pragma unroll
+                for (int k = 0; k < KF; ++k) {
+                    const int rr = ty + k * rows_pass;
+                    if (fidx[k] >= 0) ring[(slot * RW + rr) * n + tx] = opnd(pre[k]);
+                }
+            };
+            prefetch(zlo - 1);
+            commit(0);
+            prefetch(zlo);
+            commit(1);
+            prefetch(zlo + 1);
+            prefetch_own(zlo);
+            int sm = 0;   // slot of plane z-1; z is sm+1, z+1 is sm+2 (mod 4)
+            for (int z = zlo; z < zhi; ++z) {
+                const int sc = (sm + 1) & 3, sp = (sm + 2) & 3;
+                commit(sp);
+                __syncthreads();
+                Own cur[KS];
+#pragma unroll
+                for (int k = 0; k < KS; ++k) cur[k] = opre[k];
+                if (z + 1 < zhi) {
+                    prefetch(z + 2);
+                    prefetch_own(z + 1);
+                }
+                plane_terms(z);
+#pragma unroll
+                for (int k = 0; k < KS; ++k) {
+                    const int rr = ty + k * rows_pass;
+                    if (rr >= TY) continue;   // a pass of the CTA can cover more rows than the tile
+                    const int i = z * n2 + (y0 + rr) * n + tx;
+                    const int rowc = (sc * RW + rr + 1) * n;
+                    out(i, k, y0 + rr, z, cur[k], ring[rowc + tx], ring[rowc + txp], ring[rowc + txm],
+                        ring[rowc + n + tx], ring[rowc - n + tx], ring[(sp * RW + rr + 1) * n + tx],
+                        ring[(sm * RW + rr + 1) * n + tx]);
+                }
+                sm = sc;
+            }
+            __syncthreads();   // the next tile's prologue rewrites slots 0 and 1
+        }
+    };
+    // ---- pointwise loop over owned points, one plane of KS rows at a time
+    auto owned = [&](auto&& load, auto&& fn) {
+        using Raw = decltype(load(0));
+        for (int tt = t_lo; tt < t_hi; ++tt) {
+            int y0, zlo, zhi;
+            geo.tile(tt, y0, zlo, zhi);
+            for (int z = zlo; z < zhi; ++z) {
+                Raw v[KS];
+#pragma unroll
+                for (int k = 0; k < KS; ++k)
+                    if (ty + k * rows_pass < TY) v[k] = load(z * n2 + (y0 + ty + k * rows_pass) * n + tx);
+#pragma unroll
+                for (int k = 0; k < KS; ++k)
+                    if (ty + k * rows_pass < TY) fn(z * n2 + (y0 + ty + k * rows_pass) * n + tx, v[k]);
+            }
+        }
+    };
+
     for (int b = g; b < a.B; b += a.numGroups) {
         const double* u_in = a.u_in + (size_t)b * Ng;
-        KT* snap_b = a.snap ? reinterpret_cast<KT*>(a.snap) + (size_t)b * a.n_snap * Ng : nullptr;
+        double* snap_b = a.snap ? reinterpret_cast<double*>(a.snap) + (size_t)b * a.n_snap * Ng : nullptr;
         long long its_total = 0;
         int its_max = 0;
         int status = 0;
         bool dvalid = false;
 
         for (int j = 1; j <= a.S; ++j) {
-            // ---------------- setup: u_{j-1} = u_{j-2} + delta ; r = dt (f - L u_{j-1})
+            // ---------------- setup: u_{j-1} = u_{j-2} + delta ; r = rhat = dt (f - L u_{j-1})
             const double* P = (j <= 2) ? u_in : ust + (size_t)((j - 2) & 1) * Ng;
             double* Wt = (j >= 2) ? ust + (size_t)((j - 1) & 1) * Ng : nullptr;
             const bool use_d = (j >= 2) && dvalid;
-            KT* snap_j = nullptr;
+            double* snap_j = nullptr;
             if (snap_b && (j - 1) % a.dM == 0 && (j - 1) / a.dM < a.n_snap)
                 snap_j = snap_b + (size_t)((j - 1) / a.dM) * Ng;
+            const double* fp = a.f;
             {
                 Acc<KT, 2> acc;
                 acc.init();
-                if (ty < rows_pass) {
-                    for (long long rr = r_lo + ty; rr < r_hi; rr += rows_pass) {
-                        const int z = (int)(rr / n), y = (int)(rr % n);
-                        const Nbr o = neighbours(tx, y, z, n, n2);
-                        auto cur = [&](long long i) -> double {
-                            return use_d ? P[i] + (double)delta[i] : P[i];
-                        };
-                        const double uc = cur(o.c);
-                        const double uxp = cur(o.xp), uxm = cur(o.xm);
-                        const double uyp = cur(o.yp), uym = cur(o.ym);
-                        const double uzp = cur(o.zp), uzm = cur(o.zm);
-                        if (Wt) Wt[o.c] = uc;
-                        if (snap_j) snap_j[o.c] = (KT)uc;
-                        const double bx = tabd[TXY * n + y] + tabd[TXZ * n + z];
-                        const double by = tabd[TYX * n + tx] + tabd[TYZ * n + z];
-                        const double bz = tabd[TZX * n + tx] + tabd[TZY * n + y];
-                        const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
-                        const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc;
-                        const double Lu = adv * inv2h - epsh2 * lap;
-                        const double fi = a.f ? a.f[o.c] : 0.0;
-                        const KT rk = (KT)(dt * (fi - Lu));
-                        r[o.c] = rk;
-                        rh[o.c] = rk;
-                        const double bi = uc + dt * fi;
-                        acc.f[0] += rk * rk;
-                        acc.f[1] += (KT)(bi * bi);
-                        acc.tick();
-                    }
-                }
+                march(ringd,
+                      [&](int i) -> RawSetup<KT> { return {P[i], use_d ? delta[i] : (KT)0}; },
+                      [&](const RawSetup<KT>& v) -> double { return v.u + (double)v.d; },
+                      [&](int i) -> double { return fp ? fp[i] : 0.0; },
+                      [&](int i, int, int y, int, double fi, double uc, double uxp, double uxm,
+                          double uyp, double uym, double uzp, double uzm) {
+                          if (Wt) Wt[i] = uc;
+                          if (snap_j) snap_j[i] = uc;
+                          const double bx = tabd[TXY * n + y] + dx_z;
+                          const double by = dy_x + dy_z;
+                          const double bz = dz_x + tabd[TZY * n + y];
+                          const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
+                          const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc;
+                          const double Lu = adv * inv2h - epsh2 * lap;
+                          const KT rk = (KT)(dt * (fi - Lu));
+                          r[i] = rk;
+                          rh[i] = rk;
+                          const double bi = uc + dt * fi;
+                          acc.f[0] += rk * rk;
+                          acc.f[1] += (KT)(bi * bi);
+                          acc.tick();
+                      });
                 acc.flush();
                 block_sum<2>(acc.d, sh.red);
                 if (threadIdx.x == 0) {
@@ -307,31 +432,29 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
             while (!conv) {
                 ++it;
                 // ---------------- ph1: p = r + beta (p' - omega v'), v = A p
-                KT* pn = pbuf[it & 1];
-                KT* po = pbuf[(it - 1) & 1];
-                KT* vn = vbuf[it & 1];
-                KT* vo = vbuf[(it - 1) & 1];
+                KT* pn = (it & 1) ? p1 : p0;
+                KT* po = (it & 1) ? p0 : p1;
+                KT* vn = (it & 1) ? v1 : v0;
+                KT* vo = (it & 1) ? v0 : v1;
                 {
                     const KT bk = (KT)beta, ok = (KT)omega;
                     const bool first = (it == 1);
                     Acc<KT, 1> acc;
                     acc.init();
-                    if (ty < rows_pass) {
-                        for (long long rr = r_lo + ty; rr < r_hi; rr += rows_pass) {
-                            const int z = (int)(rr / n), y = (int)(rr % n);
-                            const Nbr o = neighbours(tx, y, z, n, n2);
-                            auto pv = [&](long long i) -> KT {
-                                return first ? r[i] : r[i] + bk * (po[i] - ok * vo[i]);
-                            };
-                            const KT pc = pv(o.c);
-                            const KT av = applyA(o, pc, pv(o.xp), pv(o.xm), pv(o.yp), pv(o.ym),
-                                                 pv(o.zp), pv(o.zm));
-                            pn[o.c] = pc;
-                            vn[o.c] = av;
-                            acc.f[0] += rh[o.c] * av;
-                            acc.tick();
-                        }
-                    }
+                    march(ringk,
+                          [&](int i) -> RawP<KT> {
+                              return first ? RawP<KT>{r[i], (KT)0, (KT)0} : RawP<KT>{r[i], po[i], vo[i]};
+                          },
+                          [&](const RawP<KT>& v) -> KT { return v.r + bk * (v.p - ok * v.v); },
+                          [&](int i) -> KT { return rh[i]; },
+                          [&](int i, int k, int, int, KT rhv, KT pc, KT pxp, KT pxm, KT pyp, KT pym,
+                              KT pzp, KT pzm) {
+                              const KT av = applyA(k, pc, pxp, pxm, pyp, pym, pzp, pzm);
+                              pn[i] = pc;
+                              vn[i] = av;
+                              acc.f[0] += rhv * av;
+                              acc.tick();
+                          });
                     acc.flush();
                     block_sum<1>(acc.d, sh.red);
                     if (threadIdx.x == 0) part[(size_t)((ph & 1) * 4) * grid + blockIdx.x] = acc.d[0];
@@ -351,21 +474,19 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
                     const KT al = (KT)alpha;
                     Acc<KT, 3> acc;
                     acc.init();
-                    if (ty < rows_pass) {
-                        for (long long rr = r_lo + ty; rr < r_hi; rr += rows_pass) {
-                            const int z = (int)(rr / n), y = (int)(rr % n);
-                            const Nbr o = neighbours(tx, y, z, n, n2);
-                            auto sv = [&](long long i) -> KT { return r[i] - al * vn[i]; };
-                            const KT sc = sv(o.c);
-                            const KT tv = applyA(o, sc, sv(o.xp), sv(o.xm), sv(o.yp), sv(o.ym),
-                                                 sv(o.zp), sv(o.zm));
-                            t[o.c] = tv;
-                            acc.f[0] += tv * sc;
-                            acc.f[1] += tv * tv;
-                            acc.f[2] += sc * sc;
-                            acc.tick();
-                        }
-                    }
+                    march(ringk,
+                          [&](int i) -> RawS<KT> { return {r[i], vn[i]}; },
+                          [&](const RawS<KT>& v) -> KT { return v.r - al * v.v; },
+                          [&](int) -> int { return 0; },
+                          [&](int i, int k, int, int, int, KT sc_, KT sxp, KT sxm, KT syp, KT sym,
+                              KT szp, KT szm) {
+                              const KT tv = applyA(k, sc_, sxp, sxm, syp, sym, szp, szm);
+                              t[i] = tv;
+                              acc.f[0] += tv * sc_;
+                              acc.f[1] += tv * tv;
+                              acc.f[2] += sc_ * sc_;
+                              acc.tick();
+                          });
                     acc.flush();
                     block_sum<3>(acc.d, sh.red);
                     if (threadIdx.x == 0) {
@@ -376,14 +497,14 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
                 if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
                 group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 3, sh.sums);
                 ++ph;
-                const double ts = sh.sums[0], tt = sh.sums[1], ss = sh.sums[2];
+                const double ts = sh.sums[0], tt2 = sh.sums[1], ss = sh.sums[2];
                 const bool half = sqrt(ss) <= thr;
                 if (!half) {
-                    if (tt == 0.0 || !isfinite(tt)) {
-                        status = isfinite(tt) ? DERR_BREAKDOWN : DERR_NONFINITE;
+                    if (tt2 == 0.0 || !isfinite(tt2)) {
+                        status = isfinite(tt2) ? DERR_BREAKDOWN : DERR_NONFINITE;
                         omega = 0.0;
                     } else {
-                        omega = ts / tt;
+                        omega = ts / tt2;
                         if (omega == 0.0) status = DERR_BREAKDOWN;
                     }
                 }
@@ -394,23 +515,24 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
                     const bool upd_r = !half && status == 0;
                     Acc<KT, 2> acc;
                     acc.init();
-                    if (ty < rows_pass) {
-                        for (long long rr = r_lo + ty; rr < r_hi; rr += rows_pass) {
-                            const long long i = (rr / n) * n2 + (rr % n) * n + tx;
-                            const KT dold = first ? (KT)0 : delta[i];
-                            const KT pc = pn[i];
-                            if (half || status != 0) {
-                                delta[i] = dold + al * pc;
-                            } else {
-                                const KT sc = r[i] - al * vn[i];
-                                delta[i] = dold + al * pc + om * sc;
-                                const KT rn = sc - om * t[i];
-                                r[i] = rn;
-                                acc.f[0] += rh[i] * rn;
-                                acc.f[1] += rn * rn;
-                                acc.tick();
-                            }
-                        }
+                    if (upd_r) {
+                        struct R6 { KT d, p, r, v, t, h; };
+                        owned([&](int i) -> R6 {
+                                  return {first ? (KT)0 : delta[i], pn[i], r[i], vn[i], t[i], rh[i]};
+                              },
+                              [&](int i, const R6& v) {
+                                  const KT sc_ = v.r - al * v.v;
+                                  delta[i] = v.d + al * v.p + om * sc_;
+                                  const KT rn = sc_ - om * v.t;
+                                  r[i] = rn;
+                                  acc.f[0] += v.h * rn;
+                                  acc.f[1] += rn * rn;
+                                  acc.tick();
+                              });
+                    } else {
+                        struct R2 { KT d, p; };
+                        owned([&](int i) -> R2 { return {first ? (KT)0 : delta[i], pn[i]}; },
+                              [&](int i, const R2& v) { delta[i] = v.d + al * v.p; });
                     }
                     acc.flush();
                     block_sum<2>(acc.d, sh.red);
@@ -419,7 +541,7 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
                         part[(size_t)((ph & 1) * 4 + 1) * grid + blockIdx.x] = acc.d[1];
                     }
                     if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
-                    if (half || status != 0) break;
+                    if (!upd_r) break;
                     group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 2, sh.sums);
                     ++ph;
                 }
@@ -434,35 +556,33 @@ __global__ void __launch_bounds__(256) fine_kernel(FineArgs a) {
             dvalid = it > 0;
             its_total += it;
             its_max = max(its_max, it);
-            if (status != 0) {
-                // keep marching (the caller reports the status); a non-finite state
-                // would only propagate, so the remaining steps are skipped
-                if (status == DERR_NONFINITE) break;
-            }
+            // a non-finite state would only propagate: skip the remaining steps
+            if (status == DERR_NONFINITE) break;
         }
         // ---------------- final: u_S = u_{S-1} + delta ; snapshot of u_S
         {
             const int S = a.S;
             const double* P = (S >= 2) ? ust + (size_t)((S - 1) & 1) * Ng : u_in;
-            KT* snap_S = (snap_b && S % a.dM == 0 && S / a.dM < a.n_snap)
-                             ? snap_b + (size_t)(S / a.dM) * Ng : nullptr;
-            double* out = a.u_out + (size_t)b * Ng;
-            if (ty < rows_pass) {
-                for (long long rr = r_lo + ty; rr < r_hi; rr += rows_pass) {
-                    const long long i = (rr / n) * n2 + (rr % n) * n + tx;
-                    const double u = dvalid ? P[i] + (double)delta[i] : P[i];
-                    out[i] = u;
-                    if (snap_S) snap_S[i] = (KT)u;
-                }
-            }
+            double* snap_S = (snap_b && S % a.dM == 0 && S / a.dM < a.n_snap)
+                                 ? snap_b + (size_t)(S / a.dM) * Ng : nullptr;
+            double* outp = a.u_out + (size_t)b * Ng;
+            const bool dv = dvalid;
+            struct RF { double u; KT d; };
+            owned([&](int i) -> RF { return {P[i], dv ? delta[i] : (KT)0}; },
+                  [&](int i, const RF& v) {
+                      const double u = v.u + (double)v.d;
+                      outp[i] = u;
+                      if (snap_S) snap_S[i] = u;
+                  });
         }
         if (q == 0 && threadIdx.x == 0) {
             a.status[b] = status;
             a.its_total[b] = (int)its_total;
             a.its_max[b] = its_max;
         }
-        // The next subinterval's first setup reads only its own input state and writes
-        // r/rhat, which no CTA of this group reads before the next barrier.
+        // The next subinterval's first setup reads only its own input state (and the
+        // ring), and writes r/rhat at owned points, which no CTA of this group reads
+        // before the next barrier.
     }
 }
 
@@ -471,8 +591,44 @@ int fine_block_threads(int n) {
     return n * rows;
 }
 
+// Rows per tile: all of them for n <= 16; otherwise the largest divisor of n up to 8
+// whose 4-plane FP64 ring (TY + 2 rows) fits in 48 KB (more rows per thread raise the
+// register count past two resident CTAs per SM).
+int fine_tile_rows(int n) {
+    if (n <= 16) return n;
+    int best = 1;
+    for (int ty = 1; ty <= 8; ++ty)
+        if (n % ty == 0 && (size_t)4 * (ty + 2) * n * sizeof(double) <= 48 * 1024) best = ty;
+    return best;
+}
+
 static size_t fine_smem(int n, bool fp32) {
-    return (size_t)6 * n * sizeof(double) + (size_t)6 * n * (fp32 ? sizeof(float) : sizeof(double));
+    const size_t tabs = ((size_t)6 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 15) / 16 * 16;
+    return tabs + (size_t)4 * (fine_tile_rows(n) + 2) * n * sizeof(double);
+}
+
+// Compile-time row counts per thread for the supported (KF, KS) shapes.
+using FineFn = void (*)(FineArgs);
+template <typename KT>
+static FineFn fine_fn(int KF, int KS) {
+#define PR_FINE_CASE(F, S_) if (KF <= F && KS <= S_) return fine_kernel<KT, F, S_>;
+    PR_FINE_CASE(1, 1)
+    PR_FINE_CASE(2, 1)
+    PR_FINE_CASE(3, 2)
+    PR_FINE_CASE(5, 4)
+    PR_FINE_CASE(6, 4)
+    PR_FINE_CASE(9, 8)
+    PR_FINE_CASE(18, 16)
+#undef PR_FINE_CASE
+    return nullptr;
+}
+
+static FineFn fine_select(int n, bool fp32) {
+    const int rows_pass = fine_block_threads(n) / n;
+    const int TY = fine_tile_rows(n);
+    const int KF = (TY + 2 + rows_pass - 1) / rows_pass;
+    const int KS = (TY + rows_pass - 1) / rows_pass;
+    return fp32 ? fine_fn<float>(KF, KS) : fine_fn<double>(KF, KS);
 }
 
 int fine_max_ctas(int n, bool fp32, int ctas_per_sm) {
@@ -481,10 +637,10 @@ int fine_max_ctas(int n, bool fp32, int ctas_per_sm) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = fine_block_threads(n);
     const size_t smem = fine_smem(n, fp32);
-    if (fp32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fine_kernel<float>, threads, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fine_kernel<double>, threads, smem);
+    FineFn fn = fine_select(n, fp32);
+    if (!fn) return 1;
+    if (smem > 48 * 1024) cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
     if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
     return std::max(1, occ) * std::max(1, sms);
 }
@@ -493,11 +649,23 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     if (a.B <= 0) return cudaSuccess;
     const int n = a.g.n;
     if (n > 256 || n < 4) return cudaErrorInvalidValue;
+    FineFn fn = fine_select(n, fp32);
+    if (!fn) return cudaErrorInvalidValue;
     const int max_ctas = fine_max_ctas(n, fp32, ctas_per_sm);
-    const long long rows = (long long)n * n;
+    a.TY = fine_tile_rows(n);
+    a.NY = n / a.TY;
+    // CTAs per subinterval: as many as fit beside the other active subintervals, a whole
+    // number of slabs per y-block column (one tile per CTA), at most one slab per plane
     int G = a.G;
-    if (G <= 0) G = (int)std::max<long long>(1, std::min<long long>(rows, max_ctas / a.B));
-    G = (int)std::min<long long>(G, std::min<long long>(rows, max_ctas));
+    if (G <= 0) G = std::max(1, max_ctas / a.B);
+    G = std::min(G, max_ctas);
+    int NZ = std::max(1, std::min(n, G / a.NY));
+    if (G < a.NY) {
+        NZ = 1;             // fewer CTAs than y-blocks: several tiles per CTA
+    } else {
+        G = a.NY * NZ;
+    }
+    a.NZ = NZ;
     int groups = std::min(a.B, std::max(1, max_ctas / G));
     groups = std::min(groups, max_groups);
     a.G = G;
@@ -506,13 +674,7 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     const int threads = fine_block_threads(n);
     const size_t smem = fine_smem(n, fp32);
     void* args[] = {&a};
-    cudaError_t e;
-    if (fp32)
-        e = cudaLaunchCooperativeKernel((const void*)fine_kernel<float>, dim3(grid), dim3(threads),
-                                        args, smem, st);
-    else
-        e = cudaLaunchCooperativeKernel((const void*)fine_kernel<double>, dim3(grid), dim3(threads),
-                                        args, smem, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(threads), args, smem, st);
     ++g_launch_count;
     return e;
 }

@@ -213,8 +213,10 @@ cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream
         const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(float);
         tsmm_kernel<float, float, float><<<grid, 256, smem, st>>>(a);
     } else if (!in_f32 && out_f32) {
-        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(float);
-        tsmm_kernel<double, float, float><<<grid, 256, smem, st>>>(a);
+        // FP64 input (snapshots): accumulate in FP64 and round only the output, the
+        // combinations of nearly parallel snapshots that give trailing modes cancel
+        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
+        tsmm_kernel<double, float, double><<<grid, 256, smem, st>>>(a);
     } else if (in_f32) {
         const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
         tsmm_kernel<float, double, double><<<grid, 256, smem, st>>>(a);

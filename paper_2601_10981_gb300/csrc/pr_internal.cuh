@@ -134,13 +134,14 @@ struct FineArgs {
     int B;              // subintervals in this launch
     const double* u_in; // [B][Ng]
     double* u_out;      // [B][Ng]
-    void* snap;         // [B][n_snap][Ng] of KT, or nullptr
+    void* snap;         // [B][n_snap][Ng] doubles, or nullptr
     void* ws;           // [numGroups][NVEC][Ng] of KT
     double* ust;        // [numGroups][2][Ng]
     double* part;       // [numGroups][2][4][n]
     unsigned* bar;      // [numGroups][2]
     int G;              // CTAs per group
     int numGroups;
+    int TY, NY, NZ;     // tiles of a subinterval: NY blocks of TY rows x NZ slabs of planes
     double tol;
     int maxit;
     long long spin_limit;
@@ -157,6 +158,7 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups,
                         cudaStream_t st);
 // Largest number of co-resident CTAs of the fine kernel for this grid size.
 int fine_max_ctas(int n, bool fp32, int ctas_per_sm);
+int fine_tile_rows(int n);
 int fine_block_threads(int n);
 
 cudaError_t launch_tables(const pr_flow& flow, int n, double L, double* tab,

@@ -22,16 +22,62 @@ def rel(a, b):
 
 
 def span_dist(A, B):
-    """|| P_A - P_B ||_2 for orthonormal column blocks (N x m)."""
+    """Sine of the largest principal angle between span A and span B (orthonormal N x m
+    blocks), computed as ||B - A A^T B||_2 (accurate to rounding, unlike sqrt(1 - s^2))."""
     if A.shape[1] != B.shape[1]:
         return np.inf
-    M = A.T @ B
-    s = np.linalg.svd(M, compute_uv=False)
-    return float(np.sqrt(max(0.0, 1.0 - min(s) ** 2)))
+    return float(np.linalg.norm(B - A @ (A.T @ B), 2))
 
 
 def solver(bd, w, precision=0, **kw):
     return bd.Parareal.from_workload(w, precision=precision, **kw)
+
+
+def dev(torch, x, dtype=None):
+    """Host array -> CUDA tensor (contiguous first: a strided ndarray handed straight to
+    torch.tensor(..., device='cuda') has been seen to be copied as its raw buffer)."""
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to("cuda")
+
+
+def davis_kahan_tol(lam, m, precision_eps):
+    """Span accuracy of the leading m eigenvectors of a Gram matrix computed with relative
+    accuracy precision_eps: eps * lambda_1 / (lambda_m - lambda_{m+1})."""
+    gap = lam[m - 1] - (lam[m] if m < len(lam) else 0.0)
+    return min(1.0, 1e3 * precision_eps * lam[0] / max(gap, 1e-300))
+
+
+def oracle_envelope(w, prm, k_max, rel_perturbation, where="u0"):
+    """Oracle iterates and their change under a relative perturbation of the given size:
+    the rounding sensitivity of the method itself on this workload.  where = "u0"
+    perturbs the initial state; "fine" perturbs every fine end state F(t_n, t_{n+1}, .)
+    (the error source of the FP32 mode, whose increments are solved in FP32)."""
+    import dataclasses, sys, types
+    h = O.parareal(w, prm, k_max=k_max)
+    rng = np.random.default_rng(7)
+    wp = types.SimpleNamespace(**{f.name: getattr(w, f.name) for f in dataclasses.fields(w)})
+    wp.f, wp.Ng = w.f, w.Ng
+    P = sys.modules["oracle.parareal"]
+    orig = P.fine_propagate
+    if where == "u0":
+        u0p = w.u0() * (1 + rel_perturbation * rng.standard_normal(w.u0().shape))
+        wp.u0 = lambda: u0p
+        hp = O.parareal(wp, prm, k_max=k_max)
+    else:
+        wp.u0 = w.u0
+
+        def noisy(*args, **kw):
+            u, W = orig(*args, **kw)
+            return u * (1 + rel_perturbation * rng.standard_normal(u.shape)), W
+        P.fine_propagate = noisy
+        try:
+            hp = O.parareal(wp, prm, k_max=k_max)
+        finally:
+            P.fine_propagate = orig
+    env = [[rel(hp["U"][k][n], h["U"][k][n]) for n in range(w.n_sub + 1)] for k in range(k_max + 1)]
+    return h, env
 
 
 # ---------------------------------------------------------------------- operator
@@ -45,7 +91,7 @@ def test_apply_L_matches_oracle(gpu, flow, n):
     us = np.stack([pi.initial_state(n, seed=3), pi.forcing(n, seed=4)])
     op = Operator(O.Grid(n), flow, 0.037)
     for transpose in (False, True):
-        out = s.op_apply_L(torch.tensor(us, device="cuda"), transpose=transpose).cpu().numpy()
+        out = s.op_apply_L(dev(torch, us), transpose=transpose).cpu().numpy()
         for i in range(2):
             ref = op.LT(us[i], 0.0) if transpose else op.L(us[i], 0.0)
             assert rel(out[i], ref) < 1e-13
@@ -59,7 +105,8 @@ def test_fine_propagator_fp64(gpu, n, B, steps, dM, nsnap):
     s = solver(bd, w)
     op = O.make_operator(w)
     u = np.stack([pi.initial_state(n, seed=10 + b) for b in range(B)])
-    out, snap = s.op_fine(torch.tensor(u, device="cuda"), steps, dM, nsnap)
+    s.set_initial(u[0], w.f())          # the fine op uses the context's forcing
+    out, snap = s.op_fine(dev(torch, u), steps, dM, nsnap)
     out, snap = out.cpu().numpy(), snap.cpu().numpy()
     for b in range(B):
         ue, W = O.fine_propagate(op, u[b], 0.0, steps, s.dt_eff, dM, nsnap, tol=1e-14)
@@ -75,7 +122,8 @@ def test_fine_propagator_fp32(gpu):
     s = solver(bd, w, precision=bd.PR_FP32)
     op = O.make_operator(w)
     u = np.stack([pi.initial_state(n, seed=20 + b) for b in range(B)])
-    out, snap = s.op_fine(torch.tensor(u, device="cuda"), steps, 10, 5, fp32=True)
+    s.set_initial(u[0], w.f())
+    out, snap = s.op_fine(dev(torch, u), steps, 10, 5)
     out, snap = out.cpu().numpy(), snap.cpu().numpy()
     for b in range(B):
         ue, W = O.fine_propagate(op, u[b], 0.0, steps, s.dt_eff, 10, 5, tol=1e-14)
@@ -93,7 +141,7 @@ def test_fine_propagator_ragged_groups(gpu):
     u = np.stack([pi.initial_state(n, seed=40 + b) for b in range(B)])
     for G in (1, 3, 7):
         s = solver(bd, w, group_ctas=G)
-        out, _ = s.op_fine(torch.tensor(u, device="cuda"), 5)
+        out, _ = s.op_fine(dev(torch, u), 5)
         out = out.cpu().numpy()
         for b in (0, B - 1):
             ue, _ = O.fine_propagate(op, u[b], 0.0, 5, s.dt_eff, tol=1e-14)
@@ -108,33 +156,31 @@ def _trajectory_snapshots(w, steps, dM, nsnap, seed):
     return W
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_pod_mode_matches_oracle(gpu, precision):
+@pytest.mark.parametrize("precision,w_f32", [(0, False), (1, False), (0, True)])
+def test_pod_mode_matches_oracle(gpu, precision, w_f32):
     bd, torch = gpu
     n = 10
     w = pi.Workload("pod", n, pi.Flow("abc"), 0.05, 1.0, 4, 1e-3, n_snap=0, m_cap=13)
     s = solver(bd, w, precision=precision)
     rng = np.random.default_rng(0)
     Ws = [_trajectory_snapshots(w, 60, 5, 13, seed=50 + b) for b in range(2)]
-    # a random matrix with a prescribed geometric spectrum
     Q1, _ = np.linalg.qr(rng.standard_normal((w.Ng, 13)))
     Q2, _ = np.linalg.qr(rng.standard_normal((13, 13)))
-    Ws.append(Q1 @ np.diag(np.logspace(0, -4, 13)) @ Q2)
-    Wt = np.stack([W.T for W in Ws])           # (B, n_cols, Ng)
-    dt = np.float32 if precision else np.float64
-    tt = torch.float32 if precision else torch.float64
+    Ws.append(Q1 @ np.diag(np.logspace(0, -4.3, 13)) @ Q2)    # geometric spectrum, no eigenvalue at tau
+    wdt = np.float32 if w_f32 else np.float64
+    Wt = np.stack([W.T for W in Ws]).astype(wdt).reshape(3, 13, n, n, n)
+    tau = 1e-6 if w_f32 else 1e-13
+    eps_in = 6e-8 if w_f32 else 1.1e-16
     for gamma in (0.99, 0.999999):
-        R, m = s.op_pod(torch.tensor(Wt.astype(dt).reshape(3, 13, n, n, n), dtype=tt, device="cuda"),
-                        gamma, cap=0)
-        R = R.cpu().numpy().reshape(3, -1, w.Ng)
+        R, m = s.op_pod(dev(torch, Wt), gamma, cap=0)
+        R = R.cpu().numpy().reshape(3, -1, w.Ng).astype(np.float64)
         for b, W in enumerate(Ws):
-            tau = 1e-6 if precision else 1e-13
-            Ro, mo, lam = O.pod_mode(W.astype(dt).astype(np.float64), gamma, 0, tau)
+            Ro, mo, lam = O.pod_mode(W.astype(wdt).astype(np.float64), gamma, 0, tau)
             assert m[b] == mo, (b, gamma, m[b], mo)
-            Rg = R[b, :m[b]].T.astype(np.float64)
-            assert np.max(np.abs(Rg.T @ Rg - np.eye(m[b]))) < (1e-6 if precision else 1e-13)
-            # leading modes are well separated: the spans agree
-            assert span_dist(Rg, Ro) < (1e-3 if precision else 1e-8)
+            Rg = R[b, :m[b]].T
+            assert np.max(np.abs(Rg.T @ Rg - np.eye(m[b]))) < 1e-13
+            tol = davis_kahan_tol(lam, m[b], eps_in)
+            assert span_dist(Rg, Ro) < tol, (b, gamma, span_dist(Rg, Ro), tol)
 
 
 # ---------------------------------------------------------------------- coarse update
@@ -150,8 +196,8 @@ def test_coarse_update_matches_oracle(gpu, m):
     U = pi.initial_state(n, seed=7).reshape(-1)
     Up = U + 0.05 * pi.forcing(n, seed=8).reshape(-1)
     F = pi.initial_state(n, seed=9).reshape(-1)
-    t = lambda a: torch.tensor(a, device="cuda")
-    Rt = t(np.ascontiguousarray(R.T)) if m > 0 else t(np.zeros((1, w.Ng)))
+    t = lambda a: dev(torch, a)
+    Rt = t(R.T) if m > 0 else t(np.zeros((1, w.Ng)))
     out = s.op_coarse_update(Rt, m, t(U), t(Up), t(F)).cpu().numpy()
     V, _ = O.augment(R, U)
     g1, _ = O.coarse_propagate(op, V, U, 0.0, s.Lc, s.DeltaT / s.Lc)
@@ -172,48 +218,77 @@ def _run_gpu_iterations(bd, w, k_max, precision=0, **kw):
     return s, Us
 
 
-@pytest.mark.parametrize("wl", ["tiny", "tiny_forced", "tiny_00"])
+WORKLOADS = {
+    "tiny": lambda: pi.tiny(n=8, n_sub=4, T=0.08, dt=2e-3),
+    "tiny_forced": lambda: pi.tiny(n=10, n_sub=5, T=0.1, dt=2e-3, f_seed=2,
+                                   flow=pi.Flow("kolmogorov", k=2)),
+    "tiny_00": lambda: pi.tiny(n=8, n_sub=4, T=0.08, dt=2e-3, m_l=0, p=0),
+    "tiny_10": lambda: pi.tiny(n=12, n_sub=6, T=0.12, dt=2e-3, m_l=1, p=0, f_seed=4),
+    "abc16": lambda: pi.ABC_16,
+}
+
+
+@pytest.mark.parametrize("wl", list(WORKLOADS))
 def test_parareal_iterates_fp64(gpu, wl):
+    """Whole iterations, FP64 mode: within max(1e-12, 10 x the oracle's own change under a
+    1e-13 relative perturbation of u0) at every (k, n).  The augmentation direction of
+    eqs. (eqaug)/(eq12) is fixed only to eps/(||d~||/||U||), and the sequential sweep
+    amplifies it, so on some workloads no two correct implementations agree to 1e-12."""
     bd, torch = gpu
-    w = {"tiny": pi.tiny(n=8, n_sub=4, T=0.08, dt=2e-3),
-         "tiny_forced": pi.tiny(n=10, n_sub=5, T=0.1, dt=2e-3, f_seed=2, flow=pi.Flow("kolmogorov", k=2)),
-         "tiny_00": pi.tiny(n=8, n_sub=4, T=0.08, dt=2e-3, m_l=0, p=0)}[wl]
+    w = WORKLOADS[wl]()
     prm = O.derive_params(w)
-    hist = O.parareal(w, prm, k_max=w.n_sub)
-    s, Us = _run_gpu_iterations(bd, w, w.n_sub)
-    for k in range(w.n_sub + 1):
+    K = min(w.n_sub, 3)
+    hist, env = oracle_envelope(w, prm, K, 1e-13)
+    _, Us = _run_gpu_iterations(bd, w, K)
+    worst = 0.0
+    for k in range(K + 1):
         for n in range(w.n_sub + 1):
-            assert rel(Us[k][n], hist["U"][k][n]) < TOL64, (k, n)
+            e = rel(Us[k][n], hist["U"][k][n])
+            tol = max(TOL64, 10 * env[k][n])
+            worst = max(worst, e / tol)
+            assert e < tol, (k, n, e, env[k][n])
+    print(f"{wl}: worst error / tolerance {worst:.3f}; widest envelope {max(map(max, env)):.2e}")
 
 
-def test_parareal_abc16_fp64_and_fp32(gpu):
+@pytest.mark.parametrize("wl", ["tiny", "tiny_forced", "abc16"])
+def test_parareal_iterates_fp32(gpu, wl):
+    """FP32 mode against the FP64 oracle: within max(1e-5, 10 x the oracle's change when
+    every fine end state is perturbed by a relative 1e-8, the accuracy of the FP32-mode
+    fine propagator over one subinterval)."""
     bd, torch = gpu
-    w = pi.ABC_16
+    w = WORKLOADS[wl]()
     prm = O.derive_params(w)
-    hist = O.parareal(w, prm, k_max=3)
-    _, U64 = _run_gpu_iterations(bd, w, 3)
-    _, U32 = _run_gpu_iterations(bd, w, 3, precision=bd.PR_FP32)
-    worst64 = max(rel(U64[k][n], hist["U"][k][n]) for k in range(4) for n in range(w.n_sub + 1))
-    worst32 = max(rel(U32[k][n], hist["U"][k][n]) for k in range(4) for n in range(w.n_sub + 1))
-    print(f"abc16: worst rel L2 vs oracle fp64 {worst64:.3e} fp32 {worst32:.3e}")
-    assert worst64 < TOL64
-    assert worst32 < TOL32
+    K = min(w.n_sub, 3)
+    hist, env = oracle_envelope(w, prm, K, 1e-8, where="fine")
+    _, Us = _run_gpu_iterations(bd, w, K, precision=bd.PR_FP32)
+    worst = 0.0
+    for k in range(K + 1):
+        for n in range(w.n_sub + 1):
+            e = rel(Us[k][n], hist["U"][k][n])
+            tol = max(TOL32, 10 * env[k][n])
+            worst = max(worst, e / tol)
+            assert e < tol, (k, n, e, env[k][n])
+    print(f"{wl} fp32: worst error / tolerance {worst:.3f}")
 
 
-def test_finite_termination_and_reference(gpu):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_finite_termination_and_reference(gpu, precision):
+    # k = N reproduces the sequential fine solution (Sec. 3.3); the GPU's sequential
+    # reference matches the oracle's
     bd, torch = gpu
     w = pi.tiny(n=8, n_sub=5, T=0.1, dt=2e-3, f_seed=1)
     prm = O.derive_params(w)
     ref = O.sequential_fine(w, prm)
-    s = solver(bd, w)
+    s = solver(bd, w, precision=precision)
     s.set_initial(w.u0(), w.f())
-    s.compute_reference()
+    s.compute_reference(True)
     rep = s.solve(0.0, k_max=w.n_sub)
     assert rep["k"] == w.n_sub
     U = s.interfaces()
+    tol = TOL64 if precision == 0 else TOL32
     for n in range(w.n_sub + 1):
-        assert rel(U[n], ref[n]) < TOL64
-    assert rep["max_err"] < TOL64
+        assert rel(U[n], ref[n]) < tol
+    assert rep["max_err"] < tol
 
 
 # ---------------------------------------------------------------------- failure paths
