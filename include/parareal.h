@@ -246,6 +246,20 @@ pr_status pr_op_pod(pr_ctx* ctx, const void* d_W, int w_f32, int n_cols, int B, 
 pr_status pr_op_coarse_update(pr_ctx* ctx, const void* d_R, int m, const double* d_U,
                               const double* d_Uprev, const double* d_F, double* d_out);
 
+/* The operator of pr_op_apply_L without any device allocation, for callers that cannot
+ * call cudaMalloc (another framework's allocator owns the device memory budget, or the
+ * caller must not trigger the allocator's synchronisation).  It does not need a bound
+ * workspace: its scratch (velocity tables, pointer lists) is one static device array of
+ * 13 568 bytes that every GPU loading this library holds until the process exits.
+ * Limits: n <= 256 and count <= 64 grid functions per call (PR_ERR_INVALID_ARG beyond).
+ * d_in, d_out: count x n^3 device doubles.  Runs on the context stream and synchronises.
+ * The first call on a device looks up the array's device address; make that call before
+ * any stream capture.  All calls share the array and leave the last call's contents;
+ * each call rewrites what it reads, but calls that overlap on the GPU (different streams,
+ * no ordering) race on it.  The paper has no counterpart: this is library plumbing. */
+pr_status pr_op_apply_L_noalloc(pr_ctx* ctx, const double* d_in, double* d_out, int count,
+                                int transpose);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,7 @@ _SIGS = {
     "pr_op_fine": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int]),
     "pr_op_pod": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _P, _I]),
     "pr_op_coarse_update": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, _P]),
+    "pr_op_apply_L_noalloc": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
 }
 
 _lib = None

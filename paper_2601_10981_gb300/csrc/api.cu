@@ -1226,4 +1226,18 @@ pr_status pr_op_coarse_update(pr_ctx* c, const void* d_R, int m, const double* d
     return pr_sync(c);
 }
 
+pr_status pr_op_apply_L_noalloc(pr_ctx* c, const double* d_in, double* d_out, int count, int transpose) {
+    if (!c || !d_in || !d_out || count < 0) return fail(c, PR_ERR_INVALID_ARG, "null pointer or negative count");
+    if (c->n > pr::noalloc_max_n())
+        return fail(c, PR_ERR_INVALID_ARG, "pr_op_apply_L_noalloc: n above its static scratch (n <= " +
+                                               std::to_string(pr::noalloc_max_n()) + ")");
+    if (count > pr::noalloc_max_count())
+        return fail(c, PR_ERR_INVALID_ARG, "pr_op_apply_L_noalloc: more than " +
+                                               std::to_string(pr::noalloc_max_count()) +
+                                               " grid functions in one call");
+    PR_CUDA(pr::apply_L_noalloc(c->n, c->L, c->flow, c->eps, d_in, d_out, count, transpose != 0, c->st));
+    PR_CUDA(cudaStreamSynchronize(c->st));
+    return PR_OK;
+}
+
 }  // extern "C"

@@ -288,6 +288,13 @@ cudaError_t launch_norms(const double* a, const double* b, const double* r, long
                          cudaStream_t st);
 size_t norms_part_doubles(long long Ng, int cnt);
 
+// Operator on caller buffers with its scratch in a static device array (noalloc.cu).
+cudaError_t apply_L_noalloc(int n, double L, const pr_flow& flow, double eps, const double* d_in,
+                            double* d_out, int count, bool transpose, cudaStream_t st);
+int noalloc_max_n();
+int noalloc_max_count();
+size_t noalloc_scratch_bytes();
+
 // Scan for NaN/Inf: sets *flag = 1 if any of the first `count` doubles is not finite.
 cudaError_t launch_nonfinite(const double* x, long long count, int* flag, cudaStream_t st);
 
