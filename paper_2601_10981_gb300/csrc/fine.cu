@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <math.h>
+#include <type_traits>
 
 namespace pr {
 
@@ -185,14 +186,52 @@ struct TileGeom {
     }
 };
 
-// Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
-template <typename KT> struct RawSetup { double u; KT d; };
-template <typename KT> struct RawP { KT r, p, v; };
-template <typename KT> struct RawS { KT r, v; };
+// W consecutive points along x handled by one thread (W = 4: 16-byte vector accesses).
+template <typename T, int W>
+struct Vec {
+    T v[W];
+};
+template <typename T, int W>
+__device__ __forceinline__ Vec<T, W> vload(const T* p) {
+    Vec<T, W> o;
+    if constexpr (W == 4 && sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        o.v[0] = q.x; o.v[1] = q.y; o.v[2] = q.z; o.v[3] = q.w;
+    } else if constexpr (W == 4 && sizeof(T) == 8) {
+        const double2 q0 = *reinterpret_cast<const double2*>(p);
+        const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+        o.v[0] = q0.x; o.v[1] = q0.y; o.v[2] = q1.x; o.v[3] = q1.y;
+    } else {
+#pragma unroll
+        for (int e = 0; e < W; ++e) o.v[e] = p[e];
+    }
+    return o;
+}
+template <typename T, int W>
+__device__ __forceinline__ void vstore(T* p, const Vec<T, W>& o) {
+    if constexpr (W == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
+    } else if constexpr (W == 4 && sizeof(T) == 8) {
+        *reinterpret_cast<double2*>(p) = make_double2(o.v[0], o.v[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(o.v[2], o.v[3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < W; ++e) p[e] = o.v[e];
+    }
+}
 
-// KF: ring rows each thread fills per plane (ceil((TY+2)/rows_pass)); KS: owned rows per
-// thread per plane (TY/rows_pass).  Both compile-time so the prefetch lives in registers.
-template <typename KT, int KF, int KS>
+// Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
+template <typename KT, int W> struct RawSetup { Vec<double, W> u; Vec<KT, W> d; };
+template <typename KT, int W> struct RawP { Vec<KT, W> r, p, v; };
+template <typename KT, int W> struct RawS { Vec<KT, W> r, v; };
+template <typename KT, int W> struct RawF { Vec<double, W> u; Vec<KT, W> d; };
+template <typename KT, int W> struct RawP2 { Vec<KT, W> d, p; };
+template <typename KT, int W> struct Raw6 { Vec<KT, W> d, p, r, v, t, h; };
+struct NoOwn {};
+
+// KT: Krylov type.  W: points per thread along x.  KF: ring rows each thread fills per
+// plane (ceil((TY+2)/RP)).  KS: owned rows per thread per plane (TY/RP).
+template <typename KT, int W, int KF, int KS>
 __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ FineShared sh;
@@ -204,19 +243,24 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     const int n = a.g.n;
     const int n2 = n * n;
     const long long Ng = a.g.Ng;
-    const int rows_pass = blockDim.x / n;
-    const int tx = threadIdx.x % n;
-    const int ty = threadIdx.x / n;
+    const int lanes = n / W;                 // threads per row
+    const int RP = a.RP;                     // rows per pass of the CTA (divides TY)
+    // the CTA is rounded up to whole warps; threads past lanes * RP only join the
+    // reductions and barriers
+    const bool active = threadIdx.x < lanes * RP;
+    const int lx = threadIdx.x % lanes;
+    const int ty = active ? threadIdx.x / lanes : RP + a.TY + 2;
+    const int x0 = lx * W;
     const int TY = a.TY, RW = a.TY + 2;
     const TileGeom geo{n, a.TY, a.NY, a.NZ};
     const int T = a.NY * a.NZ;
     const int t_lo = T * q / G, t_hi = T * (q + 1) / G;
-    const int txp = (tx + 1 == n) ? 0 : tx + 1;
-    const int txm = (tx == 0) ? n - 1 : tx - 1;
+    const int xl = (x0 == 0) ? n - 1 : x0 - 1;   // left neighbour of the first point
+    const int xr = (x0 + W == n) ? 0 : x0 + W;   // right neighbour of the last point
 
     double* tabd = reinterpret_cast<double*>(smem_raw);
     KT* tabk = reinterpret_cast<KT*>(tabd + 6 * n);
-    unsigned char* ring_raw = smem_raw + (((size_t)6 * n * (sizeof(double) + sizeof(KT)) + 15) / 16) * 16;
+    unsigned char* ring_raw = smem_raw + (((size_t)6 * n * (sizeof(double) + sizeof(KT)) + 31) / 32) * 32;
     double* ringd = reinterpret_cast<double*>(ring_raw);
     KT* ringk = reinterpret_cast<KT*>(ring_raw);
     for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) {
@@ -231,32 +275,36 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     const KT c1 = (KT)(dt * eps / (h * h));
     const KT c0 = (KT)(1.0 + 6.0 * dt * eps / (h * h));
 
-    KT* W = reinterpret_cast<KT*>(a.ws) + (size_t)g * FINE_NVEC * Ng;
-    KT* delta = W;
-    KT* r = W + Ng;
-    KT* rh = W + 2 * Ng;
-    KT* p0 = W + 3 * Ng;
-    KT* p1 = W + 4 * Ng;
-    KT* v0 = W + 5 * Ng;
-    KT* v1 = W + 6 * Ng;
-    KT* t = W + 7 * Ng;
+    KT* Wk = reinterpret_cast<KT*>(a.ws) + (size_t)g * FINE_NVEC * Ng;
+    KT* delta = Wk;
+    KT* r = Wk + Ng;
+    KT* rh = Wk + 2 * Ng;
+    KT* p0 = Wk + 3 * Ng;
+    KT* p1 = Wk + 4 * Ng;
+    KT* v0 = Wk + 5 * Ng;
+    KT* v1 = Wk + 6 * Ng;
+    KT* t = Wk + 7 * Ng;
     double* ust = a.ust + (size_t)g * 2 * Ng;
     unsigned* bar = a.bar + 2 * g;
     double* part = a.part;  // [2][4][grid]
     const int g0 = g * G;
     int ph = 0;
 
-    // Velocity terms: b_x = T_xy[y] + T_xz[z], b_y = T_yx[x] + T_yz[z], b_z = T_zx[x] + T_zy[y].
-    // x is fixed per thread, y per owned row slot k (set per tile), z per plane.
-    const KT ky_x = tabk[TYX * n + tx], kz_x = tabk[TZX * n + tx];
-    const double dy_x = tabd[TYX * n + tx], dz_x = tabd[TZX * n + tx];
+    // Velocity terms: b_x = T_xy[y] + T_xz[z], b_y = T_yx[x] + T_yz[z], b_z = T_zx[x] + T_zy[y],
+    // pre-scaled by dt/(2h) for the Krylov operator.  x-terms per thread, y-terms per owned
+    // row slot (set per tile), z-terms per plane.
+    KT ky_x[W], kz_x[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        ky_x[e] = tabk[TYX * n + x0 + e];
+        kz_x[e] = tabk[TZX * n + x0 + e];
+    }
     KT kx_y[KS], kz_y[KS];
     KT kx_z = 0, ky_z = 0;
-    double dx_z = 0, dy_z = 0;
     auto tile_terms = [&](int y0) {
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
-            const int y = min(y0 + ty + k * rows_pass, n - 1);
+            const int y = min(y0 + ty + k * RP, n - 1);
             kx_y[k] = tabk[TXY * n + y];
             kz_y[k] = tabk[TZY * n + y];
         }
@@ -264,27 +312,34 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     auto plane_terms = [&](int z) {
         kx_z = tabk[TXZ * n + z];
         ky_z = tabk[TYZ * n + z];
-        dx_z = tabd[TXZ * n + z];
-        dy_z = tabd[TYZ * n + z];
     };
-    auto applyA = [&](int k, KT vc, KT vxp, KT vxm, KT vyp, KT vym, KT vzp, KT vzm) -> KT {
-        const KT ax = kx_y[k] + kx_z;
-        const KT ay = ky_x + ky_z;
-        const KT az = kz_x + kz_y[k];
-        return c0 * vc + (ax - c1) * vxp - (ax + c1) * vxm + (ay - c1) * vyp - (ay + c1) * vym +
-               (az - c1) * vzp - (az + c1) * vzm;
+
+    // The x +- 1 neighbours of the W points: shifts of the centre vector plus one edge
+    // value on each side read from the ring row.
+    auto shift = [&](const auto* row, const auto& c, auto& xp, auto& xm) {
+#pragma unroll
+        for (int e = 0; e < W - 1; ++e) {
+            xp.v[e] = c.v[e + 1];
+            xm.v[e + 1] = c.v[e];
+        }
+        xp.v[W - 1] = row[xr];
+        xm.v[0] = row[xl];
     };
 
     // ---- tile march for stencil phases (ring of 4 planes, one barrier per plane):
-    //   load(i) -> Raw            inputs of the operand at index i (issued one plane ahead)
-    //   opnd(Raw) -> T            operand value written into the ring
-    //   own(i) -> Own             inputs the output needs at an owned point (one plane ahead)
-    //   out(i, k, y, z, Own, c, xp, xm, yp, ym, zp, zm)   per owned point (k: row slot)
+    //   load(i) -> Raw            inputs of the operand at the W points from index i
+    //   opnd(Raw) -> Vec          operand values written into the ring
+    //   own(i) -> Own             inputs the output needs at owned points (one plane ahead)
+    //   out(i, k, y, Own, rowc, rowzp, rowzm)   per owned W points (k: row slot); rowc is
+    //                             the ring row of the points, rowzp / rowzm the rows above /
+    //                             below in z; rowc +- n are the y neighbours
     // Plane z lives in slot (z - zlo + 1) & 3.  Iteration z commits plane z+1, then the
     // barrier, then the stencil of plane z reads planes z-1, z, z+1.  A thread that runs
     // ahead can only reach the commit of plane z+2, whose slot equals that of plane z-2,
     // which no stencil of plane z or z+1 reads; the barrier of iteration z+1 stops it there.
-    auto march = [&](auto* ring, auto&& load, auto&& opnd, auto&& own, auto&& out) {
+    //   pipe                       true: prefetch one plane ahead; false: load each plane
+    //                              just before committing it (fewer live registers)
+    auto march = [&](bool pipe, auto* ring, auto&& load, auto&& opnd, auto&& own, auto&& out) {
         using Raw = decltype(load(0));
         using Own = decltype(own(0));
         for (int tt = t_lo; tt < t_hi; ++tt) {
@@ -294,10 +349,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             int fidx[KF];
 #pragma unroll
             for (int k = 0; k < KF; ++k) {
-                const int rr = ty + k * rows_pass;
+                const int rr = ty + k * RP;
                 int y = y0 + rr - 1;
                 y = (y < 0) ? y + n : (y >= n ? y - n : y);
-                fidx[k] = (rr < RW) ? y * n + tx : -1;   // in-plane offset, -1: no row
+                fidx[k] = (rr < RW) ? y * n + x0 : -1;   // in-plane offset, -1: no row
             }
             Raw pre[KF];
             Own opre[KS];
@@ -310,43 +365,44 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             auto prefetch_own = [&](int z) {
 #pragma unroll
                 for (int k = 0; k < KS; ++k)
-                    if (ty + k * rows_pass < TY) opre[k] = own(z * n2 + (y0 + ty + k * rows_pass) * n + tx);
+                    if (ty + k * RP < TY) opre[k] = own(z * n2 + (y0 + ty + k * RP) * n + x0);
             };
             auto commit = [&](int slot) {
 #pragma unroll
                 for (int k = 0; k < KF; ++k) {
-                    const int rr = ty + k * rows_pass;
-                    if (fidx[k] >= 0) ring[(slot * RW + rr) * n + tx] = opnd(pre[k]);
+                    const int rr = ty + k * RP;
+                    if (fidx[k] >= 0) vstore(ring + (slot * RW + rr) * n + x0, opnd(pre[k]));
                 }
             };
             prefetch(zlo - 1);
             commit(0);
             prefetch(zlo);
             commit(1);
-            prefetch(zlo + 1);
-            prefetch_own(zlo);
+            if (pipe) {
+                prefetch(zlo + 1);
+                prefetch_own(zlo);
+            }
             int sm = 0;   // slot of plane z-1; z is sm+1, z+1 is sm+2 (mod 4)
             for (int z = zlo; z < zhi; ++z) {
                 const int sc = (sm + 1) & 3, sp = (sm + 2) & 3;
+                if (!pipe) prefetch(z + 1);
                 commit(sp);
                 __syncthreads();
+                if (!pipe) prefetch_own(z);
                 Own cur[KS];
 #pragma unroll
                 for (int k = 0; k < KS; ++k) cur[k] = opre[k];
-                if (z + 1 < zhi) {
+                if (pipe && z + 1 < zhi) {
                     prefetch(z + 2);
                     prefetch_own(z + 1);
                 }
                 plane_terms(z);
 #pragma unroll
                 for (int k = 0; k < KS; ++k) {
-                    const int rr = ty + k * rows_pass;
-                    if (rr >= TY) continue;   // a pass of the CTA can cover more rows than the tile
-                    const int i = z * n2 + (y0 + rr) * n + tx;
-                    const int rowc = (sc * RW + rr + 1) * n;
-                    out(i, k, y0 + rr, z, cur[k], ring[rowc + tx], ring[rowc + txp], ring[rowc + txm],
-                        ring[rowc + n + tx], ring[rowc - n + tx], ring[(sp * RW + rr + 1) * n + tx],
-                        ring[(sm * RW + rr + 1) * n + tx]);
+                    const int rr = ty + k * RP;
+                    if (rr >= TY) continue;
+                    out(z * n2 + (y0 + rr) * n + x0, k, y0 + rr, cur[k], ring + (sc * RW + rr + 1) * n,
+                        ring + (sp * RW + rr + 1) * n, ring + (sm * RW + rr + 1) * n);
                 }
                 sm = sc;
             }
@@ -363,13 +419,42 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 Raw v[KS];
 #pragma unroll
                 for (int k = 0; k < KS; ++k)
-                    if (ty + k * rows_pass < TY) v[k] = load(z * n2 + (y0 + ty + k * rows_pass) * n + tx);
+                    if (ty + k * RP < TY) v[k] = load(z * n2 + (y0 + ty + k * RP) * n + x0);
 #pragma unroll
                 for (int k = 0; k < KS; ++k)
-                    if (ty + k * rows_pass < TY) fn(z * n2 + (y0 + ty + k * rows_pass) * n + tx, v[k]);
+                    if (ty + k * RP < TY) fn(z * n2 + (y0 + ty + k * RP) * n + x0, v[k]);
             }
         }
     };
+    // The 7-point operand values of the W points from ring rows (vector loads).
+    struct Nb7 { Vec<KT, W> c, xp, xm, yp, ym, zp, zm; };
+    auto nb7 = [&](const KT* rowc, const KT* rowzp, const KT* rowzm) -> Nb7 {
+        Nb7 o;
+        o.c = vload<KT, W>(rowc + x0);
+        shift(rowc, o.c, o.xp, o.xm);
+        o.yp = vload<KT, W>(rowc + n + x0);
+        o.ym = vload<KT, W>(rowc - n + x0);
+        o.zp = vload<KT, W>(rowzp + x0);
+        o.zm = vload<KT, W>(rowzm + x0);
+        return o;
+    };
+    // A = I + dt L at the W points of row slot k
+    auto applyA = [&](int k, const Vec<KT, W>& c, const Vec<KT, W>& xp, const Vec<KT, W>& xm,
+                      const Vec<KT, W>& yp, const Vec<KT, W>& ym, const Vec<KT, W>& zp,
+                      const Vec<KT, W>& zm) -> Vec<KT, W> {
+        const KT ax = kx_y[k] + kx_z;
+        Vec<KT, W> o;
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const KT ay = ky_x[e] + ky_z;
+            const KT az = kz_x[e] + kz_y[k];
+            o.v[e] = c0 * c.v[e] + (ax - c1) * xp.v[e] - (ax + c1) * xm.v[e] + (ay - c1) * yp.v[e] -
+                     (ay + c1) * ym.v[e] + (az - c1) * zp.v[e] - (az + c1) * zm.v[e];
+        }
+        return o;
+    };
+    using VK = Vec<KT, W>;
+    using VD = Vec<double, W>;
 
     for (int b = g; b < a.B; b += a.numGroups) {
         const double* u_in = a.u_in + (size_t)b * Ng;
@@ -391,26 +476,55 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             {
                 Acc<KT, 2> acc;
                 acc.init();
-                march(ringd,
-                      [&](int i) -> RawSetup<KT> { return {P[i], use_d ? delta[i] : (KT)0}; },
-                      [&](const RawSetup<KT>& v) -> double { return v.u + (double)v.d; },
-                      [&](int i) -> double { return fp ? fp[i] : 0.0; },
-                      [&](int i, int, int y, int, double fi, double uc, double uxp, double uxm,
-                          double uyp, double uym, double uzp, double uzm) {
-                          if (Wt) Wt[i] = uc;
-                          if (snap_j) snap_j[i] = uc;
-                          const double bx = tabd[TXY * n + y] + dx_z;
-                          const double by = dy_x + dy_z;
-                          const double bz = dz_x + tabd[TZY * n + y];
-                          const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
-                          const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc;
-                          const double Lu = adv * inv2h - epsh2 * lap;
-                          const KT rk = (KT)(dt * (fi - Lu));
-                          r[i] = rk;
-                          rh[i] = rk;
-                          const double bi = uc + dt * fi;
-                          acc.f[0] += rk * rk;
-                          acc.f[1] += (KT)(bi * bi);
+                march(false, ringd,
+                      [&](int i) -> RawSetup<KT, W> {
+                          RawSetup<KT, W> o;
+                          o.u = vload<double, W>(P + i);
+                          if (use_d) o.d = vload<KT, W>(delta + i);
+                          else {
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                          }
+                          return o;
+                      },
+                      [&](const RawSetup<KT, W>& v) -> VD {
+                          VD o;
+#pragma unroll
+                          for (int e = 0; e < W; ++e) o.v[e] = v.u.v[e] + (double)v.d.v[e];
+                          return o;
+                      },
+                      [&](int) -> NoOwn { return NoOwn{}; },
+                      [&](int i, int, int y, const NoOwn&, const double* rowc, const double* rowzp,
+                          const double* rowzm) {
+                          const int z = i / n2;
+                          const double bx = tabd[TXY * n + y] + tabd[TXZ * n + z];
+                          const double byz = tabd[TYZ * n + z], bzy = tabd[TZY * n + y];
+                          // one point at a time: the FP64 stencil of all W points at once
+                          // would raise the register count of the whole kernel
+#pragma unroll 1
+                          for (int e = 0; e < W; ++e) {
+                              const int x = x0 + e;
+                              const int xp = (e == W - 1) ? xr : x + 1;
+                              const int xm = (e == 0) ? xl : x - 1;
+                              const double c = rowc[x];
+                              const double uxp = rowc[xp], uxm = rowc[xm];
+                              const double uyp = rowc[n + x], uym = rowc[x - n];
+                              const double uzp = rowzp[x], uzm = rowzm[x];
+                              const double by = tabd[TYX * n + x] + byz;
+                              const double bz = tabd[TZX * n + x] + bzy;
+                              const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
+                              const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * c;
+                              const double Lu = adv * inv2h - epsh2 * lap;
+                              const double fi = fp ? fp[i + e] : 0.0;
+                              const KT rk = (KT)(dt * (fi - Lu));
+                              if (Wt) Wt[i + e] = c;
+                              if (snap_j) snap_j[i + e] = c;
+                              r[i + e] = rk;
+                              rh[i + e] = rk;
+                              const double bi = c + dt * fi;
+                              acc.f[0] += rk * rk;
+                              acc.f[1] += (KT)(bi * bi);
+                          }
                           acc.tick();
                       });
                 acc.flush();
@@ -441,18 +555,34 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                     const bool first = (it == 1);
                     Acc<KT, 1> acc;
                     acc.init();
-                    march(ringk,
-                          [&](int i) -> RawP<KT> {
-                              return first ? RawP<KT>{r[i], (KT)0, (KT)0} : RawP<KT>{r[i], po[i], vo[i]};
+                    march(true, ringk,
+                          [&](int i) -> RawP<KT, W> {
+                              RawP<KT, W> o;
+                              o.r = vload<KT, W>(r + i);
+                              if (!first) {
+                                  o.p = vload<KT, W>(po + i);
+                                  o.v = vload<KT, W>(vo + i);
+                              } else {
+#pragma unroll
+                                  for (int e = 0; e < W; ++e) { o.p.v[e] = (KT)0; o.v.v[e] = (KT)0; }
+                              }
+                              return o;
                           },
-                          [&](const RawP<KT>& v) -> KT { return v.r + bk * (v.p - ok * v.v); },
-                          [&](int i) -> KT { return rh[i]; },
-                          [&](int i, int k, int, int, KT rhv, KT pc, KT pxp, KT pxm, KT pyp, KT pym,
-                              KT pzp, KT pzm) {
-                              const KT av = applyA(k, pc, pxp, pxm, pyp, pym, pzp, pzm);
-                              pn[i] = pc;
-                              vn[i] = av;
-                              acc.f[0] += rhv * av;
+                          [&](const RawP<KT, W>& v) -> VK {
+                              VK o;
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.v[e] = v.r.v[e] + bk * (v.p.v[e] - ok * v.v.v[e]);
+                              return o;
+                          },
+                          [&](int i) -> VK { return vload<KT, W>(rh + i); },
+                          [&](int i, int k, int, const VK& rhv, const KT* rowc, const KT* rowzp,
+                              const KT* rowzm) {
+                              const Nb7 q7 = nb7(rowc, rowzp, rowzm);
+                              const VK av = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm);
+                              vstore(pn + i, q7.c);
+                              vstore(vn + i, av);
+#pragma unroll
+                              for (int e = 0; e < W; ++e) acc.f[0] += rhv.v[e] * av.v[e];
                               acc.tick();
                           });
                     acc.flush();
@@ -474,17 +604,26 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                     const KT al = (KT)alpha;
                     Acc<KT, 3> acc;
                     acc.init();
-                    march(ringk,
-                          [&](int i) -> RawS<KT> { return {r[i], vn[i]}; },
-                          [&](const RawS<KT>& v) -> KT { return v.r - al * v.v; },
-                          [&](int) -> int { return 0; },
-                          [&](int i, int k, int, int, int, KT sc_, KT sxp, KT sxm, KT syp, KT sym,
-                              KT szp, KT szm) {
-                              const KT tv = applyA(k, sc_, sxp, sxm, syp, sym, szp, szm);
-                              t[i] = tv;
-                              acc.f[0] += tv * sc_;
-                              acc.f[1] += tv * tv;
-                              acc.f[2] += sc_ * sc_;
+                    march(true, ringk,
+                          [&](int i) -> RawS<KT, W> { return {vload<KT, W>(r + i), vload<KT, W>(vn + i)}; },
+                          [&](const RawS<KT, W>& v) -> VK {
+                              VK o;
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.v[e] = v.r.v[e] - al * v.v.v[e];
+                              return o;
+                          },
+                          [&](int) -> NoOwn { return NoOwn{}; },
+                          [&](int i, int k, int, const NoOwn&, const KT* rowc, const KT* rowzp,
+                              const KT* rowzm) {
+                              const Nb7 q7 = nb7(rowc, rowzp, rowzm);
+                              const VK tv = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm);
+                              vstore(t + i, tv);
+#pragma unroll
+                              for (int e = 0; e < W; ++e) {
+                                  acc.f[0] += tv.v[e] * q7.c.v[e];
+                                  acc.f[1] += tv.v[e] * tv.v[e];
+                                  acc.f[2] += q7.c.v[e] * q7.c.v[e];
+                              }
                               acc.tick();
                           });
                     acc.flush();
@@ -516,23 +655,51 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                     Acc<KT, 2> acc;
                     acc.init();
                     if (upd_r) {
-                        struct R6 { KT d, p, r, v, t, h; };
-                        owned([&](int i) -> R6 {
-                                  return {first ? (KT)0 : delta[i], pn[i], r[i], vn[i], t[i], rh[i]};
+                        owned([&](int i) -> Raw6<KT, W> {
+                                  Raw6<KT, W> o;
+                                  if (!first) o.d = vload<KT, W>(delta + i);
+                                  else {
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                                  }
+                                  o.p = vload<KT, W>(pn + i);
+                                  o.r = vload<KT, W>(r + i);
+                                  o.v = vload<KT, W>(vn + i);
+                                  o.t = vload<KT, W>(t + i);
+                                  o.h = vload<KT, W>(rh + i);
+                                  return o;
                               },
-                              [&](int i, const R6& v) {
-                                  const KT sc_ = v.r - al * v.v;
-                                  delta[i] = v.d + al * v.p + om * sc_;
-                                  const KT rn = sc_ - om * v.t;
-                                  r[i] = rn;
-                                  acc.f[0] += v.h * rn;
-                                  acc.f[1] += rn * rn;
+                              [&](int i, const Raw6<KT, W>& v) {
+                                  VK dn, rn;
+#pragma unroll
+                                  for (int e = 0; e < W; ++e) {
+                                      const KT sc_ = v.r.v[e] - al * v.v.v[e];
+                                      dn.v[e] = v.d.v[e] + al * v.p.v[e] + om * sc_;
+                                      rn.v[e] = sc_ - om * v.t.v[e];
+                                      acc.f[0] += v.h.v[e] * rn.v[e];
+                                      acc.f[1] += rn.v[e] * rn.v[e];
+                                  }
+                                  vstore(delta + i, dn);
+                                  vstore(r + i, rn);
                                   acc.tick();
                               });
                     } else {
-                        struct R2 { KT d, p; };
-                        owned([&](int i) -> R2 { return {first ? (KT)0 : delta[i], pn[i]}; },
-                              [&](int i, const R2& v) { delta[i] = v.d + al * v.p; });
+                        owned([&](int i) -> RawP2<KT, W> {
+                                  RawP2<KT, W> o;
+                                  if (!first) o.d = vload<KT, W>(delta + i);
+                                  else {
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                                  }
+                                  o.p = vload<KT, W>(pn + i);
+                                  return o;
+                              },
+                              [&](int i, const RawP2<KT, W>& v) {
+                                  VK dn;
+#pragma unroll
+                                  for (int e = 0; e < W; ++e) dn.v[e] = v.d.v[e] + al * v.p.v[e];
+                                  vstore(delta + i, dn);
+                              });
                     }
                     acc.flush();
                     block_sum<2>(acc.d, sh.red);
@@ -567,12 +734,22 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                                  ? snap_b + (size_t)(S / a.dM) * Ng : nullptr;
             double* outp = a.u_out + (size_t)b * Ng;
             const bool dv = dvalid;
-            struct RF { double u; KT d; };
-            owned([&](int i) -> RF { return {P[i], dv ? delta[i] : (KT)0}; },
-                  [&](int i, const RF& v) {
-                      const double u = v.u + (double)v.d;
-                      outp[i] = u;
-                      if (snap_S) snap_S[i] = u;
+            owned([&](int i) -> RawF<KT, W> {
+                      RawF<KT, W> o;
+                      o.u = vload<double, W>(P + i);
+                      if (dv) o.d = vload<KT, W>(delta + i);
+                      else {
+#pragma unroll
+                          for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                      }
+                      return o;
+                  },
+                  [&](int i, const RawF<KT, W>& v) {
+                      VD u;
+#pragma unroll
+                      for (int e = 0; e < W; ++e) u.v[e] = v.u.v[e] + (double)v.d.v[e];
+                      vstore(outp + i, u);
+                      if (snap_S) vstore(snap_S + i, u);
                   });
         }
         if (q == 0 && threadIdx.x == 0) {
@@ -586,61 +763,63 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     }
 }
 
-int fine_block_threads(int n) {
-    const int rows = n >= 256 ? 1 : 256 / n;
-    return n * rows;
+// ------------------------------------------------------------------------------------
+// Launch geometry.  W = 4 points per thread when n % 4 == 0, else 1.  A row has n/W
+// lanes; RP rows per pass of the CTA is the largest divisor of n with RP * n/W <= 256;
+// a tile has TY = KS * RP rows (KS in {1, 2}), its 4-plane FP64 ring within 64 KB.
+struct FineGeom {
+    int W, lanes, RP, TY, KS, KF, threads;
+    size_t smem;
+};
+
+static FineGeom fine_geom(int n, bool fp32) {
+    FineGeom g{};
+    g.W = (n % 4 == 0) ? 4 : 1;
+    g.lanes = n / g.W;
+    g.RP = 1;
+    for (int rp = 1; rp <= n; ++rp)
+        if (n % rp == 0 && rp * g.lanes <= 256) g.RP = rp;
+    g.KS = 1;
+    if (n % (2 * g.RP) == 0 && 2 * g.RP <= 16 && (size_t)4 * (2 * g.RP + 2) * n * 8 <= 64 * 1024) g.KS = 2;
+    g.TY = g.KS * g.RP;
+    g.KF = (g.TY + 2 + g.RP - 1) / g.RP;
+    g.threads = (g.lanes * g.RP + 31) / 32 * 32;   // whole warps (full-mask shuffles)
+    const size_t tabs = ((size_t)6 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 31) / 32 * 32;
+    g.smem = tabs + (size_t)4 * (g.TY + 2) * n * sizeof(double);
+    return g;
 }
 
-// Rows per tile: all of them for n <= 16; otherwise the largest divisor of n up to 8
-// whose 4-plane FP64 ring (TY + 2 rows) fits in 48 KB (more rows per thread raise the
-// register count past two resident CTAs per SM).
-int fine_tile_rows(int n) {
-    if (n <= 16) return n;
-    int best = 1;
-    for (int ty = 1; ty <= 8; ++ty)
-        if (n % ty == 0 && (size_t)4 * (ty + 2) * n * sizeof(double) <= 48 * 1024) best = ty;
-    return best;
-}
+int fine_block_threads(int n) { return fine_geom(n, true).threads; }
+int fine_tile_rows(int n) { return fine_geom(n, true).TY; }
 
-static size_t fine_smem(int n, bool fp32) {
-    const size_t tabs = ((size_t)6 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 15) / 16 * 16;
-    return tabs + (size_t)4 * (fine_tile_rows(n) + 2) * n * sizeof(double);
-}
-
-// Compile-time row counts per thread for the supported (KF, KS) shapes.
 using FineFn = void (*)(FineArgs);
-template <typename KT>
+template <typename KT, int W>
 static FineFn fine_fn(int KF, int KS) {
-#define PR_FINE_CASE(F, S_) if (KF <= F && KS <= S_) return fine_kernel<KT, F, S_>;
-    PR_FINE_CASE(1, 1)
+#define PR_FINE_CASE(F, S_) if (KF <= F && KS <= S_) return fine_kernel<KT, W, F, S_>;
     PR_FINE_CASE(2, 1)
+    PR_FINE_CASE(3, 1)
     PR_FINE_CASE(3, 2)
-    PR_FINE_CASE(5, 4)
-    PR_FINE_CASE(6, 4)
-    PR_FINE_CASE(9, 8)
-    PR_FINE_CASE(18, 16)
+    PR_FINE_CASE(4, 2)
 #undef PR_FINE_CASE
     return nullptr;
 }
 
 static FineFn fine_select(int n, bool fp32) {
-    const int rows_pass = fine_block_threads(n) / n;
-    const int TY = fine_tile_rows(n);
-    const int KF = (TY + 2 + rows_pass - 1) / rows_pass;
-    const int KS = (TY + rows_pass - 1) / rows_pass;
-    return fp32 ? fine_fn<float>(KF, KS) : fine_fn<double>(KF, KS);
+    const FineGeom g = fine_geom(n, fp32);
+    if (g.W == 4) return fp32 ? fine_fn<float, 4>(g.KF, g.KS) : fine_fn<double, 4>(g.KF, g.KS);
+    return fp32 ? fine_fn<float, 1>(g.KF, g.KS) : fine_fn<double, 1>(g.KF, g.KS);
 }
 
 int fine_max_ctas(int n, bool fp32, int ctas_per_sm) {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int threads = fine_block_threads(n);
-    const size_t smem = fine_smem(n, fp32);
+    const FineGeom geo = fine_geom(n, fp32);
     FineFn fn = fine_select(n, fp32);
     if (!fn) return 1;
-    if (smem > 48 * 1024) cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    if (geo.smem > 48 * 1024)
+        cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, geo.threads, geo.smem);
     if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
     return std::max(1, occ) * std::max(1, sms);
 }
@@ -651,8 +830,10 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     if (n > 256 || n < 4) return cudaErrorInvalidValue;
     FineFn fn = fine_select(n, fp32);
     if (!fn) return cudaErrorInvalidValue;
+    const FineGeom geo = fine_geom(n, fp32);
     const int max_ctas = fine_max_ctas(n, fp32, ctas_per_sm);
-    a.TY = fine_tile_rows(n);
+    a.TY = geo.TY;
+    a.RP = geo.RP;
     a.NY = n / a.TY;
     // CTAs per subinterval: as many as fit beside the other active subintervals, a whole
     // number of slabs per y-block column (one tile per CTA), at most one slab per plane
@@ -671,10 +852,8 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     a.G = G;
     a.numGroups = groups;
     const int grid = G * groups;
-    const int threads = fine_block_threads(n);
-    const size_t smem = fine_smem(n, fp32);
     void* args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(threads), args, smem, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(geo.threads), args, geo.smem, st);
     ++g_launch_count;
     return e;
 }

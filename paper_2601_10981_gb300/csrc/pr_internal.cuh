@@ -142,6 +142,7 @@ struct FineArgs {
     int G;              // CTAs per group
     int numGroups;
     int TY, NY, NZ;     // tiles of a subinterval: NY blocks of TY rows x NZ slabs of planes
+    int RP;             // rows per pass of a CTA (threads = n/W lanes x RP, rounded to warps)
     double tol;
     int maxit;
     long long spin_limit;
