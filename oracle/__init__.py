@@ -13,7 +13,8 @@ fusion.  Modules:
   (the FD analogue of the P1 FEM of Sec. 2.2), velocity fields of Sec. 4.
 * ``fine``           - implicit Euler fine propagator, eq. (semi-dis-eq)/(algform), with a
   textbook BiCGStab or a dense LU solve per step.
-* ``pod``            - POD_Mode (Algorithm 1) and the two-level POD of Case II, eq. (W^k_n).
+* ``pod``            - POD_Mode (Algorithm 1) with one Cholesky QR re-orthonormalisation,
+  and the two-level POD of Case II, eq. (W^k_n).
 * ``coarse``         - the Galerkin-reduced coarse propagator, eqs. (eq8)/(eq00)/(eq13), and
   the augmentation of eqs. (eqaug)/(eq12).
 * ``parareal``       - Algorithm 2 with the update of eq. (formula4), the sequential fine
@@ -26,14 +27,14 @@ see ``tests/test_oracle_*.py``.
 from .discretisation import (Grid, velocity, apply_L, apply_LT, assemble_L_dense,
                              make_operator)
 from .fine import bicgstab, implicit_euler_step, fine_propagate
-from .pod import pod_mode, cholqr2, level2_blocks
+from .pod import pod_mode, cholqr, level2_blocks
 from .coarse import coarse_propagate, augment, galerkin_project
 from .parareal import Params, derive_params, iteration0, parareal, sequential_fine, rel_l2
 
 __all__ = [
     "Grid", "velocity", "apply_L", "apply_LT", "assemble_L_dense", "make_operator",
     "bicgstab", "implicit_euler_step", "fine_propagate",
-    "pod_mode", "cholqr2", "level2_blocks",
+    "pod_mode", "cholqr", "level2_blocks",
     "coarse_propagate", "augment", "galerkin_project",
     "Params", "derive_params", "iteration0", "parareal", "sequential_fine", "rel_l2",
 ]

@@ -6,8 +6,10 @@ POD_Mode(W, gamma) (Sec. 2.3, Case I, and Algorithm 1), with M = I (reading R1):
      (the paper sums square roots of the eigenvalues; kept as printed, reading R6);
   3. R_tilde = first m columns of R, r_i = W y_i / sqrt(lambda_i).
 Readings: "lambda = 0" means lambda_i <= tau * lambda_1 (R5); an optional cap bounds m
-(R6); the returned basis is re-orthonormalised by CholQR twice, which keeps its span
-(R7).
+(R6); the returned basis is re-orthonormalised by one Cholesky QR pass, which keeps its
+span (R7).  R = W Y Lambda^{-1/2} is orthonormal up to eps * lambda_1 / lambda_m; one
+Cholesky QR pass brings that to rounding level, its error being eps * cond(R)^2 with
+cond(R) ~ 1.
 
 Case II level 2, eq. (W^k_n): the level-1 bases of the m_l left neighbours, of this
 subinterval and of the p previous iterations are concatenated and compressed again
@@ -32,9 +34,9 @@ def pod_select(lam: np.ndarray, gamma: float, tau: float, cap: int = 0) -> int:
     return min(m, r)
 
 
-def cholqr2(R: np.ndarray) -> np.ndarray:
-    """Two passes of Cholesky QR: R <- R L^{-T} with R^T R = L L^T (reading R7)."""
-    for _ in range(2):
+def cholqr(R: np.ndarray, passes: int = 1) -> np.ndarray:
+    """Cholesky QR: R <- R L^{-T} with R^T R = L L^T (reading R7), `passes` times."""
+    for _ in range(passes):
         G = R.T @ R
         Lc = np.linalg.cholesky(G)
         R = np.linalg.solve(Lc, R.T).T     # R L^{-T}
@@ -53,7 +55,7 @@ def pod_mode(W: np.ndarray, gamma: float, cap: int = 0, tau: float = 1e-13,
         return np.zeros((W.shape[0], 0)), 0, lam
     R = W @ Y[:, :m] / np.sqrt(lam[:m])
     if reorth:
-        R = cholqr2(R)
+        R = cholqr(R)
     return R, m, lam
 
 

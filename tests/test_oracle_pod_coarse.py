@@ -8,7 +8,7 @@ import oracle as O
 from oracle.coarse import augment, coarse_propagate, galerkin_project
 from oracle.discretisation import Operator
 from oracle.fine import fine_propagate
-from oracle.pod import cholqr2, level2_blocks, pod_mode, pod_select
+from oracle.pod import cholqr, level2_blocks, pod_mode, pod_select
 from pr_inputs import Flow, forcing, initial_state
 
 
@@ -71,11 +71,24 @@ def test_criterion_zero_snapshots():
     assert pod_select(np.zeros(5), 0.9, 1e-13) == 0
 
 
-def test_cholqr2_keeps_span_and_orthonormalises():
+def test_cholqr_keeps_span_and_orthonormalises():
     R0 = rng(6).standard_normal((300, 7)) @ np.triu(rng(7).standard_normal((7, 7)) + 3 * np.eye(7))
-    Q = cholqr2(R0)
+    Q = cholqr(R0, passes=2)
     assert np.max(np.abs(Q.T @ Q - np.eye(7))) < 1e-14
     assert np.linalg.norm(Q @ (Q.T @ R0) - R0) < 1e-12 * np.linalg.norm(R0)
+
+
+def test_one_cholqr_pass_orthonormalises_pod_projections():
+    # R = W Y Lambda^{-1/2} of snapshots with a 1e-11 eigenvalue ratio is orthonormal only
+    # to ~1e-7; one Cholesky QR pass restores rounding-level orthonormality (reading R7)
+    A = np.linalg.qr(rng(8).standard_normal((2000, 6)))[0] @ np.diag(np.logspace(0, -5.5, 6))
+    W = A @ np.linalg.qr(rng(9).standard_normal((6, 6)))[0]
+    lam, Y = np.linalg.eigh(W.T @ W)
+    o = np.argsort(lam)[::-1]
+    R = W @ Y[:, o] / np.sqrt(lam[o])
+    assert np.max(np.abs(R.T @ R - np.eye(6))) > 1e-9
+    Q = cholqr(R)
+    assert np.max(np.abs(Q.T @ Q - np.eye(6))) < 1e-14
 
 
 def test_level2_blocks_order_and_missing_blocks():
