@@ -70,6 +70,7 @@ struct pr_ctx {
     double* tab = nullptr;
     double* u0 = nullptr;
     double* f = nullptr;
+    float* f32 = nullptr;   // forcing rounded to float (FP32-mode fine sweep)
     double* Ubuf[2] = {nullptr, nullptr};
     int cur = 0;  // Ubuf[cur] holds the latest iterate
     double* Fend = nullptr;
@@ -83,7 +84,7 @@ struct pr_ctx {
     int* m2 = nullptr;
     int* mop = nullptr;            // POD dimensions of pr_op_pod
     char* LR = nullptr;
-    char* scr[2] = {nullptr, nullptr};
+    char* scr[1] = {nullptr};
     double* Mr = nullptr;
     double* Lr = nullptr;
     double* M0 = nullptr;
@@ -162,6 +163,7 @@ size_t plan(pr_ctx* c, char* base) {
     c->tab = b.take<double>(6 * (size_t)c->n);
     c->u0 = b.take<double>(Ng);
     c->f = b.take<double>(Ng);
+    c->f32 = b.take<float>(Ng);
     c->Ubuf[0] = b.take<double>((size_t)(N + 1) * Ng);
     c->Ubuf[1] = b.take<double>((size_t)(N + 1) * Ng);
     c->Fend = b.take<double>((size_t)N * Ng);
@@ -177,7 +179,6 @@ size_t plan(pr_ctx* c, char* base) {
     c->mop = b.take<int>(N + 1);
     c->LR = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
     c->scr[0] = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
-    c->scr[1] = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
     c->Mr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
     c->Lr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
     c->M0 = b.take<double>((size_t)c->mcap0 * c->mcap0);
@@ -245,6 +246,7 @@ pr_status init_ws(pr_ctx* c) {
     PR_CUDA(cudaMemsetAsync(c->m1[1], 0, sizeof(int) * c->N, st));
     PR_CUDA(cudaMemsetAsync(c->m2, 0, sizeof(int) * ((size_t)c->N + 1), st));
     PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, st));
+    PR_CUDA(cudaMemsetAsync(c->f32, 0, sizeof(float) * c->Ng, st));
     std::vector<int> ones(c->N + 1, 1);
     PR_CUDA(cudaMemcpy(c->ones, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice));
     int cn[8] = {c->ns, c->ns0, 0, 1, 0, 0, 0, 0};
@@ -360,40 +362,32 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     ta.maxKIN = maxK;
     ta.maxKOUT = mmax;
     PR_CUDA(launch_tsmm(ta, in_f32, f32, st));
-    // CholQR twice: scr[0] -> scr[1] -> dest
-    for (int pass = 0; pass < 2; ++pass) {
-        char* src = c->scr[pass];
-        pr_status s = cols_contig(c, src, (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB, c->esz);
-        if (s != PR_OK) return s;
-        GramArgs gb = ga;
-        gb.colsA = c->colsB;
-        gb.colsB = c->colsB;
-        gb.KA = c->KB;
-        gb.KB = c->KB;
-        gb.maxKA = mmax;
-        gb.maxKB = mmax;
-        gb.ldG = mmax;
-        gb.ldG_b = (long long)mmax * mmax;
-        PR_CUDA(launch_gram(gb, f32, f32, st));
-        PR_CUDA(launch_chol_inv(c->gout, mmax, (long long)mmax * mmax, m_dest, mmax, B, c->X, mmax,
-                                (long long)mmax * mmax, c->derr, st));
-        TsmmArgs tb = ta;
-        tb.colsIn = c->colsB;
-        tb.KIN = c->KB;
-        tb.KOUT = m_dest;
-        tb.C = c->X;
-        tb.ldC = mmax;
-        tb.ldC_b = (long long)mmax * mmax;
-        tb.maxKIN = mmax;
-        if (pass == 0) {
-            tb.out = c->scr[1];
-            tb.ld_out_b = (long long)mmax * c->Ng;
-        } else {
-            tb.out = dest;
-            tb.ld_out_b = (long long)dest_bstride_elems;
-        }
-        PR_CUDA(launch_tsmm(tb, f32, f32, st));
-    }
+    // one Cholesky QR pass (reading R7): scr[0] -> dest
+    pr_status s = cols_contig(c, c->scr[0], (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB, c->esz);
+    if (s != PR_OK) return s;
+    GramArgs gb = ga;
+    gb.colsA = c->colsB;
+    gb.colsB = c->colsB;
+    gb.KA = c->KB;
+    gb.KB = c->KB;
+    gb.maxKA = mmax;
+    gb.maxKB = mmax;
+    gb.ldG = mmax;
+    gb.ldG_b = (long long)mmax * mmax;
+    PR_CUDA(launch_gram(gb, f32, f32, st));
+    PR_CUDA(launch_chol_inv(c->gout, mmax, (long long)mmax * mmax, m_dest, mmax, B, c->X, mmax,
+                            (long long)mmax * mmax, c->derr, st));
+    TsmmArgs tb = ta;
+    tb.colsIn = c->colsB;
+    tb.KIN = c->KB;
+    tb.KOUT = m_dest;
+    tb.C = c->X;
+    tb.ldC = mmax;
+    tb.ldC_b = (long long)mmax * mmax;
+    tb.maxKIN = mmax;
+    tb.out = dest;
+    tb.ld_out_b = (long long)dest_bstride_elems;
+    PR_CUDA(launch_tsmm(tb, f32, f32, st));
     return PR_OK;
 }
 
@@ -444,6 +438,7 @@ pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int
     a.n_snap = snap ? n_snap : 0;
     a.dt = c->dt;
     a.f = c->has_f ? c->f : nullptr;
+    a.f32 = c->has_f ? c->f32 : nullptr;
     a.B = B;
     a.u_in = u_in;
     a.u_out = u_out;
@@ -672,6 +667,7 @@ pr_status pr_set_initial(pr_ctx* c, const double* u0, const double* f) {
     PR_CUDA(cudaMemcpyAsync(c->u0, u0, sizeof(double) * c->Ng, cudaMemcpyHostToDevice, c->st));
     if (f) PR_CUDA(cudaMemcpyAsync(c->f, f, sizeof(double) * c->Ng, cudaMemcpyHostToDevice, c->st));
     else PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, c->st));
+    PR_CUDA(launch_to_float(c->f, c->f32, c->Ng, c->st));
     PR_CUDA(cudaStreamSynchronize(c->st));
     c->has_f = f != nullptr;
     c->initial_set = true;

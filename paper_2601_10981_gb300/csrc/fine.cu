@@ -13,8 +13,13 @@
 // Each step is solved for the increment delta = u_j - u_{j-1} ("delta form"):
 //     (I + dt L) delta = dt (f - L u_{j-1}),   delta_0 = 0,
 // which generates the same Krylov iterates as BiCGStab on the paper's system started
-// from u_{j-1}.  The state u stays FP64; delta and the Krylov vectors are KT (double in
-// the FP64 mode, float in the FP32 mode).  The residual of the state is formed in FP64.
+// from u_{j-1}.  delta and the Krylov vectors are KT (double in the FP64 mode, float in
+// the FP32 mode).  The FP64 mode keeps the state u in FP64.  The FP32 mode keeps it as an
+// unevaluated sum hi + lo of two floats (8 bytes, ~48 significant bits) and runs on the
+// FP32 pipe only: GB300 issues FP64 arithmetic at 1/64 of the FP32 rate, so an FP64
+// residual stencil would cost more than all of the FP32 Krylov work.  Its residual uses
+// differences of neighbouring hi parts, which are exact when the neighbours are within a
+// factor of two (Sterbenz), so r keeps FP32 accuracy relative to the differences.
 // Snapshots are written in FP64 in both modes: the POD criterion keeps modes down to
 // lambda/lambda_1 ~ 1e-12, which FP32-rounded snapshots cannot resolve.
 // Stopping rule: ||r|| <= tol ||u_{j-1} + dt f||.
@@ -62,6 +67,18 @@ __global__ void tables_kernel(int kind, double A, double B, double C, int k, dou
 cudaError_t launch_tables(const pr_flow& flow, int n, double L, double* tab, cudaStream_t st) {
     tables_kernel<<<(n + 127) / 128, 128, 0, st>>>(flow.kind, flow.A, flow.B, flow.C, flow.k,
                                                    flow.b[0], flow.b[1], flow.b[2], n, L, tab);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+__global__ void to_float_kernel(const double* in, float* out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+cudaError_t launch_to_float(const double* in, float* out, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
     ++g_launch_count;
     return cudaGetLastError();
 }
@@ -197,6 +214,11 @@ __device__ __forceinline__ Vec<T, W> vload(const T* p) {
     if constexpr (W == 4 && sizeof(T) == 4) {
         const float4 q = *reinterpret_cast<const float4*>(p);
         o.v[0] = q.x; o.v[1] = q.y; o.v[2] = q.z; o.v[3] = q.w;
+    } else if constexpr (W == 4 && std::is_same<T, float2>::value) {
+        const float4 q0 = *reinterpret_cast<const float4*>(p);
+        const float4 q1 = *reinterpret_cast<const float4*>(p + 2);
+        o.v[0] = make_float2(q0.x, q0.y); o.v[1] = make_float2(q0.z, q0.w);
+        o.v[2] = make_float2(q1.x, q1.y); o.v[3] = make_float2(q1.z, q1.w);
     } else if constexpr (W == 4 && sizeof(T) == 8) {
         const double2 q0 = *reinterpret_cast<const double2*>(p);
         const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
@@ -211,6 +233,9 @@ template <typename T, int W>
 __device__ __forceinline__ void vstore(T* p, const Vec<T, W>& o) {
     if constexpr (W == 4 && sizeof(T) == 4) {
         *reinterpret_cast<float4*>(p) = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
+    } else if constexpr (W == 4 && std::is_same<T, float2>::value) {
+        *reinterpret_cast<float4*>(p) = make_float4(o.v[0].x, o.v[0].y, o.v[1].x, o.v[1].y);
+        *reinterpret_cast<float4*>(p + 2) = make_float4(o.v[2].x, o.v[2].y, o.v[3].x, o.v[3].y);
     } else if constexpr (W == 4 && sizeof(T) == 8) {
         *reinterpret_cast<double2*>(p) = make_double2(o.v[0], o.v[1]);
         *reinterpret_cast<double2*>(p + 2) = make_double2(o.v[2], o.v[3]);
@@ -220,14 +245,32 @@ __device__ __forceinline__ void vstore(T* p, const Vec<T, W>& o) {
     }
 }
 
+// Double-float state of the FP32 mode: u = hi + lo with |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ float2 df_split(double u) {
+    const float hi = __double2float_rn(u);
+    return make_float2(hi, __double2float_rn(u - (double)hi));
+}
+__device__ __forceinline__ double df_value(float2 u) { return (double)u.x + (double)u.y; }
+// (hi, lo) + d: TwoSum of hi and d (Knuth), then the renormalising FastTwoSum
+__device__ __forceinline__ float2 df_add(float2 u, float d) {
+    const float s = __fadd_rn(u.x, d);
+    const float bb = __fsub_rn(s, u.x);
+    const float e = __fadd_rn(__fsub_rn(u.x, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+    const float lo = __fadd_rn(u.y, e);
+    const float hi = __fadd_rn(s, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+
 // Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
-template <typename KT, int W> struct RawSetup { Vec<double, W> u; Vec<KT, W> d; };
+template <typename ST, typename KT, int W> struct RawSetup { Vec<ST, W> u; Vec<KT, W> d; };
 template <typename KT, int W> struct RawP { Vec<KT, W> r, p, v; };
 template <typename KT, int W> struct RawS { Vec<KT, W> r, v; };
-template <typename KT, int W> struct RawF { Vec<double, W> u; Vec<KT, W> d; };
+template <typename ST, typename KT, int W> struct RawF { Vec<ST, W> u; Vec<KT, W> d; };
 template <typename KT, int W> struct RawP2 { Vec<KT, W> d, p; };
 template <typename KT, int W> struct Raw6 { Vec<KT, W> d, p, r, v, t, h; };
 struct NoOwn {};
+// The 7-point values of W consecutive points: centre and the x, y, z neighbours.
+template <typename T, int W> struct Nb7 { Vec<T, W> c, xp, xm, yp, ym, zp, zm; };
 
 // KT: Krylov type.  W: points per thread along x.  KF: ring rows each thread fills per
 // plane (ceil((TY+2)/RP)).  KS: owned rows per thread per plane (TY/RP).
@@ -262,7 +305,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     KT* tabk = reinterpret_cast<KT*>(tabd + 6 * n);
     unsigned char* ring_raw = smem_raw + (((size_t)6 * n * (sizeof(double) + sizeof(KT)) + 31) / 32) * 32;
     double* ringd = reinterpret_cast<double*>(ring_raw);
+    float2* ringf = reinterpret_cast<float2*>(ring_raw);
     KT* ringk = reinterpret_cast<KT*>(ring_raw);
+    constexpr bool DF = std::is_same<KT, float>::value;   // double-float state
+    (void)ringd;
+    (void)ringf;
     for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) {
         const double v = a.g.tab[i];
         tabd[i] = v;
@@ -427,15 +474,15 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         }
     };
     // The 7-point operand values of the W points from ring rows (vector loads).
-    struct Nb7 { Vec<KT, W> c, xp, xm, yp, ym, zp, zm; };
-    auto nb7 = [&](const KT* rowc, const KT* rowzp, const KT* rowzm) -> Nb7 {
-        Nb7 o;
-        o.c = vload<KT, W>(rowc + x0);
+    auto nb7 = [&](const auto* rowc, const auto* rowzp, const auto* rowzm) {
+        using T = std::remove_const_t<std::remove_pointer_t<decltype(rowc)>>;
+        Nb7<T, W> o;
+        o.c = vload<T, W>(rowc + x0);
         shift(rowc, o.c, o.xp, o.xm);
-        o.yp = vload<KT, W>(rowc + n + x0);
-        o.ym = vload<KT, W>(rowc - n + x0);
-        o.zp = vload<KT, W>(rowzp + x0);
-        o.zm = vload<KT, W>(rowzm + x0);
+        o.yp = vload<T, W>(rowc + n + x0);
+        o.ym = vload<T, W>(rowc - n + x0);
+        o.zp = vload<T, W>(rowzp + x0);
+        o.zm = vload<T, W>(rowzm + x0);
         return o;
     };
     // A = I + dt L at the W points of row slot k
@@ -473,12 +520,12 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             if (snap_b && (j - 1) % a.dM == 0 && (j - 1) / a.dM < a.n_snap)
                 snap_j = snap_b + (size_t)((j - 1) / a.dM) * Ng;
             const double* fp = a.f;
-            {
-                Acc<KT, 2> acc;
-                acc.init();
+            Acc<KT, 2> acc;
+            acc.init();
+            if constexpr (!DF) {
                 march(false, ringd,
-                      [&](int i) -> RawSetup<KT, W> {
-                          RawSetup<KT, W> o;
+                      [&](int i) -> RawSetup<double, KT, W> {
+                          RawSetup<double, KT, W> o;
                           o.u = vload<double, W>(P + i);
                           if (use_d) o.d = vload<KT, W>(delta + i);
                           else {
@@ -487,7 +534,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return o;
                       },
-                      [&](const RawSetup<KT, W>& v) -> VD {
+                      [&](const RawSetup<double, KT, W>& v) -> VD {
                           VD o;
 #pragma unroll
                           for (int e = 0; e < W; ++e) o.v[e] = v.u.v[e] + (double)v.d.v[e];
@@ -527,6 +574,81 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           acc.tick();
                       });
+            } else {
+                // double-float state: the same residual, FP32 arithmetic only
+                const float2* Pf = (j <= 2) ? nullptr : reinterpret_cast<const float2*>(P);
+                float2* Wf = reinterpret_cast<float2*>(Wt);
+                const float* ff = a.f32;
+                const KT dtf = (KT)dt;
+                march(false, ringf,
+                      [&](int i) -> RawSetup<float2, KT, W> {
+                          RawSetup<float2, KT, W> o;
+                          if (Pf) o.u = vload<float2, W>(Pf + i);
+                          else {
+                              const VD ud = vload<double, W>(u_in + i);
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.u.v[e] = df_split(ud.v[e]);
+                          }
+                          if (use_d) o.d = vload<KT, W>(delta + i);
+                          else {
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                          }
+                          return o;
+                      },
+                      [&](const RawSetup<float2, KT, W>& v) -> Vec<float2, W> {
+                          Vec<float2, W> o;
+#pragma unroll
+                          for (int e = 0; e < W; ++e) o.v[e] = df_add(v.u.v[e], v.d.v[e]);
+                          return o;
+                      },
+                      [&](int) -> NoOwn { return NoOwn{}; },
+                      [&](int i, int k, int, const NoOwn&, const float2* rowc, const float2* rowzp,
+                          const float2* rowzm) {
+                          const auto q = nb7(rowc, rowzp, rowzm);
+                          VK fv;
+                          if (ff) fv = vload<KT, W>(ff + i);
+                          else {
+#pragma unroll
+                              for (int e = 0; e < W; ++e) fv.v[e] = (KT)0;
+                          }
+                          const KT ax = kx_y[k] + kx_z;
+                          VK rv;
+#pragma unroll
+                          for (int e = 0; e < W; ++e) {
+                              const float2 c = q.c.v[e], xp = q.xp.v[e], xm = q.xm.v[e];
+                              const float2 yp = q.yp.v[e], ym = q.ym.v[e], zp = q.zp.v[e], zm = q.zm.v[e];
+                              const KT ay = ky_x[e] + ky_z;
+                              const KT az = kz_x[e] + kz_y[k];
+                              // central differences and second differences of hi, then lo
+                              const KT dx = __fadd_rn(__fsub_rn(xp.x, xm.x), __fsub_rn(xp.y, xm.y));
+                              const KT dy = __fadd_rn(__fsub_rn(yp.x, ym.x), __fsub_rn(yp.y, ym.y));
+                              const KT dz = __fadd_rn(__fsub_rn(zp.x, zm.x), __fsub_rn(zp.y, zm.y));
+                              const KT sx = __fsub_rn(__fsub_rn(xp.x, c.x), __fsub_rn(c.x, xm.x));
+                              const KT sy = __fsub_rn(__fsub_rn(yp.x, c.x), __fsub_rn(c.x, ym.x));
+                              const KT sz = __fsub_rn(__fsub_rn(zp.x, c.x), __fsub_rn(c.x, zm.x));
+                              const KT lo = ((xp.y + xm.y) + (yp.y + ym.y) + (zp.y + zm.y)) - 6.0f * c.y;
+                              const KT lap = ((sx + sy) + sz) + lo;
+                              // r = dt (f - L u): dt b.grad(u) = a . (2h grad u), dt eps lap / h^2 = c1 lap
+                              const KT rk = dtf * fv.v[e] - (ax * dx + ay * dy + az * dz) + c1 * lap;
+                              rv.v[e] = rk;
+                              const KT bi = c.x + dtf * fv.v[e];
+                              acc.f[0] += rk * rk;
+                              acc.f[1] += bi * bi;
+                          }
+                          vstore(r + i, rv);
+                          vstore(rh + i, rv);
+                          if (Wf) vstore(Wf + i, q.c);
+                          if (snap_j) {
+                              VD sd;
+#pragma unroll
+                              for (int e = 0; e < W; ++e) sd.v[e] = df_value(q.c.v[e]);
+                              vstore(snap_j + i, sd);
+                          }
+                          acc.tick();
+                      });
+            }
+            {
                 acc.flush();
                 block_sum<2>(acc.d, sh.red);
                 if (threadIdx.x == 0) {
@@ -577,7 +699,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           [&](int i) -> VK { return vload<KT, W>(rh + i); },
                           [&](int i, int k, int, const VK& rhv, const KT* rowc, const KT* rowzp,
                               const KT* rowzm) {
-                              const Nb7 q7 = nb7(rowc, rowzp, rowzm);
+                              const auto q7 = nb7(rowc, rowzp, rowzm);
                               const VK av = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm);
                               vstore(pn + i, q7.c);
                               vstore(vn + i, av);
@@ -615,7 +737,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           [&](int) -> NoOwn { return NoOwn{}; },
                           [&](int i, int k, int, const NoOwn&, const KT* rowc, const KT* rowzp,
                               const KT* rowzm) {
-                              const Nb7 q7 = nb7(rowc, rowzp, rowzm);
+                              const auto q7 = nb7(rowc, rowzp, rowzm);
                               const VK tv = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm);
                               vstore(t + i, tv);
 #pragma unroll
@@ -734,23 +856,49 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                                  ? snap_b + (size_t)(S / a.dM) * Ng : nullptr;
             double* outp = a.u_out + (size_t)b * Ng;
             const bool dv = dvalid;
-            owned([&](int i) -> RawF<KT, W> {
-                      RawF<KT, W> o;
-                      o.u = vload<double, W>(P + i);
-                      if (dv) o.d = vload<KT, W>(delta + i);
-                      else {
+            if constexpr (!DF) {
+                owned([&](int i) -> RawF<double, KT, W> {
+                          RawF<double, KT, W> o;
+                          o.u = vload<double, W>(P + i);
+                          if (dv) o.d = vload<KT, W>(delta + i);
+                          else {
 #pragma unroll
-                          for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
-                      }
-                      return o;
-                  },
-                  [&](int i, const RawF<KT, W>& v) {
-                      VD u;
+                              for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                          }
+                          return o;
+                      },
+                      [&](int i, const RawF<double, KT, W>& v) {
+                          VD u;
 #pragma unroll
-                      for (int e = 0; e < W; ++e) u.v[e] = v.u.v[e] + (double)v.d.v[e];
-                      vstore(outp + i, u);
-                      if (snap_S) vstore(snap_S + i, u);
-                  });
+                          for (int e = 0; e < W; ++e) u.v[e] = v.u.v[e] + (double)v.d.v[e];
+                          vstore(outp + i, u);
+                          if (snap_S) vstore(snap_S + i, u);
+                      });
+            } else {
+                const float2* Pf = (S >= 2) ? reinterpret_cast<const float2*>(P) : nullptr;
+                owned([&](int i) -> RawF<float2, KT, W> {
+                          RawF<float2, KT, W> o;
+                          if (Pf) o.u = vload<float2, W>(Pf + i);
+                          else {
+                              const VD ud = vload<double, W>(u_in + i);
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.u.v[e] = df_split(ud.v[e]);
+                          }
+                          if (dv) o.d = vload<KT, W>(delta + i);
+                          else {
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                          }
+                          return o;
+                      },
+                      [&](int i, const RawF<float2, KT, W>& v) {
+                          VD u;
+#pragma unroll
+                          for (int e = 0; e < W; ++e) u.v[e] = df_value(df_add(v.u.v[e], v.d.v[e]));
+                          vstore(outp + i, u);
+                          if (snap_S) vstore(snap_S + i, u);
+                      });
+            }
         }
         if (q == 0 && threadIdx.x == 0) {
             a.status[b] = status;

@@ -131,6 +131,7 @@ struct FineArgs {
     int dM, n_snap;     // snapshot stride / count (n_snap = 0: none)
     double dt;          // fine step
     const double* f;    // forcing [Ng] or nullptr
+    const float* f32;   // the same rounded to float (FP32 mode), nullptr without forcing
     int B;              // subintervals in this launch
     const double* u_in; // [B][Ng]
     double* u_out;      // [B][Ng]
@@ -161,6 +162,9 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups,
 int fine_max_ctas(int n, bool fp32, int ctas_per_sm);
 int fine_tile_rows(int n);
 int fine_block_threads(int n);
+
+// out[i] = (float)in[i], i < n
+cudaError_t launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 
 cudaError_t launch_tables(const pr_flow& flow, int n, double L, double* tab,
                           cudaStream_t st);
