@@ -120,9 +120,7 @@ struct pr_ctx {
     double* cd = nullptr;
     double* cLd = nullptr;
     double* cLtd = nullptr;
-    double* cdots = nullptr;
     double* cpart = nullptr;
-    double* coef = nullptr;
     double* npart = nullptr;
     double* nout = nullptr;
     double* ref = nullptr;        // owned cudaMalloc
@@ -216,9 +214,7 @@ size_t plan(pr_ctx* c, char* base) {
     c->cd = b.take<double>(Ng);
     c->cLd = b.take<double>(Ng);
     c->cLtd = b.take<double>(Ng);
-    c->cdots = b.take<double>(1024);
     c->cpart = b.take<double>(coarse_part_doubles(Ng, c->mcap2));
-    c->coef = b.take<double>(64);
     c->npart = b.take<double>(norms_part_doubles(Ng, N + 1));
     c->nout = b.take<double>((size_t)4 * (N + 1));
     return b.off + 256;
@@ -827,9 +823,10 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
     return PR_OK;
 }
 
-static CoarseArgs coarse_args(pr_ctx* c) {
-    CoarseArgs a{};
+static CoarseSweepArgs coarse_args(pr_ctx* c) {
+    CoarseSweepArgs a{};
     a.g = grid_of(c);
+    a.ldM = c->mcap2;
     a.maxm = c->mcap2;
     a.dT = c->dT;
     a.Lc = c->Lc;
@@ -837,10 +834,9 @@ static CoarseArgs coarse_args(pr_ctx* c) {
     a.d = c->cd;
     a.Ld = c->cLd;
     a.Ltd = c->cLtd;
-    a.dots = c->cdots;
     a.part = c->cpart;
-    a.counter = c->counters + c->N + 16;
-    a.coef = c->coef;
+    a.bar = c->counters + c->N + 16;
+    a.spin_limit = c->o.spin_limit;
     a.err = c->derr;
     return a;
 }
@@ -854,18 +850,26 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
     PR_CUDA(cudaMemcpyAsync(Unew, Uold, sizeof(double) * (size_t)k * Ng, cudaMemcpyDeviceToDevice, c->st));
     PR_CUDA(cudaMemcpyAsync(Unew + (size_t)k * Ng, c->Fend + (size_t)(k - 1) * Ng, sizeof(double) * Ng,
                             cudaMemcpyDeviceToDevice, c->st));
-    CoarseArgs a = coarse_args(c);
-    for (int n = k; n < c->N; ++n) {
-        a.R = c->R2 + (size_t)n * c->mcap2 * Ng * c->esz;
-        a.m_ptr = c->m2 + n;
-        a.U = Unew + (size_t)n * Ng;
-        a.Up = Uold + (size_t)n * Ng;
-        a.F = c->Fend + (size_t)n * Ng;
-        a.out = Unew + (size_t)(n + 1) * Ng;
-        a.Mr = c->Mr + (size_t)n * c->mcap2 * c->mcap2;
-        a.Lr = c->Lr + (size_t)n * c->mcap2 * c->mcap2;
-        PR_CUDA(launch_coarse_update(a, false, c->st));
-    }
+    CoarseSweepArgs a = coarse_args(c);
+    a.n0 = k;
+    a.count = c->N - k;
+    a.U = Unew;
+    a.sU = Ng;
+    a.Up = Uold;
+    a.sUp = Ng;
+    a.F = c->Fend;
+    a.sF = Ng;
+    a.out = Unew + Ng;
+    a.sOut = Ng;
+    a.R = reinterpret_cast<const double*>(c->R2);
+    a.sR = (long long)c->mcap2 * Ng;
+    a.m = c->m2;
+    a.sm = 1;
+    a.Mr = c->Mr;
+    a.Lr = c->Lr;
+    a.sM = (long long)c->mcap2 * c->mcap2;
+    PR_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), c->st));
+    PR_CUDA(launch_coarse_sweep(a, c->st));
     c->cur = 1 - c->cur;
     c->k_done = k;
     c->phase = 0;
@@ -1209,16 +1213,19 @@ pr_status pr_op_coarse_update(pr_ctx* c, const void* d_R, int m, const double* d
         s = galerkin(c, (char*)d_R, (size_t)c->mcap2 * c->Ng, c->m2 + c->N, 1, c->mcap2, Mr, Lr);
         if (s != PR_OK) return s;
     }
-    CoarseArgs a = coarse_args(c);
-    a.R = d_R;
-    a.m_ptr = c->m2 + c->N;
+    CoarseSweepArgs a = coarse_args(c);
+    a.n0 = 0;
+    a.count = 1;
     a.U = d_U;
     a.Up = d_Uprev;
     a.F = d_F;
     a.out = d_out;
+    a.R = reinterpret_cast<const double*>(d_R);
+    a.m = c->m2 + c->N;
     a.Mr = Mr;
     a.Lr = Lr;
-    PR_CUDA(launch_coarse_update(a, false, c->st));
+    PR_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), c->st));
+    PR_CUDA(launch_coarse_sweep(a, c->st));
     return pr_sync(c);
 }
 

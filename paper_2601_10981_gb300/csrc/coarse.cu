@@ -1,6 +1,6 @@
 // Coarse propagator G in the augmented POD space and the parareal update of
-// eq. (formula4), for one subinterval at a time (the sweep over n is sequential,
-// Algorithm 2 and the remark after it).
+// eq. (formula4), swept over the subintervals in order (Algorithm 2 and the remark after
+// it: U^k_{n+1} needs U^k_n).
 //
 // For V = [R, d] with d~ = U - R R^T U orthogonalised once more against R and
 // d = d~ / ||d~|| (eqs. (eqaug), (eq12)), the bordered reduced matrices of eq. (eq13) are
@@ -10,15 +10,18 @@
 //     G(U) - G(P U') = V Phi^Lc Mv^{-1} V^T (U - U'),   Phi = (Mv + dT Lv)^{-1} Mv,
 // so the forcing cancels and one reduced propagation of the difference suffices.
 //
-// Passes over the grid (each a kernel; reductions are chunk partials summed in chunk
-// order by the last CTA, so results do not depend on scheduling):
-//   1  gram:     R^T U, R^T U'
-//   2  resid:    d~ = U - R c                       ; R^T d~, U.U
-//   3  reorth:   d~ -= R c2                         ; R^T d~, d~.d~, d~.U, d~.U'
-//   4  Ld:       L d~, L^T d~                       ; d~.L d~
-//   5  gram:     R^T L d~, R^T L^T d~
-//   6  small:    reduced solve (one CTA, FP64)
-//   7  update:   U^k_{n+1} = F_n + R g + d~ g_d
+// The whole sweep is one persistent cooperative launch (one CTA per SM, each owning a
+// fixed contiguous range of grid points).  Per subinterval, four grid-wide barriers:
+//   A  R^T U, R^T U', U.U
+//   B  d1 = U - R (R^T U)                       ; R^T d1
+//   C  d~ = d1 - R (R^T d1)                     ; R^T d~, d~.d~, d~.U, d~.U'
+//   D  L d~, L^T d~ at owned points             ; R^T L d~, R^T L^T d~, d~.L d~
+//   E  reduced solve, repeated by every CTA on identical inputs (no barrier)
+//   F  U^k_{n+1} = F_n + R g + d~ g_d at owned points (read back by the next A)
+// Sums over points: per-CTA partials (fixed thread and warp order), then every CTA adds
+// the partials of all CTAs in CTA order, so all CTAs hold bit-identical values and the
+// result does not depend on scheduling.  Each dot product over the basis is taken by one
+// warp per column with coalesced reads of the column.
 #include "pr_internal.cuh"
 
 #include <algorithm>
@@ -27,28 +30,6 @@
 namespace pr {
 
 constexpr int CS_THREADS = 256;
-constexpr int CS_MAXQ = 36;   // m + 3 <= 36  ->  level-2 dimension <= 33 in the coarse sweep
-
-// Offsets into the `dots` scratch (doubles).  maxm = largest level-2 dimension.
-struct DotsLayout {
-    int RU, RL, RD, RD2, UU, DD, DU, DUp, DLD, total;
-    __host__ __device__ DotsLayout(int maxm) {
-        RU = 0;                   // [maxm][2]: R^T U, R^T U'
-        RL = RU + 2 * maxm;       // [maxm][2]: R^T L d~, R^T L^T d~
-        RD = RL + 2 * maxm;       // [maxm]:    R^T d~ (first pass)
-        RD2 = RD + maxm;          // [maxm]:    R^T d~ (after re-orthogonalisation)
-        UU = RD2 + maxm;
-        DD = UU + 1;
-        DU = DD + 1;
-        DUp = DU + 1;
-        DLD = DUp + 1;
-        total = DLD + 1;
-    }
-};
-
-size_t coarse_part_doubles(long long Ng, int maxm) {
-    return (size_t)gram_chunks(Ng) * (size_t)std::max(CS_MAXQ, 2 * maxm + 2) + 64;
-}
 
 // Block-sum nq (<= MAXQ) values, write the chunk partial, and let the last CTA of the
 // batch item add the chunk partials in chunk order into out[q].
@@ -88,154 +69,8 @@ __device__ __forceinline__ void chunk_reduce(double (&acc)[MAXQ], int nq, double
     if (threadIdx.x == 0) st_relaxed_u32(counter, 0u);
 }
 
-// Pointer/count descriptors for the two gram passes, written on the device so that the
-// level-2 dimension m can stay on the device.
-struct CsDesc {
-    const void* colsR[64];
-    const void* colsUU[2];
-    const void* colsL[2];
-    int m;
-    int two;
-};
-
-__global__ void cs_prepare_kernel(CsDesc* desc, const void* R, const int* m_ptr, int maxm,
-                                  long long Ng, int esize, const double* U, const double* Up,
-                                  const double* Ld, const double* Ltd) {
-    if (threadIdx.x != 0) return;
-    const int m = min(*m_ptr, maxm);
-    for (int i = 0; i < m; ++i) desc->colsR[i] = reinterpret_cast<const char*>(R) + (size_t)i * Ng * esize;
-    desc->colsUU[0] = U;
-    desc->colsUU[1] = Up;
-    desc->colsL[0] = Ld;
-    desc->colsL[1] = Ltd;
-    desc->m = m;
-    desc->two = 2;
-}
-
-template <typename KT>
-__global__ void __launch_bounds__(CS_THREADS) cs_resid_kernel(CoarseArgs a, const CsDesc* desc,
-                                                              long long CH, int chunks) {
-    const int m = desc->m;
-    const DotsLayout L(a.maxm);
-    const double* c = a.dots + L.RU;  // [i*2 + 0] = R^T U
-    __shared__ double sc[CS_MAXQ];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sc[i] = c[2 * i];
-    __syncthreads();
-    const KT* R = reinterpret_cast<const KT*>(a.R);
-    double acc[CS_MAXQ];
-#pragma unroll
-    for (int q = 0; q < CS_MAXQ; ++q) acc[q] = 0.0;
-    double uu = 0.0;
-    const long long p_lo = (long long)blockIdx.x * CH, p_hi = min(a.g.Ng, p_lo + CH);
-    for (long long p = p_lo + threadIdx.x; p < p_hi; p += blockDim.x) {
-        const double u = a.U[p];
-        double rv[CS_MAXQ];
-        double d = u;
-#pragma unroll
-        for (int i = 0; i < CS_MAXQ - 3; ++i) {
-            if (i < m) {
-                rv[i] = (double)R[(size_t)i * a.g.Ng + p];
-                d -= rv[i] * sc[i];
-            }
-        }
-        a.d[p] = d;
-#pragma unroll
-        for (int i = 0; i < CS_MAXQ - 3; ++i)
-            if (i < m) acc[i] += rv[i] * d;
-        uu += u * u;
-    }
-    // outputs: R^T d~ -> RD[0..m), U.U -> UU (slot m)
-#pragma unroll
-    for (int q = 0; q < CS_MAXQ; ++q)
-        if (q == m) acc[q] = uu;
-    double* outs[CS_MAXQ];
-    for (int i = 0; i < CS_MAXQ; ++i) outs[i] = a.dots + L.RD + min(i, a.maxm - 1);
-    outs[m] = a.dots + L.UU;
-    chunk_reduce<CS_MAXQ>(acc, m + 1, a.part, chunks, blockIdx.x, a.counter + 0, outs);
-}
-
-template <typename KT>
-__global__ void __launch_bounds__(CS_THREADS) cs_reorth_kernel(CoarseArgs a, const CsDesc* desc,
-                                                               long long CH, int chunks) {
-    const int m = desc->m;
-    const DotsLayout L(a.maxm);
-    __shared__ double sc[CS_MAXQ];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sc[i] = a.dots[L.RD + i];
-    __syncthreads();
-    const KT* R = reinterpret_cast<const KT*>(a.R);
-    double acc[CS_MAXQ];
-#pragma unroll
-    for (int q = 0; q < CS_MAXQ; ++q) acc[q] = 0.0;
-    double dd = 0.0, du = 0.0, dup = 0.0;
-    const long long p_lo = (long long)blockIdx.x * CH, p_hi = min(a.g.Ng, p_lo + CH);
-    for (long long p = p_lo + threadIdx.x; p < p_hi; p += blockDim.x) {
-        double rv[CS_MAXQ];
-        double d = a.d[p];
-#pragma unroll
-        for (int i = 0; i < CS_MAXQ - 3; ++i) {
-            if (i < m) {
-                rv[i] = (double)R[(size_t)i * a.g.Ng + p];
-                d -= rv[i] * sc[i];
-            }
-        }
-        a.d[p] = d;
-#pragma unroll
-        for (int i = 0; i < CS_MAXQ - 3; ++i)
-            if (i < m) acc[i] += rv[i] * d;
-        dd += d * d;
-        du += d * a.U[p];
-        dup += d * a.Up[p];
-    }
-#pragma unroll
-    for (int q = 0; q < CS_MAXQ; ++q) {
-        if (q == m) acc[q] = dd;
-        if (q == m + 1) acc[q] = du;
-        if (q == m + 2) acc[q] = dup;
-    }
-    double* outs[CS_MAXQ];
-    for (int i = 0; i < CS_MAXQ; ++i) outs[i] = a.dots + L.RD2 + min(i, a.maxm - 1);
-    outs[m] = a.dots + L.DD;
-    outs[m + 1] = a.dots + L.DU;
-    outs[m + 2] = a.dots + L.DUp;
-    chunk_reduce<CS_MAXQ>(acc, m + 3, a.part, chunks, blockIdx.x, a.counter + 1, outs);
-}
-
-// L d~ and L^T d~ (b_d independent of x_d: L^T flips the advection sign), and d~.L d~.
-__global__ void __launch_bounds__(CS_THREADS) cs_Ld_kernel(CoarseArgs a, long long CH, int chunks) {
-    const int n = a.g.n;
-    const long long n2 = (long long)n * n;
-    const double* tab = a.g.tab;
-    const double inv2h = 0.5 / a.g.h, epsh2 = a.g.eps / (a.g.h * a.g.h);
-    double acc[1] = {0.0};
-    const long long p_lo = (long long)blockIdx.x * CH, p_hi = min(a.g.Ng, p_lo + CH);
-    for (long long i = p_lo + threadIdx.x; i < p_hi; i += blockDim.x) {
-        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / n2);
-        const long long base = i - x;
-        const long long rowb = i - (long long)y * n;
-        const long long plb = i - (long long)z * n2;
-        const double* d = a.d;
-        const double uc = d[i];
-        const double uxp = d[base + (x + 1 == n ? 0 : x + 1)], uxm = d[base + (x == 0 ? n - 1 : x - 1)];
-        const double uyp = d[rowb + (long long)(y + 1 == n ? 0 : y + 1) * n];
-        const double uym = d[rowb + (long long)(y == 0 ? n - 1 : y - 1) * n];
-        const double uzp = d[plb + (long long)(z + 1 == n ? 0 : z + 1) * n2];
-        const double uzm = d[plb + (long long)(z == 0 ? n - 1 : z - 1) * n2];
-        const double bx = tab[TXY * n + y] + tab[TXZ * n + z];
-        const double by = tab[TYX * n + x] + tab[TYZ * n + z];
-        const double bz = tab[TZX * n + x] + tab[TZY * n + y];
-        const double adv = (bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm)) * inv2h;
-        const double dif = epsh2 * ((uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc);
-        const double Ld = adv - dif;
-        a.Ld[i] = Ld;
-        a.Ltd[i] = -adv - dif;
-        acc[0] += uc * Ld;
-    }
-    double* outs[1] = {a.dots + DotsLayout(a.maxm).DLD};
-    chunk_reduce<1>(acc, 1, a.part, chunks, blockIdx.x, a.counter + 2, outs);
-}
-
-// Reduced solve (one CTA, FP64).  K = m + aug <= 33 (CS_MAXQ - 3).
-constexpr int CS_MAXK = CS_MAXQ - 3;
+// Small dense solves of iteration 0 (one CTA, FP64), K <= CS_MAXK.
+constexpr int CS_MAXK = 33;
 
 // LU with partial pivoting of the K x K matrix A (ld CS_MAXK) in shared memory; piv[K].
 __device__ void lu_factor(double* A, int K, int* piv) {
@@ -294,151 +129,343 @@ __device__ void lu_solve_col(const double* A, int K, const int* piv, double* x, 
     }
 }
 
-__global__ void cs_small_kernel(CoarseArgs a, const CsDesc* desc) {
-    __shared__ double Mv[CS_MAXK * CS_MAXK];
-    __shared__ double Ac[CS_MAXK * CS_MAXK];
-    __shared__ double T[CS_MAXK * CS_MAXK];
-    __shared__ double x[CS_MAXK], y[CS_MAXK];
-    __shared__ int piv[CS_MAXK];
-    __shared__ int s_K;
-    __shared__ double s_nd;
-    const int m = desc->m;
-    const DotsLayout L(a.maxm);
-    const double* D = a.dots;
-    if (threadIdx.x == 0) {
-        const double dd = D[L.DD], uu = D[L.UU];
-        const double nd = sqrt(fmax(dd, 0.0));
-        const bool aug = nd > a.aug_tol * sqrt(fmax(uu, 0.0)) && nd > 0.0;
-        s_K = aug ? m + 1 : m;
-        s_nd = aug ? nd : 0.0;
+// ------------------------------------------------------------------------------------
+// Persistent coarse sweep.
+constexpr int CSW_THREADS = 512;
+constexpr int CSW_WARPS = CSW_THREADS / 32;
+constexpr int CSW_MAXM = 32;                  // level-2 dimension supported
+constexpr int CSW_MAXK = CSW_MAXM + 1;        // with the augmentation direction
+constexpr int CSW_MAXQ = 2 * CSW_MAXM + 3;    // reductions per stage
+constexpr int CSW_LDA = 2 * CSW_MAXK + 1;     // [Ac | Mv | b]
+constexpr int CSW_MAX_GRID = 1024;
+
+size_t coarse_part_doubles(long long, int) { return (size_t)2 * CSW_MAXQ * CSW_MAX_GRID; }
+
+struct CswShared {
+    double RU[CSW_MAXM], RUp[CSW_MAXM], RD1[CSW_MAXM], RD[CSW_MAXM], RL[CSW_MAXM], RLt[CSW_MAXM];
+    double UU, DD, DU, DUp, DLD;
+    double red[CSW_WARPS * 3];
+    double g[CSW_MAXK];
+    double A[CSW_MAXK * CSW_LDA];
+    double prow[CSW_LDA];
+    double mult[CSW_MAXK];
+    double x[CSW_MAXK], y[CSW_MAXK];
+    double inv_piv;
+    int piv;
+};
+
+// Deterministic CTA sum of nq (<= 3) per-thread values; thread 0 writes part[q][cta].
+__device__ __forceinline__ void csw_block_sums(const double* v, int nq, CswShared& sh, double* part,
+                                               int G) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < nq; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) sh.red[q * CSW_WARPS + warp] = x;
     }
     __syncthreads();
-    const int K = s_K;
-    const double nd = s_nd;
+    if (threadIdx.x < nq) {
+        double s = 0.0;
+        for (int w = 0; w < CSW_WARPS; ++w) s += sh.red[threadIdx.x * CSW_WARPS + w];
+        part[(size_t)threadIdx.x * G + blockIdx.x] = s;
+    }
+}
+
+// Per-CTA partials of R_i . x0 (quantity q0 + i) and, if x1, R_i . x1 (quantity q1 + i)
+// over the owned points, one warp per column, four independent chains per lane.
+__device__ __forceinline__ void csw_dots(const double* R, long long Ng, int m, const double* x0,
+                                         int q0, const double* x1, int q1, long long lo, long long hi,
+                                         double* part, int G) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < m; i += CSW_WARPS) {
+        const double* r = R + (size_t)i * Ng;
+        double s0[4] = {0.0, 0.0, 0.0, 0.0}, s1[4] = {0.0, 0.0, 0.0, 0.0};
+        long long p = lo + lane;
+        for (; p + 96 < hi; p += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double rv = r[p + 32 * u];
+                s0[u] += rv * x0[p + 32 * u];
+                if (x1) s1[u] += rv * x1[p + 32 * u];
+            }
+        }
+        for (int u = 0; p < hi; p += 32, ++u) {
+            const double rv = r[p];
+            s0[u & 3] += rv * x0[p];
+            if (x1) s1[u & 3] += rv * x1[p];
+        }
+        double a0 = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+        double a1 = (s1[0] + s1[1]) + (s1[2] + s1[3]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, off);
+            a1 += __shfl_down_sync(0xffffffffu, a1, off);
+        }
+        if (lane == 0) {
+            part[(size_t)(q0 + i) * G + blockIdx.x] = a0;
+            if (x1) part[(size_t)(q1 + i) * G + blockIdx.x] = a1;
+        }
+    }
+}
+
+// Sum the partials of all CTAs, in CTA order, for quantities 0..nq-1; out(q) receives
+// the value.  Every CTA computes the same sums.
+template <typename Out>
+__device__ __forceinline__ void csw_reduce(const double* part, int nq, int G, Out&& out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = warp; q < nq; q += CSW_WARPS) {
+        double s = 0.0;
+        for (int c = lane; c < G; c += 32) s += part[(size_t)q * G + c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) out(q, s);
+    }
+    __syncthreads();
+}
+
+// Reduced solve of one subinterval (all threads of the CTA, FP64): Gauss-Jordan with
+// partial pivoting on [Ac | Mv | b], Ac = Mv + dT Lv, b = V^T (U - U'), which gives
+// T = Ac^{-1} Mv and y = Ac^{-1} b = T Mv^{-1} b; then x = T^{Lc-1} y = Phi^Lc Mv^{-1} b.
+__device__ void csw_small(CswShared& sh, const CoarseSweepArgs& a, int m, const double* Mr,
+                          const double* Lr) {
+    const double nd = sqrt(fmax(sh.DD, 0.0));
+    const bool aug = nd > 0.0 && nd > a.aug_tol * sqrt(fmax(sh.UU, 0.0));
+    const int K = aug ? m + 1 : m;
+    const int nc = 2 * K + 1;
     const double dT = a.dT;
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
         const int i = e / K, j = e - i * K;
         double mv, lv;
         if (i < m && j < m) {
-            mv = a.Mr[(size_t)i * a.maxm + j];
-            lv = a.Lr[(size_t)i * a.maxm + j];
-        } else if (i < m) {          // column m: R^T d, R^T L d
-            mv = D[L.RD2 + i] / nd;
-            lv = D[L.RL + 2 * i + 0] / nd;
-        } else if (j < m) {          // row m: d^T R, d^T L R = (L^T d)^T R
-            mv = D[L.RD2 + j] / nd;
-            lv = D[L.RL + 2 * j + 1] / nd;
+            mv = Mr[(size_t)i * a.ldM + j];
+            lv = Lr[(size_t)i * a.ldM + j];
+        } else if (i < m) {      // column m: R^T d, R^T L d
+            mv = sh.RD[i] / nd;
+            lv = sh.RL[i] / nd;
+        } else if (j < m) {      // row m: d^T R, (L^T d)^T R
+            mv = sh.RD[j] / nd;
+            lv = sh.RLt[j] / nd;
         } else {
-            mv = D[L.DD] / (nd * nd);
-            lv = D[L.DLD] / (nd * nd);
+            mv = sh.DD / (nd * nd);
+            lv = sh.DLD / (nd * nd);
         }
-        Mv[i * CS_MAXK + j] = mv;
-        Ac[i * CS_MAXK + j] = mv + dT * lv;
-        T[i * CS_MAXK + j] = mv;  // right-hand sides of Ac T = Mv
+        sh.A[i * CSW_LDA + j] = mv + dT * lv;
+        sh.A[i * CSW_LDA + K + j] = mv;
     }
-    // projection of the difference: V^T (U - U')
     for (int i = threadIdx.x; i < K; i += blockDim.x)
-        x[i] = (i < m) ? D[L.RU + 2 * i] - D[L.RU + 2 * i + 1] : (D[L.DU] - D[L.DUp]) / nd;
+        sh.A[i * CSW_LDA + 2 * K] = (i < m) ? sh.RU[i] - sh.RUp[i] : (sh.DU - sh.DUp) / nd;
     __syncthreads();
-    lu_factor(Ac, K, piv);
-    for (int c = threadIdx.x; c < K; c += blockDim.x) lu_solve_col(Ac, K, piv, T + c, CS_MAXK);
-    __syncthreads();
-    // Mv x0 = V^T (U - U'): factor Mv (Ac is no longer needed)
-    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-        const int i = e / K, j = e - i * K;
-        Ac[i * CS_MAXK + j] = Mv[i * CS_MAXK + j];
-    }
-    __syncthreads();
-    lu_factor(Ac, K, piv);
-    if (threadIdx.x == 0) lu_solve_col(Ac, K, piv, x, 1);
-    __syncthreads();
-    for (int l = 0; l < a.Lc; ++l) {
-        for (int i = threadIdx.x; i < K; i += blockDim.x) {
-            double s = 0.0;
-            for (int j = 0; j < K; ++j) s += T[i * CS_MAXK + j] * x[j];
-            y[i] = s;
+    for (int j = 0; j < K; ++j) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double best = -1.0;
+            int bi = j;
+            for (int i = j + lane; i < K; i += 32) {
+                const double v = fabs(sh.A[i * CSW_LDA + j]);
+                if (v > best) { best = v; bi = i; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                sh.piv = bi;
+                const double pv = sh.A[bi * CSW_LDA + j];
+                sh.inv_piv = (pv != 0.0) ? 1.0 / pv : 0.0;
+            }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < K; i += blockDim.x) x[i] = y[i];
+        const int pr = sh.piv;
+        if (pr != j) {
+            for (int c = j + threadIdx.x; c < nc; c += blockDim.x) {
+                const double t = sh.A[j * CSW_LDA + c];
+                sh.A[j * CSW_LDA + c] = sh.A[pr * CSW_LDA + c];
+                sh.A[pr * CSW_LDA + c] = t;
+            }
+        }
+        __syncthreads();
+        for (int c = j + 1 + threadIdx.x; c < nc; c += blockDim.x) sh.prow[c] = sh.A[j * CSW_LDA + c] * sh.inv_piv;
+        for (int i = threadIdx.x; i < K; i += blockDim.x) sh.mult[i] = sh.A[i * CSW_LDA + j];
+        __syncthreads();
+        const int w = nc - j - 1;
+        for (int e = threadIdx.x; e < K * w; e += blockDim.x) {
+            const int i = e / w, c = j + 1 + (e - i * w);
+            sh.A[i * CSW_LDA + c] = (i == j) ? sh.prow[c] : sh.A[i * CSW_LDA + c] - sh.mult[i] * sh.prow[c];
+        }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i <= a.maxm; i += blockDim.x) {
+    // x = y, then Lc - 1 products with T
+    for (int i = threadIdx.x; i < K; i += blockDim.x) sh.x[i] = sh.A[i * CSW_LDA + 2 * K];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = 1; l < a.Lc; ++l) {
+        for (int i = warp; i < K; i += CSW_WARPS) {
+            double s = (lane < K) ? sh.A[i * CSW_LDA + K + lane] * sh.x[lane] : 0.0;
+            if (lane + 32 < K) s += sh.A[i * CSW_LDA + K + lane + 32] * sh.x[lane + 32];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) sh.y[i] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += blockDim.x) sh.x[i] = sh.y[i];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) {
         double v = 0.0;
-        if (i < m) v = x[i];
-        else if (i == m && K == m + 1) v = x[m] / nd;
-        a.coef[i] = v;
+        if (i < m) v = sh.x[i];
+        else if (aug) v = sh.x[m] / nd;
+        sh.g[i] = v;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSweepArgs a) {
+    __shared__ CswShared sh;
+    const int G = gridDim.x;
+    const long long Ng = a.g.Ng;
+    const long long CH = (Ng + G - 1) / G;
+    const long long lo = min(Ng, (long long)blockIdx.x * CH), hi = min(Ng, lo + CH);
+    int buf = 0;
+    auto part = [&]() { return a.part + (size_t)buf * CSW_MAXQ * G; };
+    auto barrier = [&]() -> bool { return group_barrier(a.bar, (unsigned)G, a.spin_limit, a.err); };
+    const int n_ = a.g.n;
+    const long long n2 = (long long)n_ * n_;
+    const double inv2h = 0.5 / a.g.h, epsh2 = a.g.eps / (a.g.h * a.g.h);
+
+    for (int t = 0; t < a.count; ++t) {
+        const long long n = a.n0 + t;
+        const double* U = a.U + n * a.sU;
+        const double* Up = a.Up + n * a.sUp;
+        const double* F = a.F + n * a.sF;
+        double* out = a.out + n * a.sOut;
+        const double* R = a.R + n * a.sR;
+        const double* Mr = a.Mr + n * a.sM;
+        const double* Lr = a.Lr + n * a.sM;
+        int m = a.m[n * a.sm];
+        if (m > a.maxm || m < 0) {
+            if (threadIdx.x == 0) record_error(a.err, DERR_BREAKDOWN);
+            m = max(0, min(m, a.maxm));
+        }
+        // ---- A: R^T U, R^T U', U.U
+        {
+            double v[1] = {0.0};
+            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) v[0] += U[p] * U[p];
+            csw_block_sums(v, 1, sh, part() + (size_t)(2 * m) * G, G);
+            csw_dots(R, Ng, m, U, 0, Up, m, lo, hi, part(), G);
+            if (!barrier()) return;
+            csw_reduce(part(), 2 * m + 1, G, [&](int q, double s) {
+                if (q < m) sh.RU[q] = s;
+                else if (q < 2 * m) sh.RUp[q - m] = s;
+                else sh.UU = s;
+            });
+            buf ^= 1;
+        }
+        // ---- B: d1 = U - R (R^T U) ; R^T d1
+        {
+            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+                double v = U[p];
+                for (int i = 0; i < m; ++i) v -= sh.RU[i] * R[(size_t)i * Ng + p];
+                a.d[p] = v;
+            }
+            __syncthreads();
+            csw_dots(R, Ng, m, a.d, 0, nullptr, 0, lo, hi, part(), G);
+            if (!barrier()) return;
+            csw_reduce(part(), m, G, [&](int q, double s) { sh.RD1[q] = s; });
+            buf ^= 1;
+        }
+        // ---- C: d~ = d1 - R (R^T d1) ; R^T d~, d~.d~, d~.U, d~.U'
+        {
+            double v[3] = {0.0, 0.0, 0.0};
+            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+                double d = a.d[p];
+                for (int i = 0; i < m; ++i) d -= sh.RD1[i] * R[(size_t)i * Ng + p];
+                a.d[p] = d;
+                v[0] += d * d;
+                v[1] += d * U[p];
+                v[2] += d * Up[p];
+            }
+            csw_block_sums(v, 3, sh, part() + (size_t)m * G, G);
+            __syncthreads();
+            csw_dots(R, Ng, m, a.d, 0, nullptr, 0, lo, hi, part(), G);
+            if (!barrier()) return;
+            csw_reduce(part(), m + 3, G, [&](int q, double s) {
+                if (q < m) sh.RD[q] = s;
+                else if (q == m) sh.DD = s;
+                else if (q == m + 1) sh.DU = s;
+                else sh.DUp = s;
+            });
+            buf ^= 1;
+        }
+        // ---- D: L d~, L^T d~ (b_d does not depend on x_d, so L^T flips the advection) ;
+        //         R^T L d~, R^T L^T d~, d~.L d~
+        {
+            const double* tab = a.g.tab;
+            const double* d = a.d;
+            double v[1] = {0.0};
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const int x = (int)(i % n_), y = (int)((i / n_) % n_), z = (int)(i / n2);
+                const long long base = i - x, rowb = i - (long long)y * n_, plb = i - (long long)z * n2;
+                const double uc = d[i];
+                const double uxp = d[base + (x + 1 == n_ ? 0 : x + 1)], uxm = d[base + (x == 0 ? n_ - 1 : x - 1)];
+                const double uyp = d[rowb + (long long)(y + 1 == n_ ? 0 : y + 1) * n_];
+                const double uym = d[rowb + (long long)(y == 0 ? n_ - 1 : y - 1) * n_];
+                const double uzp = d[plb + (long long)(z + 1 == n_ ? 0 : z + 1) * n2];
+                const double uzm = d[plb + (long long)(z == 0 ? n_ - 1 : z - 1) * n2];
+                const double bx = tab[TXY * n_ + y] + tab[TXZ * n_ + z];
+                const double by = tab[TYX * n_ + x] + tab[TYZ * n_ + z];
+                const double bz = tab[TZX * n_ + x] + tab[TZY * n_ + y];
+                const double adv = (bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm)) * inv2h;
+                const double dif = epsh2 * ((uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc);
+                const double Ld = adv - dif;
+                a.Ld[i] = Ld;
+                a.Ltd[i] = -adv - dif;
+                v[0] += uc * Ld;
+            }
+            csw_block_sums(v, 1, sh, part() + (size_t)(2 * m) * G, G);
+            __syncthreads();
+            csw_dots(R, Ng, m, a.Ld, 0, a.Ltd, m, lo, hi, part(), G);
+            if (!barrier()) return;
+            csw_reduce(part(), 2 * m + 1, G, [&](int q, double s) {
+                if (q < m) sh.RL[q] = s;
+                else if (q < 2 * m) sh.RLt[q - m] = s;
+                else sh.DLD = s;
+            });
+            buf ^= 1;
+        }
+        // ---- E: reduced solve ; F: U^k_{n+1} = F_n + R g + d~ g_d
+        csw_small(sh, a, m, Mr, Lr);
+        for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+            double s = F[p] + a.d[p] * sh.g[m];
+            for (int i = 0; i < m; ++i) s += R[(size_t)i * Ng + p] * sh.g[i];
+            out[p] = s;
+        }
+        // out is read back at the same points by the same threads (next stage A) and by
+        // other threads of this CTA only after the __syncthreads in csw_block_sums
     }
 }
 
-template <typename KT>
-__global__ void __launch_bounds__(CS_THREADS) cs_update_kernel(CoarseArgs a, const CsDesc* desc) {
-    const int m = desc->m;
-    __shared__ double g[CS_MAXK + 1];
-    for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = a.coef[i];
-    __syncthreads();
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.g.Ng) return;
-    const KT* R = reinterpret_cast<const KT*>(a.R);
-    double s = a.F[p] + a.d[p] * g[m];
-    for (int i = 0; i < m; ++i) s += (double)R[(size_t)i * a.g.Ng + p] * g[i];
-    a.out[p] = s;
+int coarse_sweep_grid() {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, coarse_sweep_kernel, CSW_THREADS, 0);
+    return std::min(CSW_MAX_GRID, std::max(1, std::min(occ, 1) * sms));
 }
 
-cudaError_t launch_coarse_update(const CoarseArgs& a, bool r_f32, cudaStream_t st) {
-    if (a.maxm > CS_MAXK - 1) return cudaErrorInvalidValue;
-    const int chunks = gram_chunks(a.g.Ng);
-    long long CH = (a.g.Ng + chunks - 1) / chunks;
-    const DotsLayout L(a.maxm);
-    const int esize = r_f32 ? 4 : 8;
-    // descriptors live right after the dot products in the dots scratch
-    CsDesc* desc = reinterpret_cast<CsDesc*>(a.dots + ((L.total + 7) / 8) * 8);
-    cs_prepare_kernel<<<1, 32, 0, st>>>(desc, a.R, a.m_ptr, a.maxm, a.g.Ng, esize, a.U, a.Up, a.Ld, a.Ltd);
+int coarse_max_m() { return CSW_MAXM; }
+
+cudaError_t launch_coarse_sweep(CoarseSweepArgs a, cudaStream_t st) {
+    if (a.count <= 0) return cudaSuccess;
+    if (a.maxm > CSW_MAXM) return cudaErrorInvalidValue;
+    const int grid = coarse_sweep_grid();
+    void* args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)coarse_sweep_kernel, dim3(grid), dim3(CSW_THREADS),
+                                                args, 0, st);
     ++g_launch_count;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // pass 1: R^T [U, U']
-    GramArgs ga{};
-    ga.colsA = desc->colsR;
-    ga.colsB = desc->colsUU;
-    ga.KA = &desc->m;
-    ga.KB = &desc->two;
-    ga.ldcols = 0;
-    ga.Ng = a.g.Ng;
-    ga.B = 1;
-    ga.maxKA = a.maxm;
-    ga.maxKB = 2;
-    ga.sym = false;
-    ga.part = a.part;
-    ga.counter = a.counter + 3;
-    ga.G = a.dots + L.RU;
-    ga.ldG = 2;
-    ga.ldG_b = 0;
-    e = launch_gram(ga, r_f32, false, st);
-    if (e != cudaSuccess) return e;
-    // passes 2, 3
-    if (r_f32) cs_resid_kernel<float><<<chunks, CS_THREADS, 0, st>>>(a, desc, CH, chunks);
-    else cs_resid_kernel<double><<<chunks, CS_THREADS, 0, st>>>(a, desc, CH, chunks);
-    ++g_launch_count;
-    if (r_f32) cs_reorth_kernel<float><<<chunks, CS_THREADS, 0, st>>>(a, desc, CH, chunks);
-    else cs_reorth_kernel<double><<<chunks, CS_THREADS, 0, st>>>(a, desc, CH, chunks);
-    ++g_launch_count;
-    // pass 4
-    cs_Ld_kernel<<<chunks, CS_THREADS, 0, st>>>(a, CH, chunks);
-    ++g_launch_count;
-    // pass 5: R^T [L d~, L^T d~]
-    ga.colsB = desc->colsL;
-    ga.G = a.dots + L.RL;
-    ga.counter = a.counter + 4;
-    e = launch_gram(ga, r_f32, false, st);
-    if (e != cudaSuccess) return e;
-    // pass 6, 7
-    cs_small_kernel<<<1, 128, 0, st>>>(a, desc);
-    ++g_launch_count;
-    const unsigned blocks = (unsigned)((a.g.Ng + CS_THREADS - 1) / CS_THREADS);
-    if (r_f32) cs_update_kernel<float><<<blocks, CS_THREADS, 0, st>>>(a, desc);
-    else cs_update_kernel<double><<<blocks, CS_THREADS, 0, st>>>(a, desc);
-    ++g_launch_count;
-    return cudaGetLastError();
+    return e;
 }
 
 // ------------------------------------------------------------------------------------

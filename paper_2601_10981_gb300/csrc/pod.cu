@@ -170,7 +170,27 @@ cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t 
 }
 
 // ------------------------------------------------------------------------------------
-// Out_b = In_b C_b.
+// Out_b = In_b C_b.  One thread per point; a block of J outputs (J a multiple of 4, the
+// smallest that covers the remaining columns) is accumulated with compile-time trip
+// counts, so no predicated-off multiply-adds are issued.  C sits in shared memory with
+// rows padded to a multiple of 4 by zeros.
+template <typename TI, typename TO, typename TC, int J>
+__device__ __forceinline__ void tsmm_block(const void* const* cols, int KIN, const TC* sC, int KP,
+                                           int j0, int jn, long long p, long long Ng, TO* out) {
+    TC acc[J];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc[jj] = (TC)0;
+    for (int i = 0; i < KIN; ++i) {
+        const TC x = (TC)(reinterpret_cast<const TI*>(cols[i])[p]);
+        const TC* crow = sC + (size_t)i * KP + j0;
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) acc[jj] += x * crow[jj];
+    }
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj)
+        if (jj < jn) out[(size_t)(j0 + jj) * Ng + p] = (TO)acc[jj];
+}
+
 template <typename TI, typename TO, typename TC>
 __global__ void __launch_bounds__(256) tsmm_kernel(TsmmArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -178,10 +198,11 @@ __global__ void __launch_bounds__(256) tsmm_kernel(TsmmArgs a) {
     const int b = blockIdx.y;
     const int KIN = a.KIN[b], KOUT = a.KOUT[b];
     if (KOUT <= 0) return;
+    const int KP = (KOUT + 3) / 4 * 4;
     const double* Cb = a.C + (size_t)b * a.ldC_b;
-    for (int e = threadIdx.x; e < KIN * KOUT; e += blockDim.x) {
-        const int i = e / KOUT, j = e - i * KOUT;
-        sC[e] = (TC)Cb[(size_t)i * a.ldC + j];
+    for (int e = threadIdx.x; e < KIN * KP; e += blockDim.x) {
+        const int i = e / KP, j = e - i * KP;
+        sC[e] = (j < KOUT) ? (TC)Cb[(size_t)i * a.ldC + j] : (TC)0;
     }
     __syncthreads();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -190,39 +211,33 @@ __global__ void __launch_bounds__(256) tsmm_kernel(TsmmArgs a) {
     TO* out = reinterpret_cast<TO*>(a.out) + (size_t)b * a.ld_out_b;
     for (int j0 = 0; j0 < KOUT; j0 += 32) {
         const int jn = min(32, KOUT - j0);
-        TC acc[32];
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] = (TC)0;
-        for (int i = 0; i < KIN; ++i) {
-            const TC x = (TC)(reinterpret_cast<const TI*>(cols[i])[p]);
-            const TC* crow = sC + i * KOUT + j0;
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-                if (jj < jn) acc[jj] += x * crow[jj];
+        switch ((jn + 3) / 4) {
+        case 1: tsmm_block<TI, TO, TC, 4>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        case 2: tsmm_block<TI, TO, TC, 8>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        case 3: tsmm_block<TI, TO, TC, 12>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        case 4: tsmm_block<TI, TO, TC, 16>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        case 5: tsmm_block<TI, TO, TC, 20>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        case 6: tsmm_block<TI, TO, TC, 24>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        case 7: tsmm_block<TI, TO, TC, 28>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
+        default: tsmm_block<TI, TO, TC, 32>(cols, KIN, sC, KP, j0, jn, p, a.Ng, out); break;
         }
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj)
-            if (jj < jn) out[(size_t)(j0 + jj) * a.Ng + p] = (TO)acc[jj];
     }
 }
 
 cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream_t st) {
     if (a.B <= 0 || a.maxKOUT <= 0) return cudaSuccess;
     dim3 grid((unsigned)((a.Ng + 255) / 256), a.B);
+    const size_t cells = (size_t)a.maxKIN * ((a.maxKOUT + 3) / 4 * 4);
     if (in_f32 && out_f32) {
-        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(float);
-        tsmm_kernel<float, float, float><<<grid, 256, smem, st>>>(a);
+        tsmm_kernel<float, float, float><<<grid, 256, cells * sizeof(float), st>>>(a);
     } else if (!in_f32 && out_f32) {
         // FP64 input (snapshots): accumulate in FP64 and round only the output, the
         // combinations of nearly parallel snapshots that give trailing modes cancel
-        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
-        tsmm_kernel<double, float, double><<<grid, 256, smem, st>>>(a);
+        tsmm_kernel<double, float, double><<<grid, 256, cells * sizeof(double), st>>>(a);
     } else if (in_f32) {
-        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
-        tsmm_kernel<float, double, double><<<grid, 256, smem, st>>>(a);
+        tsmm_kernel<float, double, double><<<grid, 256, cells * sizeof(double), st>>>(a);
     } else {
-        const size_t smem = (size_t)a.maxKIN * a.maxKOUT * sizeof(double);
-        tsmm_kernel<double, double, double><<<grid, 256, smem, st>>>(a);
+        tsmm_kernel<double, double, double><<<grid, 256, cells * sizeof(double), st>>>(a);
     }
     ++g_launch_count;
     return cudaGetLastError();

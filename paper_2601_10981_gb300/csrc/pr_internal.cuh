@@ -253,31 +253,38 @@ cudaError_t launch_assemble_cols(const void* const* bases, const int* const* cnt
 
 // ---------------------------------------------------------------------------------
 // Coarse sweep pieces (one subinterval, sequential in n).
-struct CoarseArgs {
+// Persistent coarse sweep over subintervals n = n0 .. n0+count-1, in order: item n reads
+// U^k_n = U + n*sU (for n > n0 the output of item n-1 when sU == sOut and
+// out == U + sU), U^{k-1}_n, F_n, its level-2 basis (m[n*sm] FP64 columns of stride Ng)
+// and Galerkin blocks, and writes U^k_{n+1} = out + n*sOut.
+struct CoarseSweepArgs {
     Grid g;
-    const void* R;          // m columns (KT), contiguous, stride Ng
-    const int* m_ptr;       // device int: m
-    int maxm;
-    const double* U;        // U^k_n
-    const double* Up;       // U^{k-1}_n
-    const double* F;        // F_n
-    double* out;            // U^k_{n+1}
-    const double* Mr;       // m x m (ld maxm): R^T R
-    const double* Lr;       // m x m (ld maxm): R^T L R
+    long long n0;
+    int count;
+    const double* U;  long long sU;
+    const double* Up; long long sUp;
+    const double* F;  long long sF;
+    double* out;      long long sOut;
+    const double* R;  long long sR;
+    const int* m;     long long sm;
+    const double* Mr;       // R^T R, m x m with leading dimension ldM, stride sM per item
+    const double* Lr;       // R^T L R, same layout
+    long long sM;
+    int ldM;
+    int maxm;               // <= coarse_max_m()
     double dT;
     int Lc;
     double aug_tol;
-    // scratch
-    double* d;              // [Ng]
-    double* Ld;             // [Ng]
-    double* Ltd;            // [Ng]
-    double* dots;           // small result vectors (see coarse.cu)
-    double* part;           // chunk partials
-    unsigned* counter;      // [8] zero
-    double* coef;           // [maxm+1]
+    double* d;              // scratch [Ng] each
+    double* Ld;
+    double* Ltd;
+    double* part;           // coarse_part_doubles()
+    unsigned* bar;          // [2], bar[0] zero at launch
+    long long spin_limit;
     int* err;
 };
-cudaError_t launch_coarse_update(const CoarseArgs& a, bool r_f32, cudaStream_t st);
+cudaError_t launch_coarse_sweep(CoarseSweepArgs a, cudaStream_t st);
+int coarse_max_m();
 size_t coarse_part_doubles(long long Ng, int maxm);
 
 // Iteration 0: beta_n = reduced coordinates of U^0_n, n = 1..N (G_0 in V0), from
