@@ -238,11 +238,12 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU arm
 def fine_bytes_per_dof_step(w_bytes: int, lin_iters: float, dM: int, has_f: bool) -> float:
     """Algorithmic DRAM bytes of the fused fine sweep per grid point and fine step:
-    setup reads u (8 B) and delta (w), writes u (8 B), r and rhat (2w), reads f (8 B);
-    each BiCGStab iteration streams 17 words (phase 1: r, p', v', rhat in, p, v out;
-    phase 2: r, v in, t out; phase 3: delta, p, r, v, t, rhat in, delta, r out); one
-    snapshot word every dM steps."""
-    return 16 + 3 * w_bytes + (8 if has_f else 0) + lin_iters * 17 * w_bytes + w_bytes / dM
+    setup reads the state (8 B: FP64, or the hi + lo float pair of the FP32 mode) and
+    delta (w), writes the state (8 B), r and rhat (2w), reads f (w); each BiCGStab
+    iteration streams 17 words (phase 1: r, p', v', rhat in, p, v out; phase 2: r, v in,
+    t out; phase 3: delta, p, r, v, t, rhat in, delta, r out); one FP64 snapshot value
+    every dM steps."""
+    return 16 + 3 * w_bytes + (w_bytes if has_f else 0) + lin_iters * 17 * w_bytes + 8 / dM
 
 
 def run_ours(args):

@@ -171,15 +171,56 @@ struct Acc {
     }
 };
 
+// CTA sum of NQ per-thread partials, valid in thread 0 (fixed order).  With KT = float
+// the in-warp tree runs in float: GB300's FP64 pipe would spend five double additions
+// per thread and quantity on it, and the FP32 Krylov scalars do not need more.
+template <typename KT, int NQ>
+__device__ __forceinline__ void cta_sum(double (&v)[NQ], double* red) {
+    if constexpr (std::is_same<KT, double>::value) {
+        block_sum<NQ>(v, red);
+    } else {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int nwarps = (blockDim.x + 31) >> 5;
+        float w[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            w[q] = (float)v[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) w[q] += __shfl_down_sync(0xffffffffu, w[q], off);
+        }
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) red[q * 32 + warp] = (double)w[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                double s = 0.0;
+                for (int i = 0; i < nwarps; ++i) s += red[q * 32 + i];
+                v[q] = s;
+            }
+        }
+    }
+}
+
 struct FineShared {
     double red[4 * 32];
     double sums[4];
+    // BiCGStab scalars and decisions, written by thread 0 after each group reduction:
+    // GB300 runs FP64 divisions and square roots on its narrow FP64 pipe, so they are
+    // taken once per CTA instead of once per thread
+    double thr, rho, alpha, omega, beta;
+    int status, flag;
 };
 
 // Sum of the per-CTA partials of a group for quantities 0..nq-1 (fixed order, read by
-// warp 0, lane 0 result broadcast through shared memory).
+// warp 0); thread 0 then runs post(sums), and the results reach every thread through
+// shared memory.
+template <typename Post>
 __device__ __forceinline__ void group_sums(const double* part, int grid, int g0, int G, int nq,
-                                           double* out_sums) {
+                                           double* out_sums, Post&& post) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         for (int q = 0; q < nq; ++q) {
@@ -189,6 +230,7 @@ __device__ __forceinline__ void group_sums(const double* part, int grid, int g0,
             for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
             if (lane == 0) out_sums[q] = s;
         }
+        if (lane == 0) post(out_sums);
     }
     __syncthreads();
 }
@@ -508,8 +550,9 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         double* snap_b = a.snap ? reinterpret_cast<double*>(a.snap) + (size_t)b * a.n_snap * Ng : nullptr;
         long long its_total = 0;
         int its_max = 0;
-        int status = 0;
         bool dvalid = false;
+        __syncthreads();
+        if (threadIdx.x == 0) sh.status = 0;
 
         for (int j = 1; j <= a.S; ++j) {
             // ---------------- setup: u_{j-1} = u_{j-2} + delta ; r = rhat = dt (f - L u_{j-1})
@@ -650,20 +693,26 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             }
             {
                 acc.flush();
-                block_sum<2>(acc.d, sh.red);
+                cta_sum<KT, 2>(acc.d, sh.red);
                 if (threadIdx.x == 0) {
                     part[(size_t)((ph & 1) * 4 + 0) * grid + blockIdx.x] = acc.d[0];
                     part[(size_t)((ph & 1) * 4 + 1) * grid + blockIdx.x] = acc.d[1];
                 }
             }
             if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
-            group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 2, sh.sums);
+            group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 2, sh.sums, [&](const double* s) {
+                const double rr0 = s[0], bb = s[1];
+                sh.thr = a.tol * sqrt(bb);
+                int conv = sqrt(rr0) <= sh.thr;
+                if (!isfinite(rr0) || !isfinite(bb)) { sh.status = DERR_NONFINITE; conv = 1; }
+                sh.flag = conv;
+                sh.rho = rr0;
+                sh.alpha = 1.0;
+                sh.omega = 1.0;
+                sh.beta = 0.0;
+            });
             ++ph;
-            const double rr0 = sh.sums[0], bb = sh.sums[1];
-            const double thr = a.tol * sqrt(bb);
-            bool conv = sqrt(rr0) <= thr;
-            if (!isfinite(rr0) || !isfinite(bb)) { status = DERR_NONFINITE; conv = true; }
-            double rho = rr0, alpha = 1.0, omega = 1.0, beta = 0.0;
+            const bool conv = sh.flag != 0;
             int it = 0;
             while (!conv) {
                 ++it;
@@ -673,7 +722,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 KT* vn = (it & 1) ? v1 : v0;
                 KT* vo = (it & 1) ? v0 : v1;
                 {
-                    const KT bk = (KT)beta, ok = (KT)omega;
+                    const KT bk = (KT)sh.beta, ok = (KT)sh.omega;
                     const bool first = (it == 1);
                     Acc<KT, 1> acc;
                     acc.init();
@@ -708,22 +757,28 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               acc.tick();
                           });
                     acc.flush();
-                    block_sum<1>(acc.d, sh.red);
+                    cta_sum<KT, 1>(acc.d, sh.red);
                     if (threadIdx.x == 0) part[(size_t)((ph & 1) * 4) * grid + blockIdx.x] = acc.d[0];
                 }
                 if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
-                group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 1, sh.sums);
+                group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 1, sh.sums, [&](const double* s) {
+                    const double rv = s[0];
+                    if (rv == 0.0 || !isfinite(rv)) {
+                        sh.status = isfinite(rv) ? DERR_BREAKDOWN : DERR_NONFINITE;
+                        sh.flag = 1;
+                    } else {
+                        sh.alpha = sh.rho / rv;
+                        sh.flag = 0;
+                    }
+                });
                 ++ph;
-                const double rv = sh.sums[0];
-                if (rv == 0.0 || !isfinite(rv)) {
-                    status = isfinite(rv) ? DERR_BREAKDOWN : DERR_NONFINITE;
+                if (sh.flag) {
                     --it;
                     break;
                 }
-                alpha = rho / rv;
                 // ---------------- ph2: s = r - alpha v, t = A s
                 {
-                    const KT al = (KT)alpha;
+                    const KT al = (KT)sh.alpha;
                     Acc<KT, 3> acc;
                     acc.init();
                     march(true, ringk,
@@ -749,31 +804,34 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               acc.tick();
                           });
                     acc.flush();
-                    block_sum<3>(acc.d, sh.red);
+                    cta_sum<KT, 3>(acc.d, sh.red);
                     if (threadIdx.x == 0) {
                         for (int qq = 0; qq < 3; ++qq)
                             part[(size_t)((ph & 1) * 4 + qq) * grid + blockIdx.x] = acc.d[qq];
                     }
                 }
                 if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
-                group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 3, sh.sums);
-                ++ph;
-                const double ts = sh.sums[0], tt2 = sh.sums[1], ss = sh.sums[2];
-                const bool half = sqrt(ss) <= thr;
-                if (!half) {
-                    if (tt2 == 0.0 || !isfinite(tt2)) {
-                        status = isfinite(tt2) ? DERR_BREAKDOWN : DERR_NONFINITE;
-                        omega = 0.0;
-                    } else {
-                        omega = ts / tt2;
-                        if (omega == 0.0) status = DERR_BREAKDOWN;
+                group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 3, sh.sums, [&](const double* s) {
+                    const double ts = s[0], tt2 = s[1], ss = s[2];
+                    const int half = sqrt(ss) <= sh.thr;
+                    if (!half) {
+                        if (tt2 == 0.0 || !isfinite(tt2)) {
+                            sh.status = isfinite(tt2) ? DERR_BREAKDOWN : DERR_NONFINITE;
+                            sh.omega = 0.0;
+                        } else {
+                            sh.omega = ts / tt2;
+                            if (sh.omega == 0.0) sh.status = DERR_BREAKDOWN;
+                        }
                     }
-                }
+                    sh.flag = half;
+                });
+                ++ph;
+                const bool half = sh.flag != 0;
                 // ---------------- ph3: delta += alpha p + omega s ; r = s - omega t
                 {
-                    const KT al = (KT)alpha, om = (KT)omega;
+                    const KT al = (KT)sh.alpha, om = (KT)sh.omega;
                     const bool first = (it == 1);
-                    const bool upd_r = !half && status == 0;
+                    const bool upd_r = !half && sh.status == 0;
                     Acc<KT, 2> acc;
                     acc.init();
                     if (upd_r) {
@@ -824,29 +882,36 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               });
                     }
                     acc.flush();
-                    block_sum<2>(acc.d, sh.red);
+                    cta_sum<KT, 2>(acc.d, sh.red);
                     if (threadIdx.x == 0 && upd_r) {
                         part[(size_t)((ph & 1) * 4 + 0) * grid + blockIdx.x] = acc.d[0];
                         part[(size_t)((ph & 1) * 4 + 1) * grid + blockIdx.x] = acc.d[1];
                     }
                     if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
                     if (!upd_r) break;
-                    group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 2, sh.sums);
+                    group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 2, sh.sums, [&](const double* s) {
+                        const double rho_new = s[0], rr1 = s[1];
+                        int stop = 1;
+                        if (!isfinite(rr1)) sh.status = DERR_NONFINITE;
+                        else if (sqrt(rr1) <= sh.thr) {}
+                        else if (rho_new == 0.0) sh.status = DERR_BREAKDOWN;
+                        else if (it >= a.maxit) sh.status = DERR_NOT_CONVERGED;
+                        else {
+                            sh.beta = (rho_new / sh.rho) * (sh.alpha / sh.omega);
+                            sh.rho = rho_new;
+                            stop = 0;
+                        }
+                        sh.flag = stop;
+                    });
                     ++ph;
                 }
-                const double rho_new = sh.sums[0], rr1 = sh.sums[1];
-                if (!isfinite(rr1)) { status = DERR_NONFINITE; break; }
-                if (sqrt(rr1) <= thr) break;
-                if (rho_new == 0.0) { status = DERR_BREAKDOWN; break; }
-                if (it >= a.maxit) { status = DERR_NOT_CONVERGED; break; }
-                beta = (rho_new / rho) * (alpha / omega);
-                rho = rho_new;
+                if (sh.flag) break;
             }
             dvalid = it > 0;
             its_total += it;
             its_max = max(its_max, it);
             // a non-finite state would only propagate: skip the remaining steps
-            if (status == DERR_NONFINITE) break;
+            if (sh.status == DERR_NONFINITE) break;
         }
         // ---------------- final: u_S = u_{S-1} + delta ; snapshot of u_S
         {
@@ -901,7 +966,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             }
         }
         if (q == 0 && threadIdx.x == 0) {
-            a.status[b] = status;
+            a.status[b] = sh.status;
             a.its_total[b] = (int)its_total;
             a.its_max[b] = its_max;
         }

@@ -49,7 +49,7 @@ def test_speedup_model_limits():
 def test_fine_traffic_model():
     import bench
     # FP32: 16 + 12 + 8 (f) + 17*4*n_it + 4/dM
-    assert bench.fine_bytes_per_dof_step(4, 3.0, 5, True) == 16 + 12 + 8 + 204 + 0.8
+    assert bench.fine_bytes_per_dof_step(4, 3.0, 5, True) == 16 + 12 + 4 + 204 + 1.6
     assert bench.fine_bytes_per_dof_step(8, 2.0, 4, False) == 16 + 24 + 272 + 2
 
 
