@@ -150,20 +150,24 @@ cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols, void* cons
 // z +- 1 from the adjacent slots).  Global traffic per point and phase is one load per
 // input vector (plus the 2/TY halo rows and 2/slab halo planes) and one store per output.
 
-// Per-thread partial sums: KT = float accumulates 16 points in float, then in double.
+// Per-thread partial sums in two levels: runs of 16 ticks accumulate in f, the runs in
+// s, both in KT.  The FP32 mode thus keeps its dot products off GB300's narrow FP64 pipe
+// (a double flush per run cost a conversion and an addition there); cta_sum then gives
+// the CTA total in double.
 template <typename KT, int NQ>
 struct Acc {
-    double d[NQ];
+    double d[NQ];   // CTA total, valid in thread 0 after cta_sum
+    KT s[NQ];
     KT f[NQ];
     int c;
     __device__ __forceinline__ void init() {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) { d[q] = 0.0; f[q] = (KT)0; }
+        for (int q = 0; q < NQ; ++q) { d[q] = 0.0; s[q] = (KT)0; f[q] = (KT)0; }
         c = 0;
     }
     __device__ __forceinline__ void flush() {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) { d[q] += (double)f[q]; f[q] = (KT)0; }
+        for (int q = 0; q < NQ; ++q) { s[q] += f[q]; f[q] = (KT)0; }
         c = 0;
     }
     __device__ __forceinline__ void tick() {
@@ -171,20 +175,26 @@ struct Acc {
     }
 };
 
-// CTA sum of NQ per-thread partials, valid in thread 0 (fixed order).  With KT = float
-// the in-warp tree runs in float: GB300's FP64 pipe would spend five double additions
-// per thread and quantity on it, and the FP32 Krylov scalars do not need more.
+// CTA sum of the per-thread partials acc.s into acc.d (thread 0, fixed order).  With
+// KT = float the in-warp tree runs in float and only the warp totals are added in double.
 template <typename KT, int NQ>
-__device__ __forceinline__ void cta_sum(double (&v)[NQ], double* red) {
+__device__ __forceinline__ void cta_sum(Acc<KT, NQ>& acc, double* red) {
     if constexpr (std::is_same<KT, double>::value) {
+        double v[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] = acc.s[q];
         block_sum<NQ>(v, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc.d[q] = v[q];
+        }
     } else {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int nwarps = (blockDim.x + 31) >> 5;
         float w[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            w[q] = (float)v[q];
+            w[q] = acc.s[q];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) w[q] += __shfl_down_sync(0xffffffffu, w[q], off);
         }
@@ -197,9 +207,9 @@ __device__ __forceinline__ void cta_sum(double (&v)[NQ], double* red) {
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                double s = 0.0;
-                for (int i = 0; i < nwarps; ++i) s += red[q * 32 + i];
-                v[q] = s;
+                double t = 0.0;
+                for (int i = 0; i < nwarps; ++i) t += red[q * 32 + i];
+                acc.d[q] = t;
             }
         }
     }
@@ -693,7 +703,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             }
             {
                 acc.flush();
-                cta_sum<KT, 2>(acc.d, sh.red);
+                cta_sum<KT, 2>(acc, sh.red);
                 if (threadIdx.x == 0) {
                     part[(size_t)((ph & 1) * 4 + 0) * grid + blockIdx.x] = acc.d[0];
                     part[(size_t)((ph & 1) * 4 + 1) * grid + blockIdx.x] = acc.d[1];
@@ -757,7 +767,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               acc.tick();
                           });
                     acc.flush();
-                    cta_sum<KT, 1>(acc.d, sh.red);
+                    cta_sum<KT, 1>(acc, sh.red);
                     if (threadIdx.x == 0) part[(size_t)((ph & 1) * 4) * grid + blockIdx.x] = acc.d[0];
                 }
                 if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
@@ -804,7 +814,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               acc.tick();
                           });
                     acc.flush();
-                    cta_sum<KT, 3>(acc.d, sh.red);
+                    cta_sum<KT, 3>(acc, sh.red);
                     if (threadIdx.x == 0) {
                         for (int qq = 0; qq < 3; ++qq)
                             part[(size_t)((ph & 1) * 4 + qq) * grid + blockIdx.x] = acc.d[qq];
@@ -882,7 +892,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               });
                     }
                     acc.flush();
-                    cta_sum<KT, 2>(acc.d, sh.red);
+                    cta_sum<KT, 2>(acc, sh.red);
                     if (threadIdx.x == 0 && upd_r) {
                         part[(size_t)((ph & 1) * 4 + 0) * grid + blockIdx.x] = acc.d[0];
                         part[(size_t)((ph & 1) * 4 + 1) * grid + blockIdx.x] = acc.d[1];
