@@ -158,6 +158,25 @@ pr_status pr_fine_sweep(pr_ctx* ctx, int k);
 pr_status pr_pod_update(pr_ctx* ctx, int k);
 pr_status pr_coarse_sweep(pr_ctx* ctx, int k);
 
+/* pr_fine_sweep for several contexts at once (no counterpart in the paper: it serves
+ * several problems on one GPU).  ks[i] is the iteration of ctxs[i]; all contexts need
+ * the same n, box and precision, count <= 16, each context at most once.  Their
+ * subintervals share one persistent launch of the fine kernel, one job per context,
+ * issued on the stream of the context with the most CTA groups and ordered after each
+ * context's earlier work and before its later work; each context then continues with
+ * pr_pod_update.  With a fixed pr_opts.group_ctas the results are bit-identical to
+ * pr_fine_sweep on each context alone.  A launch-wide device error (barrier time-out) is
+ * recorded in that owning context only.  Asynchronous. */
+pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count);
+
+/* Autotuner of the fine launch shape (no counterpart in the paper): times `steps` fine
+ * steps of all n_sub subintervals from the current iterate for CTA-group sizes
+ * G = (n / tile rows) * 2^j up to the co-resident CTA count, keeps the fastest in the
+ * context (pr_opts.group_ctas) and returns it (best_ms: its time, may be NULL).  Needs
+ * iteration 0 done and no phase of the next iteration started; leaves the iterate
+ * unchanged.  Synchronises. */
+pr_status pr_tune_fine(pr_ctx* ctx, int steps, int* best_group_ctas, double* best_ms);
+
 /* Convergence after pr_coarse_sweep(k): max increment max_n ||U^k_n-U^{k-1}_n||/||U^k_n||
  * and, if a reference is set, the max error of eq. (error).  Synchronises; also returns
  * any error a kernel recorded since the last check. */
@@ -259,6 +278,69 @@ pr_status pr_op_coarse_update(pr_ctx* ctx, const void* d_R, int m, const double*
  * no ordering) race on it.  The paper has no counterpart: this is library plumbing. */
 pr_status pr_op_apply_L_noalloc(pr_ctx* ctx, const double* d_in, double* d_out, int count,
                                 int transpose);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving (no counterpart in the paper, which solves one problem at a time on a CPU
+ * cluster): parareal solves of different n, flows and eps arrive over time and share the
+ * GPU by continuous batching.
+ *
+ * A submitted request waits in arrival order until its workspace (pr_workspace_bytes)
+ * fits the memory budget next to the resident requests and the resident cap allows it;
+ * it is then admitted (device workspace and stream of its own, initial state copied,
+ * iteration 0 run) and stays resident until it finishes.  Each pr_server_step advances
+ * every resident request by one parareal iteration: fine sweeps of requests with the
+ * same n, box and precision share persistent launches (pr_fine_sweep_batch, up to 16
+ * requests each); then every request's POD update and coarse sweep are issued on its
+ * own stream before any is waited for, so that they overlap on the device; then the
+ * convergence checks.  A request finishes when its max increment
+ * max_n ||U^k_n - U^{k-1}_n|| / ||U^k_n|| <= tol or k = k_max; U^k_N (the state at the
+ * end of the horizon) is copied to host memory and the workspace released, and waiting
+ * requests are admitted in the same step.  The fine CTA-group size is tuned once per
+ * (n, box, precision) by pr_tune_fine on the first request admitted with
+ * opts.group_ctas = 0 and used for every later request of that shape; a request with
+ * group_ctas > 0 keeps its own, and then gives the same result alone and in a mix.
+ * Single-threaded: one thread calls the pr_server_* functions of a server.
+ * ------------------------------------------------------------------------------------ */
+typedef struct pr_server pr_server;
+typedef struct pr_server_opts {
+    size_t hbm_budget;   /* bytes of request workspaces resident at once; 0: 90% of the
+                            device memory free at pr_server_create */
+    int max_active;      /* resident requests at once; 0: memory is the only limit */
+    int batch_fine;      /* 1 (default): shared fine launches; 0: one launch per request */
+} pr_server_opts;
+typedef struct pr_request {
+    pr_grid grid;
+    pr_flow flow;
+    double eps, T;
+    int n_sub;
+    double dt_fine;
+    double pod_tol;
+    pr_opts opts;        /* as for pr_create */
+    const double* u0;    /* host n^3 doubles, copied by pr_server_submit */
+    const double* f;     /* host n^3 doubles or NULL, copied */
+    double tol;          /* increment tolerance, > 0 */
+    int k_max;           /* <= 0 or > n_sub: n_sub */
+} pr_request;
+enum { PR_REQ_PENDING = 0, PR_REQ_ACTIVE = 1, PR_REQ_DONE = 2, PR_REQ_FAILED = 3 };
+
+void pr_server_opts_init(pr_server_opts* opts);
+/* opts may be NULL (defaults).  Allocates nothing on the device. */
+pr_status pr_server_create(const pr_server_opts* opts, pr_server** out);
+/* Releases every request's device memory and stream. */
+void pr_server_destroy(pr_server* srv);
+/* Queue a request; *id numbers requests 0, 1, 2, ... in submission order. */
+pr_status pr_server_submit(pr_server* srv, const pr_request* req, int* id);
+/* Admit, advance every resident request by one iteration, retire finished ones, admit
+ * again.  n_active / n_pending (may be NULL): resident and waiting requests after the
+ * step.  Synchronises (the checks read increments). */
+pr_status pr_server_step(pr_server* srv, int* n_active, int* n_pending);
+/* state: PR_REQ_*, k: iterations done, max_inc: increment of the last check. */
+pr_status pr_server_query(pr_server* srv, int id, int* state, int* k, double* max_inc);
+/* U^k_N of a finished request (n^3 doubles, host).  PR_ERR_STATE if not finished. */
+pr_status pr_server_result(pr_server* srv, int id, double* host_out);
+/* Why a request failed ("" otherwise), and the last error of a server call. */
+const char* pr_server_request_error(const pr_server* srv, int id);
+const char* pr_server_last_error(const pr_server* srv);
 
 #ifdef __cplusplus
 }

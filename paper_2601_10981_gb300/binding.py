@@ -52,6 +52,19 @@ class pr_report(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class pr_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("batch_fine", C.c_int)]
+
+
+class pr_request(C.Structure):
+    _fields_ = [("grid", pr_grid), ("flow", pr_flow), ("eps", C.c_double), ("T", C.c_double),
+                ("n_sub", C.c_int), ("dt_fine", C.c_double), ("pod_tol", C.c_double),
+                ("opts", pr_opts), ("u0", C.POINTER(C.c_double)), ("f", C.POINTER(C.c_double)),
+                ("tol", C.c_double), ("k_max", C.c_int)]
+
+
+PR_REQ_PENDING, PR_REQ_ACTIVE, PR_REQ_DONE, PR_REQ_FAILED = 0, 1, 2, 3
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
@@ -91,6 +104,17 @@ _SIGS = {
     "pr_op_pod": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _P, _I]),
     "pr_op_coarse_update": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, _P]),
     "pr_op_apply_L_noalloc": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
+    "pr_fine_sweep_batch": (C.c_int, [C.POINTER(_P), _I, C.c_int]),
+    "pr_tune_fine": (C.c_int, [_P, C.c_int, _I, _D]),
+    "pr_server_opts_init": (None, [C.POINTER(pr_server_opts)]),
+    "pr_server_create": (C.c_int, [C.POINTER(pr_server_opts), C.POINTER(_P)]),
+    "pr_server_destroy": (None, [_P]),
+    "pr_server_submit": (C.c_int, [_P, C.POINTER(pr_request), _I]),
+    "pr_server_step": (C.c_int, [_P, _I, _I]),
+    "pr_server_query": (C.c_int, [_P, C.c_int, _I, _I, _D]),
+    "pr_server_result": (C.c_int, [_P, C.c_int, _D]),
+    "pr_server_request_error": (C.c_char_p, [_P, C.c_int]),
+    "pr_server_last_error": (C.c_char_p, [_P]),
 }
 
 _lib = None
@@ -311,6 +335,13 @@ class Parareal:
     def sync(self):
         self._check(self._lib.pr_sync(self.ctx))
 
+    def tune_fine(self, steps: int = 8):
+        """pr_tune_fine: the fastest CTA-group size of the fine launch (kept in the context)
+        and its time in ms."""
+        G, ms = C.c_int(), C.c_double()
+        self._check(self._lib.pr_tune_fine(self.ctx, steps, C.byref(G), C.byref(ms)))
+        return G.value, ms.value
+
     # ------------------------------------------------------------------ single ops
     def op_apply_L(self, u, transpose: bool = False):
         """u: torch float64 tensor (count, n, n, n) on the GPU."""
@@ -352,3 +383,81 @@ class Parareal:
 
 def launch_count() -> int:
     return int(lib().pr_launch_count())
+
+
+def fine_sweep_batch(problems: Sequence[Parareal], ks: Sequence[int]):
+    """pr_fine_sweep_batch: the fine sweeps of several problems in one persistent launch."""
+    arr = (C.c_void_p * len(problems))(*[p.ctx.value for p in problems])
+    kk = (C.c_int * len(ks))(*ks)
+    st = lib().pr_fine_sweep_batch(arr, kk, len(problems))
+    if st != PR_OK:
+        raise PRError(st, lib().pr_last_error(problems[0].ctx).decode())
+
+
+class Server:
+    """pr_server: continuous batching of parareal requests on one GPU."""
+
+    def __init__(self, hbm_budget: int = 0, max_active: int = 0, batch_fine: bool = True):
+        self._lib = lib()
+        o = pr_server_opts()
+        self._lib.pr_server_opts_init(C.byref(o))
+        o.hbm_budget, o.max_active, o.batch_fine = hbm_budget, max_active, int(batch_fine)
+        srv = C.c_void_p()
+        st = self._lib.pr_server_create(C.byref(o), C.byref(srv))
+        if st != PR_OK:
+            raise PRError(st, "pr_server_create failed")
+        self.srv = srv
+        self._n = {}
+
+    def _check(self, st: int):
+        if st != PR_OK:
+            raise PRError(st, self._lib.pr_server_last_error(self.srv).decode())
+
+    def submit(self, w, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float = 1e-6,
+               k_max: int = 0, precision: int = PR_FP32, **opt_kw) -> int:
+        """Queue the problem of workload w (pr_inputs.Workload fields) with initial state u0."""
+        fl = w.flow
+        r = pr_request()
+        r.grid = pr_grid(w.n, 0.0)
+        r.flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2))
+        r.eps, r.T, r.n_sub, r.dt_fine, r.pod_tol = w.eps, w.T, w.n_sub, w.dt, w.pod_tol
+        r.opts = opts(n_snap=w.n_snap, m_cap=w.m_cap, m_l=w.m_l, p=w.p, precision=precision, **opt_kw)
+        u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
+        fa = None if f is None else np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        r.u0 = _dptr(u0)
+        r.f = _dptr(fa)
+        r.tol, r.k_max = tol, k_max
+        rid = C.c_int()
+        self._check(self._lib.pr_server_submit(self.srv, C.byref(r), C.byref(rid)))
+        self._n[rid.value] = w.n
+        return rid.value
+
+    def step(self):
+        a, p = C.c_int(), C.c_int()
+        self._check(self._lib.pr_server_step(self.srv, C.byref(a), C.byref(p)))
+        return a.value, p.value
+
+    def query(self, rid: int):
+        st, k, inc = C.c_int(), C.c_int(), C.c_double()
+        self._check(self._lib.pr_server_query(self.srv, rid, C.byref(st), C.byref(k), C.byref(inc)))
+        return st.value, k.value, inc.value
+
+    def result(self, rid: int) -> np.ndarray:
+        n = self._n[rid]
+        out = np.empty((n, n, n))
+        self._check(self._lib.pr_server_result(self.srv, rid, _dptr(out)))
+        return out
+
+    def request_error(self, rid: int) -> str:
+        return self._lib.pr_server_request_error(self.srv, rid).decode()
+
+    def close(self):
+        if getattr(self, "srv", None):
+            self._lib.pr_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

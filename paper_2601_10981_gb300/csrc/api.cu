@@ -429,27 +429,32 @@ pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int
     const bool f32 = c->fp32 && !force_fp64;
     FineArgs a{};
     a.g = grid_of(c);
-    a.S = steps;
-    a.dM = c->dM;
-    a.n_snap = snap ? n_snap : 0;
-    a.dt = c->dt;
-    a.f = c->has_f ? c->f : nullptr;
-    a.f32 = c->has_f ? c->f32 : nullptr;
+    a.njobs = 1;
+    FineJob& J = a.jobs[0];
+    J.tab = c->tab;
+    J.eps = c->eps;
+    J.dt = c->dt;
+    J.S = steps;
+    J.dM = c->dM;
+    J.n_snap = snap ? n_snap : 0;
+    J.f = c->has_f ? c->f : nullptr;
+    J.f32 = c->has_f ? c->f32 : nullptr;
+    J.u_in = u_in;
+    J.u_out = u_out;
+    J.snap = snap;
+    J.tol = force_fp64 ? std::min(c->lin_tol, 1e-14) : c->lin_tol;
+    J.maxit = c->o.lin_maxit;
+    J.status = c->fstatus + stat_off;
+    J.its_total = c->fits + stat_off;
+    J.its_max = c->fitsmax + stat_off;
+    J.B = B;
     a.B = B;
-    a.u_in = u_in;
-    a.u_out = u_out;
-    a.snap = snap;
     a.ws = c->fws;
     a.ust = c->ust;
     a.part = c->fpart;
     a.bar = c->fbar;
     a.G = c->o.group_ctas;
-    a.tol = force_fp64 ? std::min(c->lin_tol, 1e-14) : c->lin_tol;
-    a.maxit = c->o.lin_maxit;
     a.spin_limit = c->o.spin_limit;
-    a.status = c->fstatus + stat_off;
-    a.its_total = c->fits + stat_off;
-    a.its_max = c->fitsmax + stat_off;
     a.err = c->derr;
     int max_groups = force_fp64 && c->fp32 ? 1 : c->groups_max;
     PR_CUDA(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned) * 2 * c->groups_max, c->st));
@@ -756,6 +761,121 @@ pr_status pr_fine_sweep(pr_ctx* c, int k) {
                            c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S, c->ns, k - 1, false);
     if (s != PR_OK) return s;
     c->phase = 1;
+    return PR_OK;
+}
+
+pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
+    if (!ctxs || !ks || count < 1) return PR_ERR_INVALID_ARG;
+    if (count > FINE_MAX_JOBS) return fail(ctxs[0], PR_ERR_INVALID_ARG, "more contexts than one fine launch holds");
+    pr_ctx* owner = nullptr;
+    for (int i = 0; i < count; ++i) {
+        pr_ctx* c = ctxs[i];
+        if (!c) return PR_ERR_INVALID_ARG;
+        const int k = ks[i];
+        if (k < 1 || k > c->N) return fail(c, PR_ERR_INVALID_ARG, "k out of range");
+        if (c->k_done != k - 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "pr_fine_sweep_batch out of order");
+        if (!c->ws_ready) return fail(c, PR_ERR_STATE, "workspace not initialised (pr_set_initial first)");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(c, PR_ERR_INVALID_ARG, "a context appears twice");
+        if (owner && (c->n != owner->n || c->L != owner->L || c->fp32 != owner->fp32))
+            return fail(c, PR_ERR_INVALID_ARG, "batched contexts need the same grid and precision");
+        if (!owner || c->groups_max > owner->groups_max) owner = c;
+    }
+    FineArgs a{};
+    a.g = grid_of(owner);
+    a.njobs = count;
+    a.B = 0;
+    for (int i = 0; i < count; ++i) {
+        pr_ctx* c = ctxs[i];
+        const int k = ks[i];
+        const long long Ng = c->Ng;
+        FineJob& J = a.jobs[i];
+        J.tab = c->tab;
+        J.eps = c->eps;
+        J.dt = c->dt;
+        J.S = c->S;
+        J.dM = c->dM;
+        J.n_snap = c->ns;
+        J.f = c->has_f ? c->f : nullptr;
+        J.f32 = c->has_f ? c->f32 : nullptr;
+        J.u_in = c->Ubuf[c->cur] + (size_t)(k - 1) * Ng;
+        J.u_out = c->Fend + (size_t)(k - 1) * Ng;
+        J.snap = c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz;
+        J.tol = c->lin_tol;
+        J.maxit = c->o.lin_maxit;
+        J.status = c->fstatus + (k - 1);
+        J.its_total = c->fits + (k - 1);
+        J.its_max = c->fitsmax + (k - 1);
+        J.B = c->N - k + 1;
+        a.B += J.B;
+    }
+    a.ws = owner->fws;
+    a.ust = owner->ust;
+    a.part = owner->fpart;
+    a.bar = owner->fbar;
+    a.G = owner->o.group_ctas;
+    a.spin_limit = owner->o.spin_limit;
+    a.err = owner->derr;
+    // order: each context's earlier work -> the launch on the owner's stream -> each
+    // context's later work
+    for (int i = 0; i < count; ++i) {
+        pr_ctx* c = ctxs[i];
+        if (c == owner) continue;
+        PR_CUDA(cudaEventRecord(c->ev[7], c->st));
+        PR_CUDA(cudaStreamWaitEvent(owner->st, c->ev[7], 0));
+    }
+    {
+        pr_ctx* c = owner;
+        PR_CUDA(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned) * 2 * c->groups_max, c->st));
+        PR_CUDA(launch_fine(a, c->fp32, c->o.ctas_per_sm, c->groups_max, c->st));
+        PR_CUDA(cudaEventRecord(c->ev[7], c->st));
+    }
+    for (int i = 0; i < count; ++i) {
+        pr_ctx* c = ctxs[i];
+        if (c == owner) continue;
+        PR_CUDA(cudaStreamWaitEvent(c->st, owner->ev[7], 0));
+    }
+    for (int i = 0; i < count; ++i) ctxs[i]->phase = 1;
+    return PR_OK;
+}
+
+pr_status pr_tune_fine(pr_ctx* c, int steps, int* best_group_ctas, double* best_ms) {
+    if (!c || !best_group_ctas) return PR_ERR_INVALID_ARG;
+    if (c->k_done < 0 || c->phase != 0 || !c->ws_ready)
+        return fail(c, PR_ERR_STATE, "pr_tune_fine needs iteration 0 done and no phase in progress");
+    steps = std::max(1, std::min(steps, c->S));
+    const int NY = c->n / fine_tile_rows(c->n);
+    const int maxc = fine_max_ctas(c->n, c->fp32, c->o.ctas_per_sm);
+    const double* u_in = c->Ubuf[c->cur];
+    const int B = c->N;
+    double best = 1e300;
+    int bestG = 0;
+    for (int z = 1; NY * z <= maxc && z <= c->n; z *= 2) {
+        c->o.group_ctas = NY * z;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
+            PR_CUDA(cudaEventRecord(c->ev[0], c->st));
+            pr_status s = run_fine(c, u_in, c->Fend, nullptr, B, steps, 0, 0, false);
+            if (s != PR_OK) return s;
+            PR_CUDA(cudaEventRecord(c->ev[1], c->st));
+        }
+        PR_CUDA(cudaEventSynchronize(c->ev[1]));
+        PR_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        if (ms < best) {
+            best = ms;
+            bestG = c->o.group_ctas;
+        }
+    }
+    c->o.group_ctas = bestG;
+    // the tuning sweeps leave no state behind: statuses and counts are cleared, F_n is
+    // rewritten by the next fine sweep
+    PR_CUDA(cudaMemsetAsync(c->fstatus, 0, sizeof(int) * (c->N + 1), c->st));
+    PR_CUDA(cudaMemsetAsync(c->fits, 0, sizeof(int) * (c->N + 1), c->st));
+    PR_CUDA(cudaMemsetAsync(c->fitsmax, 0, sizeof(int) * (c->N + 1), c->st));
+    pr_status s = read_device_errors(c);
+    if (s != PR_OK) return s;
+    *best_group_ctas = bestG;
+    if (best_ms) *best_ms = best;
     return PR_OK;
 }
 

@@ -362,17 +362,12 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     constexpr bool DF = std::is_same<KT, float>::value;   // double-float state
     (void)ringd;
     (void)ringf;
-    for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) {
-        const double v = a.g.tab[i];
-        tabd[i] = v;
-        tabk[i] = (KT)(v * a.dt * 0.5 / a.g.h);
-    }
-    __syncthreads();
-
-    const double h = a.g.h, eps = a.g.eps, dt = a.dt;
-    const double inv2h = 0.5 / h, epsh2 = eps / (h * h);
-    const KT c1 = (KT)(dt * eps / (h * h));
-    const KT c0 = (KT)(1.0 + 6.0 * dt * eps / (h * h));
+    // per-job constants (a launch can hold subintervals of several problems on the same
+    // grid, see FineJob); set by load_job
+    const double h = a.g.h;
+    const double inv2h = 0.5 / h;
+    double dt = 0.0, epsh2 = 0.0;
+    KT c1 = (KT)0, c0 = (KT)1;
 
     KT* Wk = reinterpret_cast<KT*>(a.ws) + (size_t)g * FINE_NVEC * Ng;
     KT* delta = Wk;
@@ -393,11 +388,27 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     // pre-scaled by dt/(2h) for the Krylov operator.  x-terms per thread, y-terms per owned
     // row slot (set per tile), z-terms per plane.
     KT ky_x[W], kz_x[W];
+    int cur_job = -1;
+    auto load_job = [&](int jb) {
+        const FineJob& J = a.jobs[jb];
+        __syncthreads();   // nobody reads the previous job's tables any more
+        for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) {
+            const double v = J.tab[i];
+            tabd[i] = v;
+            tabk[i] = (KT)(v * J.dt * 0.5 / h);
+        }
+        __syncthreads();
+        dt = J.dt;
+        epsh2 = J.eps / (h * h);
+        c1 = (KT)(dt * J.eps / (h * h));
+        c0 = (KT)(1.0 + 6.0 * dt * J.eps / (h * h));
 #pragma unroll
-    for (int e = 0; e < W; ++e) {
-        ky_x[e] = tabk[TYX * n + x0 + e];
-        kz_x[e] = tabk[TZX * n + x0 + e];
-    }
+        for (int e = 0; e < W; ++e) {
+            ky_x[e] = tabk[TYX * n + x0 + e];
+            kz_x[e] = tabk[TZX * n + x0 + e];
+        }
+        cur_job = jb;
+    };
     KT kx_y[KS], kz_y[KS];
     KT kx_z = 0, ky_z = 0;
     auto tile_terms = [&](int y0) {
@@ -556,23 +567,29 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     using VD = Vec<double, W>;
 
     for (int b = g; b < a.B; b += a.numGroups) {
-        const double* u_in = a.u_in + (size_t)b * Ng;
-        double* snap_b = a.snap ? reinterpret_cast<double*>(a.snap) + (size_t)b * a.n_snap * Ng : nullptr;
+        // job of item b and its index lb within the job
+        int jb = 0, lb = b;
+        while (jb + 1 < a.njobs && lb >= a.jobs[jb].B) lb -= a.jobs[jb++].B;
+        if (jb != cur_job) load_job(jb);
+        const FineJob& J = a.jobs[jb];
+        const int S = J.S, dM = J.dM, n_snap = J.n_snap;
+        const double* u_in = J.u_in + (size_t)lb * Ng;
+        double* snap_b = J.snap ? reinterpret_cast<double*>(J.snap) + (size_t)lb * n_snap * Ng : nullptr;
         long long its_total = 0;
         int its_max = 0;
         bool dvalid = false;
         __syncthreads();
         if (threadIdx.x == 0) sh.status = 0;
 
-        for (int j = 1; j <= a.S; ++j) {
+        for (int j = 1; j <= S; ++j) {
             // ---------------- setup: u_{j-1} = u_{j-2} + delta ; r = rhat = dt (f - L u_{j-1})
             const double* P = (j <= 2) ? u_in : ust + (size_t)((j - 2) & 1) * Ng;
             double* Wt = (j >= 2) ? ust + (size_t)((j - 1) & 1) * Ng : nullptr;
             const bool use_d = (j >= 2) && dvalid;
             double* snap_j = nullptr;
-            if (snap_b && (j - 1) % a.dM == 0 && (j - 1) / a.dM < a.n_snap)
-                snap_j = snap_b + (size_t)((j - 1) / a.dM) * Ng;
-            const double* fp = a.f;
+            if (snap_b && (j - 1) % dM == 0 && (j - 1) / dM < n_snap)
+                snap_j = snap_b + (size_t)((j - 1) / dM) * Ng;
+            const double* fp = J.f;
             Acc<KT, 2> acc;
             acc.init();
             if constexpr (!DF) {
@@ -631,7 +648,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 // double-float state: the same residual, FP32 arithmetic only
                 const float2* Pf = (j <= 2) ? nullptr : reinterpret_cast<const float2*>(P);
                 float2* Wf = reinterpret_cast<float2*>(Wt);
-                const float* ff = a.f32;
+                const float* ff = J.f32;
                 const KT dtf = (KT)dt;
                 march(false, ringf,
                       [&](int i) -> RawSetup<float2, KT, W> {
@@ -712,7 +729,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
             group_sums(part + (size_t)(ph & 1) * 4 * grid, grid, g0, G, 2, sh.sums, [&](const double* s) {
                 const double rr0 = s[0], bb = s[1];
-                sh.thr = a.tol * sqrt(bb);
+                sh.thr = J.tol * sqrt(bb);
                 int conv = sqrt(rr0) <= sh.thr;
                 if (!isfinite(rr0) || !isfinite(bb)) { sh.status = DERR_NONFINITE; conv = 1; }
                 sh.flag = conv;
@@ -905,7 +922,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                         if (!isfinite(rr1)) sh.status = DERR_NONFINITE;
                         else if (sqrt(rr1) <= sh.thr) {}
                         else if (rho_new == 0.0) sh.status = DERR_BREAKDOWN;
-                        else if (it >= a.maxit) sh.status = DERR_NOT_CONVERGED;
+                        else if (it >= J.maxit) sh.status = DERR_NOT_CONVERGED;
                         else {
                             sh.beta = (rho_new / sh.rho) * (sh.alpha / sh.omega);
                             sh.rho = rho_new;
@@ -925,11 +942,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         }
         // ---------------- final: u_S = u_{S-1} + delta ; snapshot of u_S
         {
-            const int S = a.S;
             const double* P = (S >= 2) ? ust + (size_t)((S - 1) & 1) * Ng : u_in;
-            double* snap_S = (snap_b && S % a.dM == 0 && S / a.dM < a.n_snap)
-                                 ? snap_b + (size_t)(S / a.dM) * Ng : nullptr;
-            double* outp = a.u_out + (size_t)b * Ng;
+            double* snap_S = (snap_b && S % dM == 0 && S / dM < n_snap)
+                                 ? snap_b + (size_t)(S / dM) * Ng : nullptr;
+            double* outp = J.u_out + (size_t)lb * Ng;
             const bool dv = dvalid;
             if constexpr (!DF) {
                 owned([&](int i) -> RawF<double, KT, W> {
@@ -976,9 +992,9 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             }
         }
         if (q == 0 && threadIdx.x == 0) {
-            a.status[b] = sh.status;
-            a.its_total[b] = (int)its_total;
-            a.its_max[b] = its_max;
+            J.status[lb] = sh.status;
+            J.its_total[lb] = (int)its_total;
+            J.its_max[lb] = its_max;
         }
         // The next subinterval's first setup reads only its own input state (and the
         // ring), and writes r/rhat at owned points, which no CTA of this group reads

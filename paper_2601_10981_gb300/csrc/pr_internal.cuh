@@ -125,17 +125,34 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* red) {
 
 // ---------------------------------------------------------------------------------
 // Fine sweep (a batch of independent implicit-Euler runs, one per subinterval).
-struct FineArgs {
-    Grid g;
+// One problem in a fine launch: B consecutive subintervals that share grid size, Krylov
+// type and tile geometry with the other jobs of the launch but have their own flow,
+// diffusion, step, forcing, buffers and tolerance.
+struct FineJob {
+    const double* tab;  // velocity tables [6][n]
+    double eps;
+    double dt;          // fine step
     int S;              // fine steps
     int dM, n_snap;     // snapshot stride / count (n_snap = 0: none)
-    double dt;          // fine step
     const double* f;    // forcing [Ng] or nullptr
     const float* f32;   // the same rounded to float (FP32 mode), nullptr without forcing
-    int B;              // subintervals in this launch
     const double* u_in; // [B][Ng]
     double* u_out;      // [B][Ng]
     void* snap;         // [B][n_snap][Ng] doubles, or nullptr
+    double tol;
+    int maxit;
+    int* status;        // [B] per-subinterval error code
+    int* its_total;     // [B]
+    int* its_max;       // [B]
+    int B;
+};
+constexpr int FINE_MAX_JOBS = 16;
+
+struct FineArgs {
+    Grid g;             // n, Ng, h (the per-job flow and eps are in jobs[])
+    int njobs;
+    FineJob jobs[FINE_MAX_JOBS];
+    int B;              // subintervals in this launch: the sum of jobs[].B
     void* ws;           // [numGroups][NVEC][Ng] of KT
     double* ust;        // [numGroups][2][Ng]
     double* part;       // [numGroups][2][4][n]
@@ -144,12 +161,7 @@ struct FineArgs {
     int numGroups;
     int TY, NY, NZ;     // tiles of a subinterval: NY blocks of TY rows x NZ slabs of planes
     int RP;             // rows per pass of a CTA (threads = n/W lanes x RP, rounded to warps)
-    double tol;
-    int maxit;
     long long spin_limit;
-    int* status;        // [B] per-subinterval error code
-    int* its_total;     // [B]
-    int* its_max;       // [B]
     int* err;           // launch-wide error code
 };
 constexpr int FINE_NVEC = 8; // delta, r, rhat, p0, p1, v0, v1, t
