@@ -246,6 +246,71 @@ def fine_bytes_per_dof_step(w_bytes: int, lin_iters: float, dM: int, has_f: bool
     return 16 + 3 * w_bytes + (w_bytes if has_f else 0) + lin_iters * 17 * w_bytes + 8 / dM
 
 
+def serving_sample(n_req: int, rate: float, t_scale: float, seed: int = 5):
+    """The first n_req requests of the mixed Poisson request stream (grids 32^3..128^3, ABC
+    or Kolmogorov flows, eps log-uniform in [0.002, 0.05], N in {16, 32, 64}; see
+    pr_inputs.serving_stream) with their horizons T scaled by t_scale, so that the whole
+    sample is served in about a minute."""
+    import dataclasses
+    import pr_inputs as pi
+    reqs = pi.serving_stream(n_req, rate, seed)
+    for r in reqs:
+        r["workload"] = dataclasses.replace(r["workload"], T=r["workload"].T * t_scale)
+    return reqs
+
+
+def run_serving(bd, n_req: int, rate: float, t_scale: float, tol: float = 1e-6):
+    """Serve the sample in real time: requests are submitted at their arrival times, the
+    server steps whenever it holds work; latency = finish - arrival."""
+    import math
+    import numpy as np
+    reqs = serving_sample(n_req, rate, t_scale)
+    srv = bd.Server()
+    ids, arrival, finish, work = {}, {}, {}, {}
+    nxt = 0
+    t0 = time.perf_counter()
+    active = pending = 0
+    while len(finish) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+            w = reqs[nxt]["workload"]
+            ids[nxt] = srv.submit(w, w.u0(), None, tol=tol, precision=bd.PR_FP32)
+            arrival[nxt] = reqs[nxt]["arrival"]
+            nxt += 1
+        if active == 0 and pending == 0 and nxt < len(reqs) and len(ids) == len(finish):
+            time.sleep(max(0.0, reqs[nxt]["arrival"] - (time.perf_counter() - t0)))
+            continue
+        active, pending = srv.step()
+        now = time.perf_counter() - t0
+        for i, rid in ids.items():
+            if i in finish:
+                continue
+            st, k, _ = srv.query(rid)
+            if st in (bd.PR_REQ_DONE, bd.PR_REQ_FAILED):
+                finish[i] = now
+                w = reqs[i]["workload"]
+                S = math.ceil(w.T / w.n_sub / w.dt - 1e-9)
+                # iteration 0 (one subinterval) + iterations 1..k over N-k+1 subintervals
+                work[i] = (S + sum(w.n_sub - kk + 1 for kk in range(1, k + 1)) * S) * w.n ** 3 \
+                    if st == bd.PR_REQ_DONE else 0
+                if st == bd.PR_REQ_FAILED:
+                    work[i] = -1
+    makespan = max(finish.values())
+    failed = sum(1 for v in work.values() if v < 0)
+    lat = np.array([finish[i] - arrival[i] for i in finish])
+    srv.close()
+    sizes = sorted({r["workload"].n for r in reqs})
+    return {
+        "requests": len(reqs), "failed": failed, "rate_per_s": rate,
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "throughput_req_per_s": len(reqs) / makespan,
+        "gdof_steps_per_s": sum(v for v in work.values() if v > 0) / makespan / 1e9,
+        "makespan_s": makespan, "grids": sizes, "tol_increment": tol, "precision": "fp32",
+        "sample": f"first {len(reqs)} requests of the seeded Poisson stream (rate {rate}/s), "
+                  f"horizons T x {t_scale}",
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -382,6 +447,9 @@ def run_ours(args):
                          "t_coarse": rep["t_coarse"], "t_iter0": rep["t_iter0"],
                          "sequential_fine_fp64_s": t_seq}
         s2.close()
+    if rank == 0 and args.serve_requests > 0:
+        s.close()
+        line["serving"] = run_serving(bd, args.serve_requests, args.serve_rate, args.serve_tscale)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -399,6 +467,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--solve", type=int, default=1, help="also time a full solve to 1e-6")
     ap.add_argument("--solve-kmax", type=int, default=0, help="0: N (finite termination)")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests of the mixed serving stream to serve (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=5.0)
+    ap.add_argument("--serve-tscale", type=float, default=0.1)
     ap.add_argument("--subintervals", type=int, default=0,
                     help="profiling: first N subintervals of the workload (same per-subinterval size)")
     ap.add_argument("--mode", default="bench", choices=["bench", "fine"],
