@@ -144,7 +144,7 @@ cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols, void* cons
 //
 // Ownership: the n^3 points of a subinterval are cut into NY x NZ tiles of TY rows (y) by
 // a slab of planes (z); CTA q of a group owns a contiguous range of tiles.  Stencil
-// phases march a tile plane by plane through a 3-plane shared-memory ring: the operand
+// phases march a tile plane by plane through a shared-memory ring of planes: the operand
 // of the stencil (u, p or s) is computed once per plane, with one halo row on each side
 // in y, and the 6 neighbours of a point come from the ring (x +- 1 wraps inside the row,
 // z +- 1 from the adjacent slots).  Global traffic per point and phase is one load per
@@ -297,6 +297,13 @@ __device__ __forceinline__ void vstore(T* p, const Vec<T, W>& o) {
     }
 }
 
+// Planes per barrier of the stencil march and slots of its shared-memory ring.  Two
+// planes per barrier halve the barriers but cost registers (spills) and expose the
+// owned-point loads of the second plane: 110 ms against 102 ms for the 64^3 Kolmogorov
+// sweep, so one plane per barrier stays.
+constexpr int FINE_PLANES = 1;
+constexpr int FINE_SLOTS = 2 * FINE_PLANES + 2;
+
 // Double-float state of the FP32 mode: u = hi + lo with |lo| <= ulp(hi) / 2.
 __device__ __forceinline__ float2 df_split(double u) {
     const float hi = __double2float_rn(u);
@@ -436,22 +443,26 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         xm.v[0] = row[xl];
     };
 
-    // ---- tile march for stencil phases (ring of 4 planes, one barrier per plane):
+    // ---- tile march for stencil phases (ring of FINE_SLOTS planes, one barrier per
+    // FINE_PLANES planes):
     //   load(i) -> Raw            inputs of the operand at the W points from index i
     //   opnd(Raw) -> Vec          operand values written into the ring
-    //   own(i) -> Own             inputs the output needs at owned points (one plane ahead)
+    //   own(i) -> Own             inputs the output needs at owned points
     //   out(i, k, y, Own, rowc, rowzp, rowzm)   per owned W points (k: row slot); rowc is
     //                             the ring row of the points, rowzp / rowzm the rows above /
     //                             below in z; rowc +- n are the y neighbours
-    // Plane z lives in slot (z - zlo + 1) & 3.  Iteration z commits plane z+1, then the
-    // barrier, then the stencil of plane z reads planes z-1, z, z+1.  A thread that runs
-    // ahead can only reach the commit of plane z+2, whose slot equals that of plane z-2,
-    // which no stencil of plane z or z+1 reads; the barrier of iteration z+1 stops it there.
-    //   pipe                       true: prefetch one plane ahead; false: load each plane
-    //                              just before committing it (fewer live registers)
+    // Plane p lives in slot (p - zlo + 1) mod FINE_SLOTS.  A round at z commits planes
+    // z+1 .. z+np (np <= PL), then the barrier, then the stencils of planes z .. z+np-1
+    // read planes z-1 .. z+np.  A thread that runs ahead can only reach the commits of
+    // the next round, planes z+np+1 .. z+2np, whose slots differ from those of z-1 .. z+np
+    // as long as 2 PL + 2 <= FINE_SLOTS; the next barrier stops it there.
+    //   pipe                       true: prefetch the next round's first plane during the
+    //                              stencils; false: load each plane just before committing
+    //                              it (fewer live registers)
     auto march = [&](bool pipe, auto* ring, auto&& load, auto&& opnd, auto&& own, auto&& out) {
         using Raw = decltype(load(0));
         using Own = decltype(own(0));
+        constexpr int PL = FINE_PLANES, NSL = FINE_SLOTS;
         for (int tt = t_lo; tt < t_hi; ++tt) {
             int y0, zlo, zhi;
             geo.tile(tt, y0, zlo, zhi);
@@ -472,16 +483,17 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 for (int k = 0; k < KF; ++k)
                     if (fidx[k] >= 0) pre[k] = load(zz * n2 + fidx[k]);
             };
-            auto prefetch_own = [&](int z) {
+            auto own_of = [&](int z, Own (&dst)[KS]) {
 #pragma unroll
                 for (int k = 0; k < KS; ++k)
-                    if (ty + k * RP < TY) opre[k] = own(z * n2 + (y0 + ty + k * RP) * n + x0);
+                    if (ty + k * RP < TY) dst[k] = own(z * n2 + (y0 + ty + k * RP) * n + x0);
             };
-            auto commit = [&](int slot) {
+            auto slot = [&](int p) { return (p - zlo + 1) % NSL; };
+            auto commit = [&](int sl) {
 #pragma unroll
                 for (int k = 0; k < KF; ++k) {
                     const int rr = ty + k * RP;
-                    if (fidx[k] >= 0) vstore(ring + (slot * RW + rr) * n + x0, opnd(pre[k]));
+                    if (fidx[k] >= 0) vstore(ring + (sl * RW + rr) * n + x0, opnd(pre[k]));
                 }
             };
             prefetch(zlo - 1);
@@ -490,31 +502,47 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             commit(1);
             if (pipe) {
                 prefetch(zlo + 1);
-                prefetch_own(zlo);
+                own_of(zlo, opre);
             }
-            int sm = 0;   // slot of plane z-1; z is sm+1, z+1 is sm+2 (mod 4)
-            for (int z = zlo; z < zhi; ++z) {
-                const int sc = (sm + 1) & 3, sp = (sm + 2) & 3;
-                if (!pipe) prefetch(z + 1);
-                commit(sp);
+            for (int z = zlo; z < zhi; z += PL) {
+                const int np = min(PL, zhi - z);
+#pragma unroll
+                for (int q = 1; q <= PL; ++q) {
+                    if (q > np) break;
+                    if (!pipe || q > 1) prefetch(z + q);
+                    commit(slot(z + q));
+                }
                 __syncthreads();
-                if (!pipe) prefetch_own(z);
-                Own cur[KS];
+                Own cur[PL][KS];
+                if (pipe) {
 #pragma unroll
-                for (int k = 0; k < KS; ++k) cur[k] = opre[k];
-                if (pipe && z + 1 < zhi) {
-                    prefetch(z + 2);
-                    prefetch_own(z + 1);
-                }
-                plane_terms(z);
+                    for (int k = 0; k < KS; ++k) cur[0][k] = opre[k];
 #pragma unroll
-                for (int k = 0; k < KS; ++k) {
-                    const int rr = ty + k * RP;
-                    if (rr >= TY) continue;
-                    out(z * n2 + (y0 + rr) * n + x0, k, y0 + rr, cur[k], ring + (sc * RW + rr + 1) * n,
-                        ring + (sp * RW + rr + 1) * n, ring + (sm * RW + rr + 1) * n);
+                    for (int q = 1; q < PL; ++q)
+                        if (q < np) own_of(z + q, cur[q]);
+                    if (z + np < zhi) {
+                        prefetch(z + np + 1);
+                        own_of(z + np, opre);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < PL; ++q)
+                        if (q < np) own_of(z + q, cur[q]);
                 }
-                sm = sc;
+#pragma unroll
+                for (int q = 0; q < PL; ++q) {
+                    if (q >= np) break;
+                    const int zq = z + q;
+                    const int sc = slot(zq), sp = slot(zq + 1), sm = slot(zq - 1);
+                    plane_terms(zq);
+#pragma unroll
+                    for (int k = 0; k < KS; ++k) {
+                        const int rr = ty + k * RP;
+                        if (rr >= TY) continue;
+                        out(zq * n2 + (y0 + rr) * n + x0, k, y0 + rr, cur[q][k], ring + (sc * RW + rr + 1) * n,
+                            ring + (sp * RW + rr + 1) * n, ring + (sm * RW + rr + 1) * n);
+                    }
+                }
             }
             __syncthreads();   // the next tile's prologue rewrites slots 0 and 1
         }
@@ -1005,7 +1033,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
 // ------------------------------------------------------------------------------------
 // Launch geometry.  W = 4 points per thread when n % 4 == 0, else 1.  A row has n/W
 // lanes; RP rows per pass of the CTA is the largest divisor of n with RP * n/W <= 256;
-// a tile has TY = KS * RP rows (KS in {1, 2}), its 4-plane FP64 ring within 64 KB.
+// a tile has TY = KS * RP rows (KS in {1, 2}), its FINE_SLOTS-plane 8-byte ring within 64 KB.
 struct FineGeom {
     int W, lanes, RP, TY, KS, KF, threads;
     size_t smem;
@@ -1019,12 +1047,13 @@ static FineGeom fine_geom(int n, bool fp32) {
     for (int rp = 1; rp <= n; ++rp)
         if (n % rp == 0 && rp * g.lanes <= 256) g.RP = rp;
     g.KS = 1;
-    if (n % (2 * g.RP) == 0 && 2 * g.RP <= 16 && (size_t)4 * (2 * g.RP + 2) * n * 8 <= 64 * 1024) g.KS = 2;
+    if (n % (2 * g.RP) == 0 && 2 * g.RP <= 16 && (size_t)FINE_SLOTS * (2 * g.RP + 2) * n * 8 <= 64 * 1024)
+        g.KS = 2;
     g.TY = g.KS * g.RP;
     g.KF = (g.TY + 2 + g.RP - 1) / g.RP;
     g.threads = (g.lanes * g.RP + 31) / 32 * 32;   // whole warps (full-mask shuffles)
     const size_t tabs = ((size_t)6 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 31) / 32 * 32;
-    g.smem = tabs + (size_t)4 * (g.TY + 2) * n * sizeof(double);
+    g.smem = tabs + (size_t)FINE_SLOTS * (g.TY + 2) * n * sizeof(double);
     return g;
 }
 
