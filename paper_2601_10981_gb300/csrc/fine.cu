@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 float2* Wf = reinterpret_cast<float2*>(Wt);
                 const float* ff = J.f32;
                 const KT dtf = (KT)dt;
-                march(false, ringf,
+                march(true, ringf,
                       [&](int i) -> RawSetup<float2, KT, W> {
                           RawSetup<float2, KT, W> o;
                           if (Pf) o.u = vload<float2, W>(Pf + i);
@@ -700,16 +700,18 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           for (int e = 0; e < W; ++e) o.v[e] = df_add(v.u.v[e], v.d.v[e]);
                           return o;
                       },
-                      [&](int) -> NoOwn { return NoOwn{}; },
-                      [&](int i, int k, int, const NoOwn&, const float2* rowc, const float2* rowzp,
-                          const float2* rowzm) {
-                          const auto q = nb7(rowc, rowzp, rowzm);
-                          VK fv;
-                          if (ff) fv = vload<KT, W>(ff + i);
+                      [&](int i) -> VK {
+                          VK fo;
+                          if (ff) fo = vload<KT, W>(ff + i);
                           else {
 #pragma unroll
-                              for (int e = 0; e < W; ++e) fv.v[e] = (KT)0;
+                              for (int e = 0; e < W; ++e) fo.v[e] = (KT)0;
                           }
+                          return fo;
+                      },
+                      [&](int i, int k, int, const VK& fv, const float2* rowc, const float2* rowzp,
+                          const float2* rowzm) {
+                          const auto q = nb7(rowc, rowzp, rowzm);
                           const KT ax = kx_y[k] + kx_z;
                           VK rv;
 #pragma unroll
