@@ -320,6 +320,25 @@ __device__ __forceinline__ float2 df_add(float2 u, float d) {
     return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
 }
 
+// float -> double by moving bits (exact; float denormals, |x| < 1.2e-38, read as zero):
+// keeps the FP64 pipe out of the snapshot conversion but for one addition.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long ed = (e == 255u) ? 2047ull : (unsigned long long)(e + (1023u - 127u));
+    const unsigned long long m = (unsigned long long)(b & 0x7fffffu) << 29;
+    return __longlong_as_double(e == 0u ? sgn : (sgn | (ed << 52) | m));
+}
+__device__ __forceinline__ double df_value_bits(float hi, float lo) { return f2d_bits(hi) + f2d_bits(lo); }
+
+// Operand of the FP32-mode setup march: the float pair of the state, stored in the ring
+// as two float planes (hi, then lo at a fixed offset), so that the stencil reads the hi
+// neighbours with float loads.
+template <int W> struct HiLo { Vec<float, W> hi, lo; };
+template <typename T> struct is_hilo : std::false_type {};
+template <int W> struct is_hilo<HiLo<W>> : std::true_type {};
+
 // Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
 template <typename ST, typename KT, int W> struct RawSetup { Vec<ST, W> u; Vec<KT, W> d; };
 template <typename KT, int W> struct RawP { Vec<KT, W> r, p, v; };
@@ -364,11 +383,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     KT* tabk = reinterpret_cast<KT*>(tabd + 6 * n);
     unsigned char* ring_raw = smem_raw + (((size_t)6 * n * (sizeof(double) + sizeof(KT)) + 31) / 32) * 32;
     double* ringd = reinterpret_cast<double*>(ring_raw);
-    float2* ringf = reinterpret_cast<float2*>(ring_raw);
     KT* ringk = reinterpret_cast<KT*>(ring_raw);
     constexpr bool DF = std::is_same<KT, float>::value;   // double-float state
+    // float offset of the lo planes of the FP32-mode setup ring (the ring's upper half)
+    const int ring_lo = FINE_SLOTS * (a.TY + 2) * n;
     (void)ringd;
-    (void)ringf;
     // per-job constants (a launch can hold subintervals of several problems on the same
     // grid, see FineJob); set by load_job
     const double h = a.g.h;
@@ -493,7 +512,15 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
 #pragma unroll
                 for (int k = 0; k < KF; ++k) {
                     const int rr = ty + k * RP;
-                    if (fidx[k] >= 0) vstore(ring + (sl * RW + rr) * n + x0, opnd(pre[k]));
+                    if (fidx[k] < 0) continue;
+                    auto* dst = ring + (sl * RW + rr) * n + x0;
+                    const auto val = opnd(pre[k]);
+                    if constexpr (is_hilo<std::decay_t<decltype(val)>>::value) {
+                        vstore(dst, val.hi);
+                        vstore(dst + ring_lo, val.lo);
+                    } else {
+                        vstore(dst, val);
+                    }
                 }
             };
             prefetch(zlo - 1);
@@ -678,7 +705,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 float2* Wf = reinterpret_cast<float2*>(Wt);
                 const float* ff = J.f32;
                 const KT dtf = (KT)dt;
-                march(true, ringf,
+                // residual from the hi parts (exact neighbour differences, Sterbenz); the
+                // neglected dt L(lo) is ~1e-7 of dt L(u), at the level of the solver
+                // tolerance; lo enters the state update and the snapshots
+                float* ringh = reinterpret_cast<float*>(ring_raw);
+                march(true, ringh,
                       [&](int i) -> RawSetup<float2, KT, W> {
                           RawSetup<float2, KT, W> o;
                           if (Pf) o.u = vload<float2, W>(Pf + i);
@@ -694,10 +725,14 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return o;
                       },
-                      [&](const RawSetup<float2, KT, W>& v) -> Vec<float2, W> {
-                          Vec<float2, W> o;
+                      [&](const RawSetup<float2, KT, W>& v) -> HiLo<W> {
+                          HiLo<W> o;
 #pragma unroll
-                          for (int e = 0; e < W; ++e) o.v[e] = df_add(v.u.v[e], v.d.v[e]);
+                          for (int e = 0; e < W; ++e) {
+                              const float2 u = df_add(v.u.v[e], v.d.v[e]);
+                              o.hi.v[e] = u.x;
+                              o.lo.v[e] = u.y;
+                          }
                           return o;
                       },
                       [&](int i) -> VK {
@@ -709,40 +744,43 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return fo;
                       },
-                      [&](int i, int k, int, const VK& fv, const float2* rowc, const float2* rowzp,
-                          const float2* rowzm) {
+                      [&](int i, int k, int, const VK& fv, const float* rowc, const float* rowzp,
+                          const float* rowzm) {
                           const auto q = nb7(rowc, rowzp, rowzm);
+                          const VK clo = vload<float, W>(rowc + ring_lo + x0);
                           const KT ax = kx_y[k] + kx_z;
                           VK rv;
 #pragma unroll
                           for (int e = 0; e < W; ++e) {
-                              const float2 c = q.c.v[e], xp = q.xp.v[e], xm = q.xm.v[e];
-                              const float2 yp = q.yp.v[e], ym = q.ym.v[e], zp = q.zp.v[e], zm = q.zm.v[e];
+                              const float c = q.c.v[e];
                               const KT ay = ky_x[e] + ky_z;
                               const KT az = kz_x[e] + kz_y[k];
-                              // central differences and second differences of hi, then lo
-                              const KT dx = __fadd_rn(__fsub_rn(xp.x, xm.x), __fsub_rn(xp.y, xm.y));
-                              const KT dy = __fadd_rn(__fsub_rn(yp.x, ym.x), __fsub_rn(yp.y, ym.y));
-                              const KT dz = __fadd_rn(__fsub_rn(zp.x, zm.x), __fsub_rn(zp.y, zm.y));
-                              const KT sx = __fsub_rn(__fsub_rn(xp.x, c.x), __fsub_rn(c.x, xm.x));
-                              const KT sy = __fsub_rn(__fsub_rn(yp.x, c.x), __fsub_rn(c.x, ym.x));
-                              const KT sz = __fsub_rn(__fsub_rn(zp.x, c.x), __fsub_rn(c.x, zm.x));
-                              const KT lo = ((xp.y + xm.y) + (yp.y + ym.y) + (zp.y + zm.y)) - 6.0f * c.y;
-                              const KT lap = ((sx + sy) + sz) + lo;
+                              const KT dx = __fsub_rn(q.xp.v[e], q.xm.v[e]);
+                              const KT dy = __fsub_rn(q.yp.v[e], q.ym.v[e]);
+                              const KT dz = __fsub_rn(q.zp.v[e], q.zm.v[e]);
+                              const KT sx = __fsub_rn(__fsub_rn(q.xp.v[e], c), __fsub_rn(c, q.xm.v[e]));
+                              const KT sy = __fsub_rn(__fsub_rn(q.yp.v[e], c), __fsub_rn(c, q.ym.v[e]));
+                              const KT sz = __fsub_rn(__fsub_rn(q.zp.v[e], c), __fsub_rn(c, q.zm.v[e]));
+                              const KT lap = (sx + sy) + sz;
                               // r = dt (f - L u): dt b.grad(u) = a . (2h grad u), dt eps lap / h^2 = c1 lap
                               const KT rk = dtf * fv.v[e] - (ax * dx + ay * dy + az * dz) + c1 * lap;
                               rv.v[e] = rk;
-                              const KT bi = c.x + dtf * fv.v[e];
+                              const KT bi = c + dtf * fv.v[e];
                               acc.f[0] += rk * rk;
                               acc.f[1] += bi * bi;
                           }
                           vstore(r + i, rv);
                           vstore(rh + i, rv);
-                          if (Wf) vstore(Wf + i, q.c);
+                          if (Wf) {
+                              Vec<float2, W> u2;
+#pragma unroll
+                              for (int e = 0; e < W; ++e) u2.v[e] = make_float2(q.c.v[e], clo.v[e]);
+                              vstore(Wf + i, u2);
+                          }
                           if (snap_j) {
                               VD sd;
 #pragma unroll
-                              for (int e = 0; e < W; ++e) sd.v[e] = df_value(q.c.v[e]);
+                              for (int e = 0; e < W; ++e) sd.v[e] = df_value_bits(q.c.v[e], clo.v[e]);
                               vstore(snap_j + i, sd);
                           }
                           acc.tick();
