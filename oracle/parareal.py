@@ -16,7 +16,12 @@ Iteration k >= 1:
         V = [R^k_n, d^k_n] (augmentation with U^k_n, eqs. (eqaug)/(eq12))
         U^k_{n+1} = G_V(U^k_n) + F_n - G_V(P_V U^{k-1}_n)         eq. (formula4)
 Stop when max_n ||U^k_n - U^{k-1}_n|| / ||U^k_n|| <= tol, or k = N, or k = k_max
-(reading R12).  The error of eq. (error) is measured against the sequential fine
+(reading R12).
+
+The comparator "Parareal-I" of Sec. 4 (method = "parareal_I") is plain parareal with
+the POD space of iteration 0 as the coarse space for every subinterval and iteration:
+no level-1 or level-2 POD and no augmentation, U^k_{n+1} = G_{V0}(U^k_n) + F_n -
+G_{V0}(U^{k-1}_n); the paper gives it a longer Case-I window (T0 = 10).  The error of eq. (error) is measured against the sequential fine
 solution U_n = F(0, t_n, u0).
 
 Parameter readings (R3, R4, R15, R16): S = fine steps per subinterval is DeltaT/dt
@@ -67,10 +72,12 @@ class Params:
     tau: float = 1e-13
     lin_tol: float = 1e-14
     aug_tol: float = 1e-12
+    method: str = "adaptive"      # or "parareal_I" (the comparator of Sec. 4)
 
 
 def derive_params(w, T0: Optional[float] = None, dT: Optional[float] = None,
-                  lin_tol: float = 1e-14, pod_tol3: Optional[float] = None) -> Params:
+                  lin_tol: float = 1e-14, pod_tol3: Optional[float] = None,
+                  method: str = "adaptive") -> Params:
     N = w.n_sub
     DeltaT = w.T / N
     S = steps_for(DeltaT, w.dt)
@@ -90,8 +97,10 @@ def derive_params(w, T0: Optional[float] = None, dT: Optional[float] = None,
         n_s0 = min(n_s0, w.n_snap)
     g12 = 1.0 - w.pod_tol
     g3 = 1.0 - (w.pod_tol * 4e-3 if pod_tol3 is None else pod_tol3)
+    if method not in ("adaptive", "parareal_I"):
+        raise ValueError(f"unknown method {method!r}")
     return Params(N, DeltaT, S, dt, T0, S0, DeltaT / Lc, Lc, dM, n_s, n_s0, g12, g12, g3,
-                  w.m_cap, w.m_l, w.p, lin_tol=lin_tol)
+                  w.m_cap, w.m_l, w.p, lin_tol=lin_tol, method=method)
 
 
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
@@ -147,10 +156,15 @@ def parareal(w, prm: Params, k_max: int = 0, tol: float = 0.0, reference=None,
         return store[max(cands)] if cands else None
 
     k_done = 0
+    plain = prm.method == "parareal_I"
     for k in range(1, k_max + 1):
         F: Dict[int, np.ndarray] = {}
         m1 = {}
         for n in range(k - 1, N):
+            if plain:
+                F[n], _ = fine_propagate(op, U_prev[n], prm.T0 + n * prm.DeltaT, prm.S, prm.dt,
+                                         tol=prm.lin_tol)
+                continue
             Fn, Wn = fine_propagate(op, U_prev[n], prm.T0 + n * prm.DeltaT, prm.S, prm.dt,
                                     prm.dM, prm.n_s, tol=prm.lin_tol)
             F[n] = Fn
@@ -164,6 +178,12 @@ def parareal(w, prm: Params, k_max: int = 0, tol: float = 0.0, reference=None,
         m2 = {}
         augs = {}
         for n in range(k, N):
+            if plain:
+                t_n = prm.T0 + n * prm.DeltaT
+                g_new, _ = coarse_propagate(op, V0, U[n], t_n, prm.Lc, prm.dT)
+                g_old, _ = coarse_propagate(op, V0, U_prev[n], t_n, prm.Lc, prm.dT)
+                U[n + 1] = (g_new + F[n].reshape(-1) - g_old).reshape(shape)
+                continue
             blocks = level2_blocks(level1, k, n, prm.m_l, prm.p, V0)
             R2, m, _ = pod_mode(np.concatenate(blocks, axis=1), prm.gamma3, prm.m_cap,
                                 prm.tau)

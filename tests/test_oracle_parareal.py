@@ -142,3 +142,41 @@ def test_exact_coarse_space_converges_in_one_iteration(monkeypatch):
     hist = O.parareal(w, prm, k_max=1, reference=ref)
     assert max(hist["err"][0]) > 1e-3
     assert max(hist["err"][1]) < 1e-12
+
+
+def test_parareal_I_reaches_the_sequential_solution_at_k_equals_N():
+    # plain parareal with the fixed coarse space V0 (Sec. 4, "Parareal-I"): after k = N
+    # iterations every U^N_n is the sequential fine solution, whatever G is
+    w = pi.tiny(n=6, n_sub=4, T=0.04, dt=2e-3, f_seed=3)
+    prm = derive_params(w, method="parareal_I")
+    ref = O.sequential_fine(w, prm)
+    hist = O.parareal(w, prm, reference=ref)
+    assert hist["k"] == w.n_sub
+    assert max(hist["err"][0]) > 1e-4
+    assert max(hist["err"][-1]) < 1e-13
+
+
+def test_parareal_I_with_an_exact_coarse_propagator_converges_in_one_iteration(monkeypatch):
+    # V0 = I and dT = dt make G = F: U^1 is exact after one iteration.  A poor V0 would
+    # not; the coarse space of every later iteration must be V0 itself.
+    import sys
+    P = sys.modules["oracle.parareal"]
+    w = pi.tiny(n=5, n_sub=4, T=0.04, dt=2e-3, f_seed=3)
+    prm = derive_params(w, dT=2e-3, method="parareal_I")
+    Ng = w.Ng
+    monkeypatch.setattr(P, "pod_mode", lambda W, gamma, cap=0, tau=1e-13, reorth=True:
+                        (np.eye(Ng), Ng, None))
+    ref = O.sequential_fine(w, prm)
+    hist = O.parareal(w, prm, k_max=1, reference=ref)
+    assert max(hist["err"][1]) < 1e-12
+
+
+def test_parareal_I_differs_from_the_adaptive_method_and_keeps_v0():
+    # the comparator must not build level-1/2 bases (its iterates use V0 only): with a
+    # poor V0 its first iterate is worse than the adaptive one on the same inputs
+    w = pi.tiny(n=6, n_sub=4, T=0.04, dt=2e-3, f_seed=3, m_cap=2)
+    ref = O.sequential_fine(w, derive_params(w))
+    ha = O.parareal(w, derive_params(w), k_max=1, reference=ref)
+    hp = O.parareal(w, derive_params(w, method="parareal_I"), k_max=1, reference=ref)
+    assert hp["m1"][0] == {} and hp["m2"][0] == {}
+    assert max(hp["err"][1]) > 2 * max(ha["err"][1])
