@@ -90,7 +90,14 @@ typedef struct pr_opts {
     int ctas_per_sm;        /* resident CTAs per SM for the fine sweep; 0: occupancy max  */
     long long spin_limit;   /* polls of an in-kernel barrier before PR_ERR_TIMEOUT
                                (default 1<<22, about a second)                            */
+    int method;             /* enum pr_method; default PR_METHOD_ADAPTIVE                 */
 } pr_opts;
+
+/* PR_METHOD_ADAPTIVE: Algorithm 2.  PR_METHOD_PARAREAL_I: the comparator "Parareal-I" of
+ * Sec. 4, plain parareal whose coarse space is the iteration-0 POD space V0 for every
+ * subinterval and iteration (no level-1/2 POD, no augmentation; pr_pod_update does
+ * nothing, snapshots are not taken); the paper gives it a longer window T0 = 10. */
+enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1 };
 
 /* Per-solve report (pr_solve).  Times are seconds measured with CUDA events. */
 typedef struct pr_report {

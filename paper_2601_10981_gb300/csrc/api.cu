@@ -506,6 +506,7 @@ void pr_opts_init(pr_opts* o) {
     o->lin_maxit = 200;
     o->aug_tol = 1e-12;
     o->spin_limit = 1LL << 22;
+    o->method = PR_METHOD_ADAPTIVE;
 }
 
 const char* pr_status_string(pr_status s) {
@@ -541,6 +542,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (opts) o = *opts; else pr_opts_init(&o);
     if (o.m_l < 0 || o.m_l > 1 || o.p < 0 || o.p > 1) return PR_ERR_UNSUPPORTED;
     if (o.precision != PR_FP64 && o.precision != PR_FP32) return PR_ERR_INVALID_ARG;
+    if (o.method != PR_METHOD_ADAPTIVE && o.method != PR_METHOD_PARAREAL_I) return PR_ERR_INVALID_ARG;
     if (o.lin_maxit <= 0) o.lin_maxit = 200;
     if (o.spin_limit < 0) o.spin_limit = 1LL << 22;
     if (o.aug_tol <= 0) o.aug_tol = 1e-12;
@@ -591,7 +593,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     c->maxK = std::max(c->nsmax, c->w2);
     c->ldcols = c->maxK + 2;
     c->has_f = false;
-    if (c->mcap2 > 32 || c->mcap0 > 33) {
+    if (c->mcap2 > 32 || c->mcap0 > 33 || (o.method == PR_METHOD_PARAREAL_I && c->mcap0 > coarse_max_m())) {
         delete c;
         return PR_ERR_UNSUPPORTED;  // reduced systems are solved in one CTA (<= 33 unknowns)
     }
@@ -757,8 +759,10 @@ pr_status pr_fine_sweep(pr_ctx* c, int k) {
     const long long Ng = c->Ng;
     const int B = c->N - k + 1;
     const double* Uprev = c->Ubuf[c->cur];
+    const bool plain = c->o.method == PR_METHOD_PARAREAL_I;   // no snapshots needed
     pr_status s = run_fine(c, Uprev + (size_t)(k - 1) * Ng, c->Fend + (size_t)(k - 1) * Ng,
-                           c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S, c->ns, k - 1, false);
+                           plain ? nullptr : c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S,
+                           c->ns, k - 1, false);
     if (s != PR_OK) return s;
     c->phase = 1;
     return PR_OK;
@@ -795,12 +799,13 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         J.dt = c->dt;
         J.S = c->S;
         J.dM = c->dM;
-        J.n_snap = c->ns;
+        const bool plain = c->o.method == PR_METHOD_PARAREAL_I;
+        J.n_snap = plain ? 0 : c->ns;
         J.f = c->has_f ? c->f : nullptr;
         J.f32 = c->has_f ? c->f32 : nullptr;
         J.u_in = c->Ubuf[c->cur] + (size_t)(k - 1) * Ng;
         J.u_out = c->Fend + (size_t)(k - 1) * Ng;
-        J.snap = c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz;
+        J.snap = plain ? nullptr : c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz;
         J.tol = c->lin_tol;
         J.maxit = c->o.lin_maxit;
         J.status = c->fstatus + (k - 1);
@@ -882,6 +887,10 @@ pr_status pr_tune_fine(pr_ctx* c, int steps, int* best_group_ctas, double* best_
 pr_status pr_pod_update(pr_ctx* c, int k) {
     if (!c) return PR_ERR_INVALID_ARG;
     if (c->k_done != k - 1 || c->phase != 1) return fail(c, PR_ERR_STATE, "pr_pod_update out of order");
+    if (c->o.method == PR_METHOD_PARAREAL_I) {   // the coarse space stays V0
+        c->phase = 2;
+        return PR_OK;
+    }
     const long long Ng = c->Ng;
     const int N = c->N;
     pr_status s;
@@ -951,6 +960,7 @@ static CoarseSweepArgs coarse_args(pr_ctx* c) {
     a.dT = c->dT;
     a.Lc = c->Lc;
     a.aug_tol = c->o.aug_tol;
+    a.augment = 1;
     a.d = c->cd;
     a.Ld = c->cLd;
     a.Ltd = c->cLtd;
@@ -988,6 +998,18 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
     a.Mr = c->Mr;
     a.Lr = c->Lr;
     a.sM = (long long)c->mcap2 * c->mcap2;
+    if (c->o.method == PR_METHOD_PARAREAL_I) {   // G in the fixed space V0
+        a.R = reinterpret_cast<const double*>(c->V0);
+        a.sR = 0;
+        a.m = c->m0;
+        a.sm = 0;
+        a.Mr = c->M0;
+        a.Lr = c->L0;
+        a.sM = 0;
+        a.ldM = c->mcap0;
+        a.maxm = c->mcap0;
+        a.augment = 0;
+    }
     PR_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), c->st));
     PR_CUDA(launch_coarse_sweep(a, c->st));
     c->cur = 1 - c->cur;
@@ -1218,7 +1240,7 @@ pr_status pr_rewind(pr_ctx* c) {
     if (c->k_done < 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "no completed iteration to undo");
     PR_CUDA(cudaStreamSynchronize(c->st));
     c->cur = 1 - c->cur;
-    c->r1cur = 1 - c->r1cur;
+    if (c->o.method != PR_METHOD_PARAREAL_I) c->r1cur = 1 - c->r1cur;
     c->k_done -= 1;
     c->phase = 0;
     return PR_OK;

@@ -363,6 +363,23 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             });
             buf ^= 1;
         }
+        if (!a.augment) {
+            // plain coarse space: no augmentation direction
+            if (threadIdx.x == 0) {
+                sh.DD = 0.0;
+                sh.DU = 0.0;
+                sh.DUp = 0.0;
+                sh.DLD = 0.0;
+            }
+            __syncthreads();
+            csw_small(sh, a, m, Mr, Lr);
+            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+                double s = F[p];
+                for (int i = 0; i < m; ++i) s += R[(size_t)i * Ng + p] * sh.g[i];
+                out[p] = s;
+            }
+            continue;
+        }
         // ---- B: d1 = U - R (R^T U) ; R^T d1
         {
             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
         return;
     }
     const int Kp = K + (K & 1);
-    const int ld = Kp;
+    const int ld = Kp + 1;   // odd stride in doubles: row and column sweeps hit distinct banks
     double* A = reinterpret_cast<double*>(smem_raw);
     double* V = A + (size_t)Kp * ld;
     double* cs = V + (size_t)Kp * ld;           // [Kp/2][2]
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
 cudaError_t launch_eig_pod(const EigArgs& a, cudaStream_t st) {
     if (a.B <= 0) return cudaSuccess;
     const int Kp = a.maxK + (a.maxK & 1);
-    const size_t smem = (size_t)2 * Kp * Kp * sizeof(double) + (size_t)2 * Kp * sizeof(double) +
+    const size_t smem = (size_t)2 * Kp * (Kp + 1) * sizeof(double) + (size_t)2 * Kp * sizeof(double) +
                         (size_t)Kp * sizeof(int) + 16;
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {

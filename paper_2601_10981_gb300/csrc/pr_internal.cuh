@@ -287,6 +287,7 @@ struct CoarseSweepArgs {
     double dT;
     int Lc;
     double aug_tol;
+    int augment;            // 0: plain coarse space R (no d~ stages, no augmentation)
     double* d;              // scratch [Ng] each
     double* Ld;
     double* Ltd;
