@@ -41,7 +41,12 @@ typedef enum pr_status {
 enum pr_flow_kind {
     PR_FLOW_ABC = 0,        /* (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x) */
     PR_FLOW_KOLMOGOROV = 1, /* (sin(k y), 0, 0)                                          */
-    PR_FLOW_CONST = 2       /* (b[0], b[1], b[2])                                        */
+    PR_FLOW_CONST = 2,      /* (b[0], b[1], b[2])                                        */
+    /* the time-dependent flows of Sec. 4, with their forcing added to the given f:       */
+    PR_FLOW_PAPER_KOLMOGOROV = 3, /* eq. (koleq): (cos y, cos z, cos x) +
+                                     (sin z, sin x, sin y) cos t, f += -cos y - sin z cos t */
+    PR_FLOW_PAPER_ABC = 4   /* Sec. 4.2: ABC (A = B = C = 1) with every argument shifted
+                               by sin(w t), f += -sin(z + sin wt) - cos(y + sin wt)      */
 };
 
 /* Arithmetic of the fine Krylov solves.  Interface states U^k_n, fine states and end
@@ -64,6 +69,7 @@ typedef struct pr_flow {
     double A, B, C;         /* ABC coefficients                                         */
     int k;                  /* Kolmogorov wave number                                   */
     double b[3];            /* constant velocity                                        */
+    double w;               /* time frequency of PR_FLOW_PAPER_ABC                       */
 } pr_flow;
 
 /* Options; pr_opts_init fills the defaults.  Values marked "0: derive" are computed from

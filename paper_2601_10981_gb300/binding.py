@@ -20,6 +20,7 @@ STATUS = {0: "PR_OK", 1: "PR_ERR_INVALID_ARG", 2: "PR_ERR_OOM", 3: "PR_ERR_CUDA"
           4: "PR_ERR_NOT_CONVERGED", 5: "PR_ERR_BREAKDOWN", 6: "PR_ERR_TIMEOUT",
           7: "PR_ERR_NONFINITE", 8: "PR_ERR_STATE", 9: "PR_ERR_UNSUPPORTED"}
 PR_FLOW_ABC, PR_FLOW_KOLMOGOROV, PR_FLOW_CONST = 0, 1, 2
+PR_FLOW_PAPER_KOLMOGOROV, PR_FLOW_PAPER_ABC = 3, 4
 PR_FP64, PR_FP32 = 0, 1
 PR_METHOD_ADAPTIVE, PR_METHOD_PARAREAL_I = 0, 1
 
@@ -30,7 +31,7 @@ class pr_grid(C.Structure):
 
 class pr_flow(C.Structure):
     _fields_ = [("kind", C.c_int), ("A", C.c_double), ("B", C.c_double), ("C", C.c_double),
-                ("k", C.c_int), ("b", C.c_double * 3)]
+                ("k", C.c_int), ("b", C.c_double * 3), ("w", C.c_double)]
 
 
 class pr_opts(C.Structure):
@@ -165,11 +166,13 @@ def opts(**kw) -> pr_opts:
     return o
 
 
-def flow_struct(kind: str, A=1.0, B=1.0, Cc=1.0, k=1, b=(0.0, 0.0, 0.0)) -> pr_flow:
+def flow_struct(kind: str, A=1.0, B=1.0, Cc=1.0, k=1, b=(0.0, 0.0, 0.0), w=1.0) -> pr_flow:
     f = pr_flow()
-    f.kind = {"abc": PR_FLOW_ABC, "kolmogorov": PR_FLOW_KOLMOGOROV, "const": PR_FLOW_CONST}[kind]
+    f.kind = {"abc": PR_FLOW_ABC, "kolmogorov": PR_FLOW_KOLMOGOROV, "const": PR_FLOW_CONST,
+              "paper_kolmogorov": PR_FLOW_PAPER_KOLMOGOROV, "paper_abc": PR_FLOW_PAPER_ABC}[kind]
     f.A, f.B, f.C, f.k = A, B, Cc, k
     f.b[0], f.b[1], f.b[2] = b
+    f.w = w
     return f
 
 
@@ -212,7 +215,7 @@ class Parareal:
     @classmethod
     def from_workload(cls, w, precision: int = PR_FP64, **opt_kw):
         fl = w.flow
-        flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2))
+        flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2), fl.w)
         o = opts(n_snap=w.n_snap, m_cap=w.m_cap, m_l=w.m_l, p=w.p, precision=precision, **opt_kw)
         obj = cls(w.n, flow, w.eps, w.T, w.n_sub, w.dt, w.pod_tol, o)
         return obj
@@ -351,14 +354,14 @@ class Parareal:
         self._check(self._lib.pr_op_apply_L(self.ctx, _tptr(u), _tptr(out), count, int(transpose)))
         return out
 
-    def op_fine(self, u, steps: int, dM: int = 1, n_snap: int = 0):
+    def op_fine(self, u, steps: int, dM: int = 1, n_snap: int = 0, t0: float = 0.0):
         B = u.shape[0]
         out = self.torch.empty_like(u)
         snap = None
         if n_snap > 0:
             snap = self.torch.zeros((B, n_snap) + tuple(u.shape[1:]), dtype=self.torch.float64,
                                     device=u.device)
-        self._check(self._lib.pr_op_fine(self.ctx, _tptr(u), _tptr(out), _tptr(snap), B, 0.0,
+        self._check(self._lib.pr_op_fine(self.ctx, _tptr(u), _tptr(out), _tptr(snap), B, t0,
                                          steps, dM, n_snap))
         return out, snap
 
@@ -420,7 +423,7 @@ class Server:
         fl = w.flow
         r = pr_request()
         r.grid = pr_grid(w.n, 0.0)
-        r.flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2))
+        r.flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2), fl.w)
         r.eps, r.T, r.n_sub, r.dt_fine, r.pod_tol = w.eps, w.T, w.n_sub, w.dt, w.pod_tol
         r.opts = opts(n_snap=w.n_snap, m_cap=w.m_cap, m_l=w.m_l, p=w.p, precision=precision, **opt_kw)
         u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)

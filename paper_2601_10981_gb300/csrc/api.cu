@@ -61,6 +61,7 @@ struct pr_ctx {
     int groups_max = 1;
     int max_ctas = 1;
     bool has_f = false;
+    bool tdep = false;   // time-dependent flow of Sec. 4 (tables and Galerkin pieces per time)
     // device
     cudaStream_t st = nullptr;
     bool own_ws = false;
@@ -91,6 +92,9 @@ struct pr_ctx {
     double* L0 = nullptr;
     double* p0 = nullptr;
     double* q0 = nullptr;
+    double* qg = nullptr;         // V0^T g^0, V0^T g^1 (time-dependent flows)
+    double* gq = nullptr;         // g^0, g^1 as grid functions (time-dependent flows)
+    double* cA1 = nullptr;        // coarse-sweep scratch A1 d~
     double* beta = nullptr;
     double* gout = nullptr;
     double* lam = nullptr;
@@ -158,7 +162,7 @@ size_t plan(pr_ctx* c, char* base) {
     b.base = base;
     const long long Ng = c->Ng;
     const int N = c->N;
-    c->tab = b.take<double>(6 * (size_t)c->n);
+    c->tab = b.take<double>((size_t)TAB_TOTAL * c->n);
     c->u0 = b.take<double>(Ng);
     c->f = b.take<double>(Ng);
     c->f32 = b.take<float>(Ng);
@@ -178,11 +182,15 @@ size_t plan(pr_ctx* c, char* base) {
     c->LR = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
     c->scr[0] = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
     c->Mr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
-    c->Lr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
+    // Galerkin blocks of L: R^T L R (steady flows) or the pieces R^T D R, R^T A0 R, R^T A1 R
+    c->Lr = b.take<double>((size_t)(N + 1) * 3 * c->mcap2 * c->mcap2);
     c->M0 = b.take<double>((size_t)c->mcap0 * c->mcap0);
-    c->L0 = b.take<double>((size_t)c->mcap0 * c->mcap0);
+    c->L0 = b.take<double>((size_t)3 * c->mcap0 * c->mcap0);
     c->p0 = b.take<double>(c->mcap0);
     c->q0 = b.take<double>(c->mcap0);
+    c->qg = b.take<double>((size_t)2 * c->mcap0);
+    c->gq = c->tdep ? b.take<double>((size_t)2 * Ng) : nullptr;
+    c->cA1 = b.take<double>(Ng);
     c->beta = b.take<double>((size_t)N * c->mcap0);
     c->gout = b.take<double>((size_t)N * c->maxK * c->maxK);
     c->lam = b.take<double>((size_t)N * c->maxK);
@@ -247,7 +255,8 @@ pr_status init_ws(pr_ctx* c) {
     PR_CUDA(cudaMemcpy(c->ones, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice));
     int cn[8] = {c->ns, c->ns0, 0, 1, 0, 0, 0, 0};
     PR_CUDA(cudaMemcpy(c->cnst, cn, sizeof(cn), cudaMemcpyHostToDevice));
-    PR_CUDA(launch_tables(c->flow, c->n, c->L, c->tab, st));
+    PR_CUDA(launch_flow_tables(c->flow, c->n, c->L, c->tab, st));
+    if (c->tdep) PR_CUDA(launch_g_fields(c->tab, c->n, c->gq, c->gq + c->Ng, st));
     if (!c->ev_ready) {
         for (auto& e : c->ev) PR_CUDA(cudaEventCreate(&e));
         c->ev_ready = true;
@@ -389,6 +398,9 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
 
 // Galerkin blocks of B bases (dest columns, counts m[b]): M = R^T R, L = R^T L_h R
 // into Mo/Lo + b*mmax*mmax (ld mmax).
+// Galerkin blocks of B bases R (eqs. (eq8)/(eq00)): Mo = R^T R and, with item stride
+// 3 mmax^2 in Lo, R^T L R (steady flows) or the pieces R^T D R, R^T A0 R, R^T A1 R
+// (time-dependent flows, L(t) = D + c0(t) A0 + c1(t) A1, D = -eps Lap_h).
 pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B, int mmax, double* Mo,
                    double* Lo) {
     const bool f32 = false;
@@ -396,9 +408,6 @@ pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B
     if (s != PR_OK) return s;
     s = cols_contig(c, c->LR, (size_t)mmax * c->Ng * c->esz, m, 1, B, c->colsB, c->KB, c->esz);
     if (s != PR_OK) return s;
-    Grid g = grid_of(c);
-    PR_CUDA(launch_apply_L(g, c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, f32, f32,
-                           false, c->st));
     GramArgs ga{};
     ga.colsA = c->colsA;
     ga.colsB = c->colsA;
@@ -416,22 +425,43 @@ pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B
     ga.ldG = mmax;
     ga.ldG_b = (long long)mmax * mmax;
     PR_CUDA(launch_gram(ga, f32, f32, c->st));
+    const Grid g = grid_of(c);
+    Grid pieces[3] = {g, g, g};
+    int np = 1;
+    if (c->tdep) {
+        pieces[0].tab = c->tab + (size_t)TAB_ZERO * c->n;   // D: no advection
+        pieces[1].eps = 0.0;                                 // A0
+        pieces[2].eps = 0.0;                                 // A1
+        pieces[2].tab = c->tab + (size_t)TAB_B1 * c->n;
+        np = 3;
+    }
     ga.sym = false;
     ga.colsB = c->colsB;
     ga.KB = c->KB;
-    ga.G = Lo;
-    PR_CUDA(launch_gram(ga, f32, f32, c->st));
+    ga.ldG_b = (long long)3 * mmax * mmax;
+    for (int q = 0; q < np; ++q) {
+        PR_CUDA(launch_apply_L(pieces[q], c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, f32, f32,
+                               false, c->st));
+        ga.G = Lo + (size_t)q * mmax * mmax;
+        PR_CUDA(launch_gram(ga, f32, f32, c->st));
+    }
     return PR_OK;
 }
 
+// Fine propagation of B subintervals; item b starts at t0 + b * DeltaT.
 pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int B, int steps,
-                   int n_snap, int stat_off, bool force_fp64) {
+                   int n_snap, int stat_off, bool force_fp64, double t0, double DeltaT) {
     const bool f32 = c->fp32 && !force_fp64;
     FineArgs a{};
     a.g = grid_of(c);
     a.njobs = 1;
     FineJob& J = a.jobs[0];
     J.tab = c->tab;
+    J.tdep = c->tdep ? 1 : 0;
+    J.kind = c->flow.kind;
+    J.w = c->flow.w;
+    J.t0 = t0;
+    J.DeltaT = DeltaT;
     J.eps = c->eps;
     J.dt = c->dt;
     J.S = steps;
@@ -537,7 +567,8 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (grid->n < 4 || grid->n > 256) return PR_ERR_UNSUPPORTED;
     if (!(eps > 0) || !(T > 0) || n_sub < 1 || !(dt_fine > 0) || !(pod_tol >= 0 && pod_tol < 1))
         return PR_ERR_INVALID_ARG;
-    if (flow->kind < PR_FLOW_ABC || flow->kind > PR_FLOW_CONST) return PR_ERR_INVALID_ARG;
+    if (flow->kind < PR_FLOW_ABC || flow->kind > PR_FLOW_PAPER_ABC) return PR_ERR_INVALID_ARG;
+    if (flow->kind == PR_FLOW_PAPER_ABC && !std::isfinite(flow->w)) return PR_ERR_INVALID_ARG;
     pr_opts o;
     if (opts) o = *opts; else pr_opts_init(&o);
     if (o.m_l < 0 || o.m_l > 1 || o.p < 0 || o.p > 1) return PR_ERR_UNSUPPORTED;
@@ -552,6 +583,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     c->h = c->L / c->n;
     c->Ng = (long long)c->n * c->n * c->n;
     c->flow = *flow;
+    c->tdep = flow_time_dependent(flow->kind);
     c->eps = eps;
     c->T = T;
     c->N = n_sub;
@@ -687,7 +719,7 @@ pr_status pr_iteration0(pr_ctx* c) {
     double* U = c->Ubuf[0];
     c->cur = 0;
     // fine propagator on [0, T0] with snapshots (slot 0 of the snapshot store)
-    s = run_fine(c, c->u0, U, c->snap, 1, c->S0, c->ns0, 0, false);
+    s = run_fine(c, c->u0, U, c->snap, 1, c->S0, c->ns0, 0, false, 0.0, 0.0);
     if (s != PR_OK) return s;
     // V0 = POD_Mode(W, gamma1)
     s = cols_contig(c, c->snap, 0, c->cnst + 1, 0, 1, c->colsA, c->KA, sizeof(double));
@@ -724,9 +756,26 @@ pr_status pr_iteration0(pr_ctx* c) {
             ga.G = c->q0;
             PR_CUDA(launch_gram(ga, false, false, c->st));
         }
+        if (c->tdep) {
+            // qg = V0^T g^0, V0^T g^1: the time-dependent forcing pieces
+            std::vector<const void*> gs = {c->gq, c->gq + Ng};
+            PR_CUDA(cudaMemcpyAsync(c->colsB + 2, gs.data(), sizeof(void*) * 2, cudaMemcpyHostToDevice, c->st));
+            PR_CUDA(cudaStreamSynchronize(c->st));
+            for (int q = 0; q < 2; ++q) {
+                ga.colsB = c->colsB + 2 + q;
+                ga.G = c->qg + (size_t)q * c->mcap0;
+                PR_CUDA(launch_gram(ga, false, false, c->st));
+            }
+        }
     }
+    G0Tdep td{};
+    td.tdep = c->tdep ? 1 : 0;
+    td.kind = c->flow.kind;
+    td.w = c->flow.w;
+    td.T0 = c->T0;
+    td.qg = c->qg;
     PR_CUDA(launch_g0(c->M0, c->L0, c->p0, c->has_f ? c->q0 : nullptr, c->m0, c->mcap0, c->N, c->Lc, c->dT,
-                      c->beta, c->mcap0, c->derr, c->st));
+                      c->beta, c->mcap0, c->derr, td, c->st));
     // U^0_{n+1} = V0 beta_n
     s = cols_contig(c, c->V0, 0, c->m0, 0, c->N, c->colsA, c->KA, c->esz);
     if (s != PR_OK) return s;
@@ -762,7 +811,7 @@ pr_status pr_fine_sweep(pr_ctx* c, int k) {
     const bool plain = c->o.method == PR_METHOD_PARAREAL_I;   // no snapshots needed
     pr_status s = run_fine(c, Uprev + (size_t)(k - 1) * Ng, c->Fend + (size_t)(k - 1) * Ng,
                            plain ? nullptr : c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S,
-                           c->ns, k - 1, false);
+                           c->ns, k - 1, false, c->T0 + (k - 1) * c->DeltaT, c->DeltaT);
     if (s != PR_OK) return s;
     c->phase = 1;
     return PR_OK;
@@ -795,6 +844,11 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         const long long Ng = c->Ng;
         FineJob& J = a.jobs[i];
         J.tab = c->tab;
+        J.tdep = c->tdep ? 1 : 0;
+        J.kind = c->flow.kind;
+        J.w = c->flow.w;
+        J.t0 = c->T0 + (k - 1) * c->DeltaT;
+        J.DeltaT = c->DeltaT;
         J.eps = c->eps;
         J.dt = c->dt;
         J.S = c->S;
@@ -860,7 +914,7 @@ pr_status pr_tune_fine(pr_ctx* c, int steps, int* best_group_ctas, double* best_
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
             PR_CUDA(cudaEventRecord(c->ev[0], c->st));
-            pr_status s = run_fine(c, u_in, c->Fend, nullptr, B, steps, 0, 0, false);
+            pr_status s = run_fine(c, u_in, c->Fend, nullptr, B, steps, 0, 0, false, c->T0, c->DeltaT);
             if (s != PR_OK) return s;
             PR_CUDA(cudaEventRecord(c->ev[1], c->st));
         }
@@ -944,7 +998,7 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
                          c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k);
         if (s != PR_OK) return s;
         s = galerkin(c, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k, B2,
-                     c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * c->mcap2 * c->mcap2);
+                     c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * 3 * c->mcap2 * c->mcap2);
         if (s != PR_OK) return s;
     }
     c->r1cur = nw;
@@ -955,6 +1009,12 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
 static CoarseSweepArgs coarse_args(pr_ctx* c) {
     CoarseSweepArgs a{};
     a.g = grid_of(c);
+    a.tdep = c->tdep ? 1 : 0;
+    a.kind = c->flow.kind;
+    a.w = c->flow.w;
+    a.t0 = c->T0;
+    a.DeltaT = c->DeltaT;
+    a.A1d = c->cA1;
     a.ldM = c->mcap2;
     a.maxm = c->mcap2;
     a.dT = c->dT;
@@ -998,6 +1058,7 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
     a.Mr = c->Mr;
     a.Lr = c->Lr;
     a.sM = (long long)c->mcap2 * c->mcap2;
+    a.sML = (long long)3 * c->mcap2 * c->mcap2;
     if (c->o.method == PR_METHOD_PARAREAL_I) {   // G in the fixed space V0
         a.R = reinterpret_cast<const double*>(c->V0);
         a.sR = 0;
@@ -1006,6 +1067,7 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
         a.Mr = c->M0;
         a.Lr = c->L0;
         a.sM = 0;
+        a.sML = 0;
         a.ldM = c->mcap0;
         a.maxm = c->mcap0;
         a.augment = 0;
@@ -1093,11 +1155,11 @@ pr_status pr_compute_reference(pr_ctx* c, int fp64) {
     if (s != PR_OK) return s;
     const long long Ng = c->Ng;
     const bool force = fp64 != 0;
-    s = run_fine(c, c->u0, c->ref, nullptr, 1, c->S0, 0, c->N, force);
+    s = run_fine(c, c->u0, c->ref, nullptr, 1, c->S0, 0, c->N, force, 0.0, 0.0);
     if (s != PR_OK) return s;
     for (int n = 0; n < c->N; ++n) {
         s = run_fine(c, c->ref + (size_t)n * Ng, c->ref + (size_t)(n + 1) * Ng, nullptr, 1, c->S, 0, c->N,
-                     force);
+                     force, c->T0 + n * c->DeltaT, c->DeltaT);
         if (s != PR_OK) return s;
     }
     return pr_sync(c);
@@ -1288,6 +1350,7 @@ pr_status pr_get_basis(pr_ctx* c, int level, int n, void* out, int* m_out) {
 // ---------------------------------------------------------------------------------
 pr_status pr_op_apply_L(pr_ctx* c, const double* d_in, double* d_out, int count, int transpose) {
     if (!c || !d_in || !d_out || count < 0) return PR_ERR_INVALID_ARG;
+    if (c->tdep) return fail(c, PR_ERR_UNSUPPORTED, "pr_op_apply_L: time-dependent flows need a time");
     pr_status s = ensure_ws(c);
     if (s != PR_OK) return s;
     Grid g = grid_of(c);
@@ -1309,14 +1372,13 @@ pr_status pr_op_apply_L(pr_ctx* c, const double* d_in, double* d_out, int count,
 
 pr_status pr_op_fine(pr_ctx* c, const double* d_in, double* d_out, void* d_snap, int B, double t0,
                      int steps, int dM, int n_snap) {
-    (void)t0;  // time-independent flows
     if (!c || !d_in || !d_out || B < 1 || B > c->N || steps < 1) return PR_ERR_INVALID_ARG;
     if (n_snap < 0 || (n_snap > 0 && (!d_snap || dM < 1))) return PR_ERR_INVALID_ARG;
     pr_status s = ensure_ws(c);
     if (s != PR_OK) return s;
     const int saved = c->dM;
     c->dM = dM > 0 ? dM : 1;
-    s = run_fine(c, d_in, d_out, (char*)d_snap, B, steps, n_snap, 0, false);
+    s = run_fine(c, d_in, d_out, (char*)d_snap, B, steps, n_snap, 0, false, t0, 0.0);
     c->dM = saved;
     if (s != PR_OK) return s;
     return pr_sync(c);
@@ -1346,11 +1408,12 @@ pr_status pr_op_coarse_update(pr_ctx* c, const void* d_R, int m, const double* d
                               const double* d_F, double* d_out) {
     if (!c || !d_R || !d_U || !d_Uprev || !d_F || !d_out || m < 0) return PR_ERR_INVALID_ARG;
     if (m > c->mcap2) return fail(c, PR_ERR_INVALID_ARG, "m above the context's level-2 cap");
+    if (c->tdep) return fail(c, PR_ERR_UNSUPPORTED, "pr_op_coarse_update: time-dependent flows need a time");
     pr_status s = ensure_ws(c);
     if (s != PR_OK) return s;
     PR_CUDA(cudaMemcpy(c->m2 + c->N, &m, sizeof(int), cudaMemcpyHostToDevice));
     double* Mr = c->Mr + (size_t)c->N * c->mcap2 * c->mcap2;
-    double* Lr = c->Lr + (size_t)c->N * c->mcap2 * c->mcap2;
+    double* Lr = c->Lr + (size_t)c->N * 3 * c->mcap2 * c->mcap2;
     if (m > 0) {
         s = galerkin(c, (char*)d_R, (size_t)c->mcap2 * c->Ng, c->m2 + c->N, 1, c->mcap2, Mr, Lr);
         if (s != PR_OK) return s;
@@ -1373,6 +1436,7 @@ pr_status pr_op_coarse_update(pr_ctx* c, const void* d_R, int m, const double* d
 
 pr_status pr_op_apply_L_noalloc(pr_ctx* c, const double* d_in, double* d_out, int count, int transpose) {
     if (!c || !d_in || !d_out || count < 0) return fail(c, PR_ERR_INVALID_ARG, "null pointer or negative count");
+    if (c->tdep) return fail(c, PR_ERR_UNSUPPORTED, "pr_op_apply_L_noalloc: time-dependent flows need a time");
     if (c->n > pr::noalloc_max_n())
         return fail(c, PR_ERR_INVALID_ARG, "pr_op_apply_L_noalloc: n above its static scratch (n <= " +
                                                std::to_string(pr::noalloc_max_n()) + ")");

@@ -135,7 +135,7 @@ constexpr int CSW_THREADS = 512;
 constexpr int CSW_WARPS = CSW_THREADS / 32;
 constexpr int CSW_MAXM = 32;                  // level-2 dimension supported
 constexpr int CSW_MAXK = CSW_MAXM + 1;        // with the augmentation direction
-constexpr int CSW_MAXQ = 2 * CSW_MAXM + 3;    // reductions per stage
+constexpr int CSW_MAXQ = 3 * CSW_MAXM + 3;    // reductions per stage
 constexpr int CSW_LDA = 2 * CSW_MAXK + 1;     // [Ac | Mv | b]
 constexpr int CSW_MAX_GRID = 1024;
 
@@ -144,6 +144,10 @@ size_t coarse_part_doubles(long long, int) { return (size_t)2 * CSW_MAXQ * CSW_M
 struct CswShared {
     double RU[CSW_MAXM], RUp[CSW_MAXM], RD1[CSW_MAXM], RD[CSW_MAXM], RL[CSW_MAXM], RLt[CSW_MAXM];
     double UU, DD, DU, DUp, DLD;
+    // time-dependent flows: R^T D d~, R^T A_q d~ and d~.D d~, d~.A_q d~
+    double RPD[CSW_MAXM], RPA0[CSW_MAXM], RPA1[CSW_MAXM];
+    double PDD, PDA0, PDA1;
+    double c0, c1;
     double red[CSW_WARPS * 3];
     double g[CSW_MAXK];
     double A[CSW_MAXK * CSW_LDA];
@@ -322,6 +326,120 @@ __device__ void csw_small(CswShared& sh, const CoarseSweepArgs& a, int m, const 
     __syncthreads();
 }
 
+// Gauss-Jordan with partial pivoting on the K x nc matrix sh.A (columns K.. are
+// right-hand sides); afterwards those columns hold Ac^{-1} times them.
+__device__ void csw_gauss_jordan(CswShared& sh, int K, int nc) {
+    for (int j = 0; j < K; ++j) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double best = -1.0;
+            int bi = j;
+            for (int i = j + lane; i < K; i += 32) {
+                const double v = fabs(sh.A[i * CSW_LDA + j]);
+                if (v > best) { best = v; bi = i; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                sh.piv = bi;
+                const double pv = sh.A[bi * CSW_LDA + j];
+                sh.inv_piv = (pv != 0.0) ? 1.0 / pv : 0.0;
+            }
+        }
+        __syncthreads();
+        const int pr = sh.piv;
+        if (pr != j) {
+            for (int c = j + threadIdx.x; c < nc; c += blockDim.x) {
+                const double t = sh.A[j * CSW_LDA + c];
+                sh.A[j * CSW_LDA + c] = sh.A[pr * CSW_LDA + c];
+                sh.A[pr * CSW_LDA + c] = t;
+            }
+        }
+        __syncthreads();
+        for (int c = j + 1 + threadIdx.x; c < nc; c += blockDim.x) sh.prow[c] = sh.A[j * CSW_LDA + c] * sh.inv_piv;
+        for (int i = threadIdx.x; i < K; i += blockDim.x) sh.mult[i] = sh.A[i * CSW_LDA + j];
+        __syncthreads();
+        const int w = nc - j - 1;
+        for (int e = threadIdx.x; e < K * w; e += blockDim.x) {
+            const int i = e / w, c = j + 1 + (e - i * w);
+            sh.A[i * CSW_LDA + c] = (i == j) ? sh.prow[c] : sh.A[i * CSW_LDA + c] - sh.mult[i] * sh.prow[c];
+        }
+        __syncthreads();
+    }
+}
+
+// Reduced propagation for a time-dependent flow: the matrices change with the coarse
+// time, so each of the Lc steps solves (Mv + dT Lv(t_l)) x_l = Mv x_{l-1}, started from
+// x_1 = Ac(t_1)^{-1} b, b = V^T (U - U') (the same vector as Phi_1 Mv^{-1} b).
+__device__ void csw_small_tdep(CswShared& sh, const CoarseSweepArgs& a, int m, const double* Mr,
+                               const double* Lr, double t_n) {
+    const double nd = sqrt(fmax(sh.DD, 0.0));
+    const bool aug = a.augment && nd > 0.0 && nd > a.aug_tol * sqrt(fmax(sh.UU, 0.0));
+    const int K = aug ? m + 1 : m;
+    const double dT = a.dT;
+    const long long PL = (long long)a.ldM * a.ldM;
+    // Mv in the x slot area: keep it in sh.y? use the RHS column for b, Mv read from Mr
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        sh.x[i] = (i < m) ? sh.RU[i] - sh.RUp[i] : (sh.DU - sh.DUp) / nd;
+    __syncthreads();
+    auto mv = [&](int i, int j) -> double {
+        if (i < m && j < m) return Mr[(size_t)i * a.ldM + j];
+        if (i < m) return sh.RD[i] / nd;
+        if (j < m) return sh.RD[j] / nd;
+        return sh.DD / (nd * nd);
+    };
+    for (int l = 1; l <= a.Lc; ++l) {
+        if (threadIdx.x == 0) {
+            double q0, q1;
+            flow_coeffs(a.kind, a.w, t_n + l * dT, q0, q1);
+            sh.c0 = q0;
+            sh.c1 = q1;
+        }
+        __syncthreads();
+        const double q0 = sh.c0, q1 = sh.c1;
+        for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+            const int i = e / K, j = e - i * K;
+            double lv;
+            if (i < m && j < m) {
+                const size_t o = (size_t)i * a.ldM + j;
+                lv = Lr[o] + q0 * Lr[PL + o] + q1 * Lr[2 * PL + o];
+            } else if (i < m) {     // column m: R^T L d
+                lv = (sh.RPD[i] + q0 * sh.RPA0[i] + q1 * sh.RPA1[i]) / nd;
+            } else if (j < m) {     // row m: (L^T d)^T R, advection pieces antisymmetric
+                lv = (sh.RPD[j] - q0 * sh.RPA0[j] - q1 * sh.RPA1[j]) / nd;
+            } else {
+                lv = (sh.PDD + q0 * sh.PDA0 + q1 * sh.PDA1) / (nd * nd);
+            }
+            sh.A[i * CSW_LDA + j] = mv(i, j) + dT * lv;
+        }
+        // right-hand side: b at the first step, then Mv x
+        for (int i = threadIdx.x; i < K; i += blockDim.x) {
+            double r;
+            if (l == 1) r = sh.x[i];
+            else {
+                r = 0.0;
+                for (int j = 0; j < K; ++j) r += mv(i, j) * sh.x[j];
+            }
+            sh.A[i * CSW_LDA + K] = r;
+        }
+        __syncthreads();
+        csw_gauss_jordan(sh, K, K + 1);
+        for (int i = threadIdx.x; i < K; i += blockDim.x) sh.x[i] = sh.A[i * CSW_LDA + K];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) {
+        double v = 0.0;
+        if (i < m) v = sh.x[i];
+        else if (aug) v = sh.x[m] / nd;
+        sh.g[i] = v;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSweepArgs a) {
     __shared__ CswShared sh;
     const int G = gridDim.x;
@@ -343,7 +461,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
         double* out = a.out + n * a.sOut;
         const double* R = a.R + n * a.sR;
         const double* Mr = a.Mr + n * a.sM;
-        const double* Lr = a.Lr + n * a.sM;
+        const double* Lr = a.Lr + n * a.sML;
+        const double t_n = a.t0 + n * a.DeltaT;
         int m = a.m[n * a.sm];
         if (m > a.maxm || m < 0) {
             if (threadIdx.x == 0) record_error(a.err, DERR_BREAKDOWN);
@@ -372,7 +491,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
                 sh.DLD = 0.0;
             }
             __syncthreads();
-            csw_small(sh, a, m, Mr, Lr);
+            if (a.tdep) csw_small_tdep(sh, a, m, Mr, Lr, t_n);
+            else csw_small(sh, a, m, Mr, Lr);
             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
                 double s = F[p];
                 for (int i = 0; i < m; ++i) s += R[(size_t)i * Ng + p] * sh.g[i];
@@ -417,7 +537,52 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             buf ^= 1;
         }
         // ---- D: L d~, L^T d~ (b_d does not depend on x_d, so L^T flips the advection) ;
-        //         R^T L d~, R^T L^T d~, d~.L d~
+        //         R^T L d~, R^T L^T d~, d~.L d~.  Time-dependent flows: the pieces D d~,
+        //         A0 d~, A1 d~ and their projections instead, combined per coarse step.
+        if (a.tdep) {
+            const double* tab0 = a.g.tab;
+            const double* tab1 = a.g.tab + (size_t)TAB_B1 * n_;
+            const double* d = a.d;
+            double v[3] = {0.0, 0.0, 0.0};
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const int x = (int)(i % n_), y = (int)((i / n_) % n_), z = (int)(i / n2);
+                const long long base = i - x, rowb = i - (long long)y * n_, plb = i - (long long)z * n2;
+                const double uc = d[i];
+                const double uxp = d[base + (x + 1 == n_ ? 0 : x + 1)], uxm = d[base + (x == 0 ? n_ - 1 : x - 1)];
+                const double uyp = d[rowb + (long long)(y + 1 == n_ ? 0 : y + 1) * n_];
+                const double uym = d[rowb + (long long)(y == 0 ? n_ - 1 : y - 1) * n_];
+                const double uzp = d[plb + (long long)(z + 1 == n_ ? 0 : z + 1) * n2];
+                const double uzm = d[plb + (long long)(z == 0 ? n_ - 1 : z - 1) * n2];
+                const double dx = uxp - uxm, dy = uyp - uym, dz = uzp - uzm;
+                const double pd = -epsh2 * ((uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc);
+                const double a0 = ((tab0[TXY * n_ + y] + tab0[TXZ * n_ + z]) * dx +
+                                   (tab0[TYX * n_ + x] + tab0[TYZ * n_ + z]) * dy +
+                                   (tab0[TZX * n_ + x] + tab0[TZY * n_ + y]) * dz) * inv2h;
+                const double a1 = ((tab1[TXY * n_ + y] + tab1[TXZ * n_ + z]) * dx +
+                                   (tab1[TYX * n_ + x] + tab1[TYZ * n_ + z]) * dy +
+                                   (tab1[TZX * n_ + x] + tab1[TZY * n_ + y]) * dz) * inv2h;
+                a.Ld[i] = pd;
+                a.Ltd[i] = a0;
+                a.A1d[i] = a1;
+                v[0] += uc * pd;
+                v[1] += uc * a0;
+                v[2] += uc * a1;
+            }
+            csw_block_sums(v, 3, sh, part() + (size_t)(3 * m) * G, G);
+            __syncthreads();
+            csw_dots(R, Ng, m, a.Ld, 0, a.Ltd, m, lo, hi, part(), G);
+            csw_dots(R, Ng, m, a.A1d, 2 * m, nullptr, 0, lo, hi, part(), G);
+            if (!barrier()) return;
+            csw_reduce(part(), 3 * m + 3, G, [&](int q, double s) {
+                if (q < m) sh.RPD[q] = s;
+                else if (q < 2 * m) sh.RPA0[q - m] = s;
+                else if (q < 3 * m) sh.RPA1[q - 2 * m] = s;
+                else if (q == 3 * m) sh.PDD = s;
+                else if (q == 3 * m + 1) sh.PDA0 = s;
+                else sh.PDA1 = s;
+            });
+            buf ^= 1;
+        } else
         {
             const double* tab = a.g.tab;
             const double* d = a.d;
@@ -453,7 +618,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             buf ^= 1;
         }
         // ---- E: reduced solve ; F: U^k_{n+1} = F_n + R g + d~ g_d
-        csw_small(sh, a, m, Mr, Lr);
+        if (a.tdep) csw_small_tdep(sh, a, m, Mr, Lr, t_n);
+        else csw_small(sh, a, m, Mr, Lr);
         for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
             double s = F[p] + a.d[p] * sh.g[m];
             for (int i = 0; i < m; ++i) s += R[(size_t)i * Ng + p] * sh.g[i];
@@ -491,15 +657,61 @@ cudaError_t launch_coarse_sweep(CoarseSweepArgs a, cudaStream_t st) {
 // stored in beta[n*ldb .. ] (n = 0..N-1 gives U^0_{n+1}).
 __global__ void g0_kernel(const double* M0, const double* L0, const double* p0, const double* q0,
                           const int* m0p, int ld, int N, int Lc, double dT, double* beta, int ldb,
-                          int* err) {
+                          int* err, G0Tdep td) {
     __shared__ double Mv[CS_MAXK * CS_MAXK];
     __shared__ double Ac[CS_MAXK * CS_MAXK];
     __shared__ double T[CS_MAXK * CS_MAXK];
     __shared__ double w[CS_MAXK], x[CS_MAXK], y[CS_MAXK];
     __shared__ int piv[CS_MAXK];
+    __shared__ double s_c[2];
     const int K = *m0p;
     if (K <= 0 || K > CS_MAXK) {
         if (K > CS_MAXK && threadIdx.x == 0) record_error(err, DERR_BREAKDOWN);
+        return;
+    }
+    if (td.tdep) {
+        // L(t) = D + c0(t) A0 + c1(t) A1 and f(t) = f + c0(t) g0 + c1(t) g1: assemble and
+        // factor at every coarse time t = T0 + l dT
+        const size_t PL = (size_t)ld * ld;
+        for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+            const int i = e / K, j = e - i * K;
+            Mv[i * CS_MAXK + j] = M0[(size_t)i * ld + j];
+            T[i * CS_MAXK + j] = M0[(size_t)i * ld + j];   // Mv, kept for the right-hand side
+        }
+        for (int i = threadIdx.x; i < K; i += blockDim.x) x[i] = p0[i];
+        __syncthreads();
+        lu_factor(Mv, K, piv);
+        if (threadIdx.x == 0) lu_solve_col(Mv, K, piv, x, 1);   // beta_0 = M0^{-1} V0^T u_hat0
+        __syncthreads();
+        for (int n = 0; n < N; ++n) {
+            for (int l = 1; l <= Lc; ++l) {
+                if (threadIdx.x == 0) {
+                    double c0, c1;
+                    flow_coeffs(td.kind, td.w, td.T0 + ((double)n * Lc + l) * dT, c0, c1);
+                    s_c[0] = c0;
+                    s_c[1] = c1;
+                }
+                __syncthreads();
+                const double c0 = s_c[0], c1 = s_c[1];
+                for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+                    const int i = e / K, j = e - i * K;
+                    const size_t o = (size_t)i * ld + j;
+                    Ac[i * CS_MAXK + j] = T[i * CS_MAXK + j] + dT * (L0[o] + c0 * L0[PL + o] + c1 * L0[2 * PL + o]);
+                }
+                for (int i = threadIdx.x; i < K; i += blockDim.x) {
+                    double r = dT * ((q0 ? q0[i] : 0.0) + c0 * td.qg[i] + c1 * td.qg[ld + i]);
+                    for (int j = 0; j < K; ++j) r += T[i * CS_MAXK + j] * x[j];
+                    y[i] = r;
+                }
+                __syncthreads();
+                lu_factor(Ac, K, piv);
+                if (threadIdx.x == 0) lu_solve_col(Ac, K, piv, y, 1);
+                __syncthreads();
+                for (int i = threadIdx.x; i < K; i += blockDim.x) x[i] = y[i];
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < K; i += blockDim.x) beta[(size_t)n * ldb + i] = x[i];
+        }
         return;
     }
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
@@ -544,8 +756,8 @@ __global__ void g0_kernel(const double* M0, const double* L0, const double* p0, 
 
 cudaError_t launch_g0(const double* M0, const double* L0, const double* p0, const double* q0,
                       const int* m0, int ld, int N, int Lc, double dT, double* beta, int ldb,
-                      int* err, cudaStream_t st) {
-    g0_kernel<<<1, 128, 0, st>>>(M0, L0, p0, q0, m0, ld, N, Lc, dT, beta, ldb, err);
+                      int* err, const G0Tdep& td, cudaStream_t st) {
+    g0_kernel<<<1, 128, 0, st>>>(M0, L0, p0, q0, m0, ld, N, Lc, dT, beta, ldb, err, td);
     ++g_launch_count;
     return cudaGetLastError();
 }

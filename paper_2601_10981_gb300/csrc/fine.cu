@@ -64,6 +64,85 @@ __global__ void tables_kernel(int kind, double A, double B, double C, int k, dou
     for (int t = 0; t < 6; ++t) tab[t * n + i] = v[t];
 }
 
+// Table buffer of a context: b^0, b^1, g^0, g^1 and a zero block (layout in pr_internal.cuh).
+// Eq. (koleq): b^0 = (cos y, cos z, cos x), b^1 = (sin z, sin x, sin y), c = (1, cos t);
+// g^0 = -cos y, g^1 = -sin z.  Sec. 4.2 (A = B = C = 1, phase p = sin wt):
+// sin(a + p) = cos p sin a + sin p cos a and cos(a + p) = cos p cos a - sin p sin a give
+// b^0 = the steady ABC field, b^1 = (cos z - sin y, cos x - sin z, cos y - sin x),
+// c = (cos p, sin p); g^0 = -sin z - cos y, g^1 = -cos z + sin y.
+__global__ void flow_tables_kernel(int kind, double A, double B, double C, int k, double b0,
+                                   double b1, double b2, int n, double L, double* tab) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = i * (L / n);
+    double v0[6] = {0, 0, 0, 0, 0, 0}, v1[6] = {0, 0, 0, 0, 0, 0};
+    double g0[3] = {0, 0, 0}, g1[3] = {0, 0, 0};   // GX, GY, GZ
+    const double sx = sin(x), cx = cos(x);
+    if (kind == PR_FLOW_ABC) {
+        v0[TXY] = C * cx;
+        v0[TXZ] = A * sx;
+        v0[TYX] = B * sx;
+        v0[TYZ] = A * cx;
+        v0[TZX] = B * cx;
+        v0[TZY] = C * sx;
+    } else if (kind == PR_FLOW_KOLMOGOROV) {
+        v0[TXY] = sin((double)k * x);
+    } else if (kind == PR_FLOW_CONST) {
+        v0[TXY] = b0;
+        v0[TYX] = b1;
+        v0[TZX] = b2;
+    } else if (kind == PR_FLOW_PAPER_KOLMOGOROV) {
+        v0[TXY] = cx;   // b_x: cos y + sin z cos t
+        v1[TXZ] = sx;
+        v0[TYZ] = cx;   // b_y: cos z + sin x cos t
+        v1[TYX] = sx;
+        v0[TZX] = cx;   // b_z: cos x + sin y cos t
+        v1[TZY] = sx;
+        g0[1] = -cx;    // f: -cos y - sin z cos t
+        g1[2] = -sx;
+    } else if (kind == PR_FLOW_PAPER_ABC) {
+        v0[TXZ] = sx;  v0[TXY] = cx;  v1[TXZ] = cx;  v1[TXY] = -sx;   // b_x
+        v0[TYX] = sx;  v0[TYZ] = cx;  v1[TYX] = cx;  v1[TYZ] = -sx;   // b_y
+        v0[TZY] = sx;  v0[TZX] = cx;  v1[TZY] = cx;  v1[TZX] = -sx;   // b_z
+        g0[2] = -sx;  g0[1] = -cx;  g1[2] = -cx;  g1[1] = sx;         // f
+    }
+    for (int t = 0; t < 6; ++t) {
+        tab[t * n + i] = v0[t];
+        tab[(TAB_B1 + t) * n + i] = v1[t];
+        tab[(TAB_ZERO + t) * n + i] = 0.0;
+    }
+    for (int t = 0; t < 3; ++t) {
+        tab[(TAB_G + t) * n + i] = g0[t];
+        tab[(TAB_G + 3 + t) * n + i] = g1[t];
+    }
+}
+
+cudaError_t launch_flow_tables(const pr_flow& flow, int n, double L, double* tab, cudaStream_t st) {
+    flow_tables_kernel<<<(n + 127) / 128, 128, 0, st>>>(flow.kind, flow.A, flow.B, flow.C, flow.k,
+                                                        flow.b[0], flow.b[1], flow.b[2], n, L, tab);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+// g^q(x, y, z) = GX_q[x] + GY_q[y] + GZ_q[z] as grid functions (the forcing pieces of a
+// time-dependent flow, for their projections onto V0).
+__global__ void g_fields_kernel(const double* tab, int n, double* g0, double* g1) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n3 = (long long)n * n * n;
+    if (i >= n3) return;
+    const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+    const double* G = tab + (size_t)TAB_G * n;
+    g0[i] = G[x] + G[n + y] + G[2 * n + z];
+    g1[i] = G[3 * n + x] + G[4 * n + y] + G[5 * n + z];
+}
+
+cudaError_t launch_g_fields(const double* tab, int n, double* g0, double* g1, cudaStream_t st) {
+    const long long n3 = (long long)n * n * n;
+    g_fields_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(tab, n, g0, g1);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tables(const pr_flow& flow, int n, double L, double* tab, cudaStream_t st) {
     tables_kernel<<<(n + 127) / 128, 128, 0, st>>>(flow.kind, flow.A, flow.B, flow.C, flow.k,
                                                    flow.b[0], flow.b[1], flow.b[2], n, L, tab);
@@ -223,6 +302,7 @@ struct FineShared {
     // taken once per CTA instead of once per thread
     double thr, rho, alpha, omega, beta;
     int status, flag;
+    double c0, c1;   // time coefficients of a time-dependent flow at the current step
 };
 
 // Sum of the per-CTA partials of a group for quantities 0..nq-1 (fixed order, read by
@@ -379,9 +459,13 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     const int xl = (x0 == 0) ? n - 1 : x0 - 1;   // left neighbour of the first point
     const int xr = (x0 + W == n) ? 0 : x0 + W;   // right neighbour of the last point
 
+    // velocity tables (FP64, and scaled by dt/(2h) in KT), forcing tables of the
+    // time-dependent flows (GX, GY, GZ combined for the current step), then the ring
     double* tabd = reinterpret_cast<double*>(smem_raw);
     KT* tabk = reinterpret_cast<KT*>(tabd + 6 * n);
-    unsigned char* ring_raw = smem_raw + (((size_t)6 * n * (sizeof(double) + sizeof(KT)) + 31) / 32) * 32;
+    double* ftd = reinterpret_cast<double*>(smem_raw + (size_t)6 * n * (sizeof(double) + sizeof(KT)));
+    KT* ftk = reinterpret_cast<KT*>(ftd + 3 * n);
+    unsigned char* ring_raw = smem_raw + (((size_t)9 * n * (sizeof(double) + sizeof(KT)) + 31) / 32) * 32;
     double* ringd = reinterpret_cast<double*>(ring_raw);
     KT* ringk = reinterpret_cast<KT*>(ring_raw);
     constexpr bool DF = std::is_same<KT, float>::value;   // double-float state
@@ -434,6 +518,37 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             kz_x[e] = tabk[TZX * n + x0 + e];
         }
         cur_job = jb;
+    };
+    // Time-dependent flows: the tables of b(t_new) = c0 b^0 + c1 b^1 and of the forcing
+    // part c0 g^0 + c1 g^1 for the step ending at t_new (the implicit step evaluates L and
+    // f at the new time).  Every reader of the previous tables has passed a barrier.
+    auto step_tables = [&](const FineJob& J, double t_new) {
+        if (threadIdx.x == 0) {
+            double q0, q1;
+            flow_coeffs(J.kind, J.w, t_new, q0, q1);
+            sh.c0 = q0;
+            sh.c1 = q1;
+        }
+        __syncthreads();
+        const double q0 = sh.c0, q1 = sh.c1;
+        const double* T1 = J.tab + (size_t)TAB_B1 * n;
+        const double* Gt = J.tab + (size_t)TAB_G * n;
+        for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) {
+            const double v = q0 * J.tab[i] + q1 * T1[i];
+            tabd[i] = v;
+            tabk[i] = (KT)(v * dt * 0.5 / h);
+        }
+        for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+            const double v = q0 * Gt[i] + q1 * Gt[3 * n + i];
+            ftd[i] = v;
+            ftk[i] = (KT)v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            ky_x[e] = tabk[TYX * n + x0 + e];
+            kz_x[e] = tabk[TZX * n + x0 + e];
+        }
     };
     KT kx_y[KS], kz_y[KS];
     KT kx_z = 0, ky_z = 0;
@@ -636,7 +751,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         __syncthreads();
         if (threadIdx.x == 0) sh.status = 0;
 
+        const bool tdep = J.tdep != 0;
+        const double t_item = J.t0 + lb * J.DeltaT;   // start of this subinterval
         for (int j = 1; j <= S; ++j) {
+            if (tdep) step_tables(J, t_item + j * dt);
             // ---------------- setup: u_{j-1} = u_{j-2} + delta ; r = rhat = dt (f - L u_{j-1})
             const double* P = (j <= 2) ? u_in : ust + (size_t)((j - 2) & 1) * Ng;
             double* Wt = (j >= 2) ? ust + (size_t)((j - 1) & 1) * Ng : nullptr;
@@ -687,7 +805,8 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
                               const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * c;
                               const double Lu = adv * inv2h - epsh2 * lap;
-                              const double fi = fp ? fp[i + e] : 0.0;
+                              double fi = fp ? fp[i + e] : 0.0;
+                              if (tdep) fi += ftd[x] + ftd[n + y] + ftd[2 * n + z];
                               const KT rk = (KT)(dt * (fi - Lu));
                               if (Wt) Wt[i + e] = c;
                               if (snap_j) snap_j[i + e] = c;
@@ -744,10 +863,16 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return fo;
                       },
-                      [&](int i, int k, int, const VK& fv, const float* rowc, const float* rowzp,
+                      [&](int i, int k, int yy, const VK& fv0, const float* rowc, const float* rowzp,
                           const float* rowzm) {
                           const auto q = nb7(rowc, rowzp, rowzm);
                           const VK clo = vload<float, W>(rowc + ring_lo + x0);
+                          VK fv = fv0;
+                          if (tdep) {
+                              const KT fyz = ftk[n + yy] + ftk[2 * n + i / n2];
+#pragma unroll
+                              for (int e = 0; e < W; ++e) fv.v[e] += ftk[x0 + e] + fyz;
+                          }
                           const KT ax = kx_y[k] + kx_z;
                           VK rv;
 #pragma unroll
@@ -1092,7 +1217,7 @@ static FineGeom fine_geom(int n, bool fp32) {
     g.TY = g.KS * g.RP;
     g.KF = (g.TY + 2 + g.RP - 1) / g.RP;
     g.threads = (g.lanes * g.RP + 31) / 32 * 32;   // whole warps (full-mask shuffles)
-    const size_t tabs = ((size_t)6 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 31) / 32 * 32;
+    const size_t tabs = ((size_t)9 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 31) / 32 * 32;
     g.smem = tabs + (size_t)FINE_SLOTS * (g.TY + 2) * n * sizeof(double);
     return g;
 }

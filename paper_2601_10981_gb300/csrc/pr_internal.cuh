@@ -37,6 +37,34 @@ struct Grid {
 
 enum TabIdx { TXY = 0, TXZ = 1, TYX = 2, TYZ = 3, TZX = 4, TZY = 5 };
 
+// Time-dependent flows (Sec. 4) are separable: b(x, t) = c0(t) b^0(x) + c1(t) b^1(x) and
+// f(x, t) = f_given(x) + c0(t) g^0(x) + c1(t) g^1(x), each b^q with the six 1-D tables
+// above and each g^q = GX[x] + GY[y] + GZ[z].  A context's table buffer holds
+// [b^0 (6n) | b^1 (6n) | g^0, g^1 (2 x 3n) | zeros (6n)]; steady flows have b^0 = b,
+// b^1 = 0, g = 0, c = (1, 0).
+constexpr int TAB_B1 = 6, TAB_G = 12, TAB_ZERO = 18, TAB_TOTAL = 24;   // offsets in units of n
+__host__ __device__ inline bool flow_time_dependent(int kind) {
+    return kind == PR_FLOW_PAPER_KOLMOGOROV || kind == PR_FLOW_PAPER_ABC;
+}
+// c0(t), c1(t) of the flow (and of its forcing)
+__device__ inline void flow_coeffs(int kind, double w, double t, double& c0, double& c1) {
+    if (kind == PR_FLOW_PAPER_KOLMOGOROV) {
+        c0 = 1.0;
+        c1 = cos(t);
+    } else if (kind == PR_FLOW_PAPER_ABC) {
+        const double ph = sin(w * t);
+        c0 = cos(ph);
+        c1 = sin(ph);
+    } else {
+        c0 = 1.0;
+        c1 = 0.0;
+    }
+}
+// All TAB_TOTAL * n table entries of a flow (see above).
+cudaError_t launch_flow_tables(const pr_flow& flow, int n, double L, double* tab, cudaStream_t st);
+// The forcing pieces g^0, g^1 of a table buffer as grid functions.
+cudaError_t launch_g_fields(const double* tab, int n, double* g0, double* g1, cudaStream_t st);
+
 // ---------------------------------------------------------------------------------
 // Memory-model helpers (PTX acquire/release at gpu scope).
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -129,7 +157,12 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* red) {
 // type and tile geometry with the other jobs of the launch but have their own flow,
 // diffusion, step, forcing, buffers and tolerance.
 struct FineJob {
-    const double* tab;  // velocity tables [6][n]
+    const double* tab;  // velocity tables [6][n]; time-dependent flows: the whole table
+                        // buffer [b^0 | b^1 | g^0, g^1 | 0] (TAB_TOTAL x n)
+    int tdep;           // time-dependent flow: tables rebuilt at every step
+    int kind;           // pr_flow_kind (time coefficients)
+    double w;
+    double t0, DeltaT;  // item lb of the job starts at t0 + lb DeltaT
     double eps;
     double dt;          // fine step
     int S;              // fine steps
@@ -280,9 +313,17 @@ struct CoarseSweepArgs {
     const double* R;  long long sR;
     const int* m;     long long sm;
     const double* Mr;       // R^T R, m x m with leading dimension ldM, stride sM per item
-    const double* Lr;       // R^T L R, same layout
-    long long sM;
+    const double* Lr;       // R^T L R (steady flows) or the pieces R^T D R, R^T A0 R,
+                            // R^T A1 R (time-dependent), ldM x ldM each, ldM^2 apart,
+                            // stride sML per item
+    long long sM, sML;
     int ldM;
+    // time-dependent flows: L(t) = D + c0(t) A0 + c1(t) A1 with D = -eps Lap_h and the
+    // advection pieces A_q = b^q . grad_h (antisymmetric); coarse step l of item n ends at
+    // t0 + n DeltaT + l dT
+    int tdep, kind;
+    double w, t0, DeltaT;
+    double* A1d;            // scratch [Ng] (A1 d~)
     int maxm;               // <= coarse_max_m()
     double dT;
     int Lc;
@@ -302,9 +343,16 @@ size_t coarse_part_doubles(long long Ng, int maxm);
 
 // Iteration 0: beta_n = reduced coordinates of U^0_n, n = 1..N (G_0 in V0), from
 // M0 = V0^T V0, L0 = V0^T L V0, p0 = V0^T u_hat0, q0 = V0^T f.
+// Time-dependent flows in iteration 0: L0 holds the pieces V0^T D V0, V0^T A0 V0,
+// V0^T A1 V0 (ld^2 apart) and qg the projections V0^T g^0, V0^T g^1 (ld apart).
+struct G0Tdep {
+    int tdep, kind;
+    double w, T0;
+    const double* qg;
+};
 cudaError_t launch_g0(const double* M0, const double* L0, const double* p0, const double* q0,
                       const int* m0, int ld, int N, int Lc, double dT, double* beta, int ldb,
-                      int* err, cudaStream_t st);
+                      int* err, const G0Tdep& td, cudaStream_t st);
 
 // Convergence: for n < cnt: out[n*4 + 0..3] = ||a_n-b_n||^2, ||a_n||^2, ||a_n-r_n||^2,
 // ||r_n||^2 (r may be null: last two zero).
