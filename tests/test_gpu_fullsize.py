@@ -76,3 +76,65 @@ def test_coarse_update_from_gpu_basis(kol64):
     env = rel(pert, ref)
     e = rel(U1[n + 1], ref)
     assert e < max(1e-12, 10 * env), (e, env)
+
+
+# ---------------------------------------------------------------------------------------
+# The grid sizes of the other two configurations: 128^3 ABC (eps 0.005, dt 5e-4) and 256^3
+# Kolmogorov sin(8y) (eps 0.002, dt 2.5e-4).  The fine kernel tiles them differently
+# from 64^3 (8 and 4 grid rows per CTA pass); a few steps are compared point for point.
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_fine_steps_at_128(gpu, prec):
+    bd, torch = gpu
+    from test_gpu_parity import dev
+    w = pi.Workload("abc128", 128, pi.Flow("abc"), 0.005, 1.0, 8, 5e-4, m_cap=8, f_seed=7)
+    s = bd.Parareal.from_workload(w, precision=prec)
+    op = O.make_operator(w)
+    u = np.stack([pi.initial_state(128, seed=50 + b) for b in range(2)])
+    s.set_initial(u[0], w.f())
+    out, snap = s.op_fine(dev(torch, u), 3, 3, 2)
+    out, snap = out.cpu().numpy(), snap.cpu().numpy()
+    tol = 1e-12 if prec == 0 else 1e-5
+    for b in range(2):
+        ue, W = O.fine_propagate(op, u[b], 0.0, 3, s.dt_eff, 3, 2, tol=1e-14)
+        assert rel(out[b], ue) < tol
+        assert rel(snap[b, 1], W[:, 1]) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0], ids=["fp32", "fp64"])
+def test_fine_steps_at_256(gpu, prec):
+    bd, torch = gpu
+    from test_gpu_parity import dev
+    w = pi.Workload("kol256", 256, pi.Flow("kolmogorov", k=8), 0.002, 1.0, 8, 2.5e-4, n_snap=16,
+                    m_cap=8)
+    s = bd.Parareal.from_workload(w, precision=prec)
+    op = O.make_operator(w)
+    u = pi.initial_state(256, seed=60)[None]
+    s.set_initial(u[0], None)
+    out, _ = s.op_fine(dev(torch, u), 2)
+    out = out.cpu().numpy()
+    ue, _ = O.fine_propagate(op, u[0], 0.0, 2, s.dt_eff, tol=1e-14)
+    assert rel(out[0], ue) < (1e-12 if prec == 0 else 1e-5)
+    s.close()
+
+
+def test_parareal_iteration_at_128(gpu):
+    # iteration 0 and one iteration of the method on a 128^3 ABC problem (N = 4, two fine
+    # steps per subinterval), within the method's own rounding envelope
+    bd, torch = gpu
+    from test_gpu_parity import oracle_envelope
+    w = pi.Workload("abc128_short", 128, pi.Flow("abc"), 0.005, 0.004, 4, 5e-4, n_snap=0,
+                    m_cap=4)
+    prm = O.derive_params(w)
+    hist, env = oracle_envelope(w, prm, 1, 1e-13)
+    s = bd.Parareal.from_workload(w)
+    s.set_initial(w.u0(), w.f())
+    s.iteration0()
+    U0 = s.interfaces()
+    s.iterate(1)
+    U1 = s.interfaces()
+    for k, U in ((0, U0), (1, U1)):
+        for n in range(w.n_sub + 1):
+            e = rel(U[n], hist["U"][k][n])
+            assert e < max(1e-12, 10 * env[k][n]), (k, n, e, env[k][n])
+    s.close()
