@@ -13,6 +13,10 @@ dense LU solve on tiny grids.
 
 Snapshots (Case I, Sec. 2.3): the states at steps 0, dM, 2 dM, ..., (n_s - 1) dM, the
 initial state included (reading R4).
+
+An explicit alternative to the paper's implicit Euler (not used by the paper; the build
+target names it): the classical fourth-order Runge-Kutta method (Kutta 1901) on the
+semi-discrete system u' = -L_h(t) u + f(t), fine_propagate_rk4.
 """
 from __future__ import annotations
 
@@ -101,6 +105,37 @@ def fine_propagate(op, u0: np.ndarray, t0: float, steps: int, dt: float, dM: int
         u, its = implicit_euler_step(op, u, t0 + j * dt, dt, tol, dense_A)
         if stats is not None:
             stats.append(its)
+        if n_snap > 0 and j % dM == 0 and j // dM < n_snap:
+            W[:, j // dM] = u.reshape(-1)
+    return u, W
+
+
+def rk4_step(op, u: np.ndarray, t: float, dt: float) -> np.ndarray:
+    """One classical Runge-Kutta step of u' = g(t, u) = -L_h(t) u + f(t) from t to t + dt:
+    k1 = g(t, u), k2 = g(t + dt/2, u + dt/2 k1), k3 = g(t + dt/2, u + dt/2 k2),
+    k4 = g(t + dt, u + dt k3), u_new = u + dt/6 (k1 + 2 k2 + 2 k3 + k4)."""
+    def g(tt, v):
+        out = -op.L(v, tt)
+        if op.has_forcing:
+            out = out + op.forcing(tt)
+        return out
+    k1 = g(t, u)
+    k2 = g(t + dt / 2, u + dt / 2 * k1)
+    k3 = g(t + dt / 2, u + dt / 2 * k2)
+    k4 = g(t + dt, u + dt * k3)
+    return u + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+
+def fine_propagate_rk4(op, u0: np.ndarray, t0: float, steps: int, dt: float, dM: int = 0,
+                       n_snap: int = 0):
+    """F(t0, t0 + steps*dt, u0) with rk4_step; snapshots as in fine_propagate."""
+    u = u0.copy()
+    W = None
+    if n_snap > 0:
+        W = np.zeros((u0.size, n_snap))
+        W[:, 0] = u.reshape(-1)
+    for j in range(1, steps + 1):
+        u = rk4_step(op, u, t0 + (j - 1) * dt, dt)
         if n_snap > 0 and j % dM == 0 and j // dM < n_snap:
             W[:, j // dM] = u.reshape(-1)
     return u, W

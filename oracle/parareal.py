@@ -39,7 +39,7 @@ import numpy as np
 
 from .coarse import augment, coarse_propagate
 from .discretisation import make_operator
-from .fine import fine_propagate
+from .fine import fine_propagate as _fine_implicit_euler, fine_propagate_rk4
 from .pod import level2_blocks, pod_mode
 
 
@@ -73,11 +73,12 @@ class Params:
     lin_tol: float = 1e-14
     aug_tol: float = 1e-12
     method: str = "adaptive"      # or "parareal_I" (the comparator of Sec. 4)
+    fine: str = "implicit_euler"  # or "rk4": the explicit fine integrator (not the paper's)
 
 
 def derive_params(w, T0: Optional[float] = None, dT: Optional[float] = None,
                   lin_tol: float = 1e-14, pod_tol3: Optional[float] = None,
-                  method: str = "adaptive") -> Params:
+                  method: str = "adaptive", fine: str = "implicit_euler") -> Params:
     N = w.n_sub
     DeltaT = w.T / N
     S = steps_for(DeltaT, w.dt)
@@ -99,8 +100,17 @@ def derive_params(w, T0: Optional[float] = None, dT: Optional[float] = None,
     g3 = 1.0 - (w.pod_tol * 4e-3 if pod_tol3 is None else pod_tol3)
     if method not in ("adaptive", "parareal_I"):
         raise ValueError(f"unknown method {method!r}")
+    if fine not in ("implicit_euler", "rk4"):
+        raise ValueError(f"unknown fine integrator {fine!r}")
     return Params(N, DeltaT, S, dt, T0, S0, DeltaT / Lc, Lc, dM, n_s, n_s0, g12, g12, g3,
-                  w.m_cap, w.m_l, w.p, lin_tol=lin_tol, method=method)
+                  w.m_cap, w.m_l, w.p, lin_tol=lin_tol, method=method, fine=fine)
+
+
+# The fine propagator selected by the parameters (the module-level name stays patchable).
+def fine_propagate(op, u0, t0, steps, dt, dM=0, n_snap=0, tol=1e-14, prm=None, **kw):
+    if prm is not None and prm.fine == "rk4":
+        return fine_propagate_rk4(op, u0, t0, steps, dt, dM, n_snap)
+    return _fine_implicit_euler(op, u0, t0, steps, dt, dM, n_snap, tol=tol, **kw)
 
 
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
@@ -112,10 +122,11 @@ def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
 def sequential_fine(w, prm: Params, op=None) -> List[np.ndarray]:
     """U_n = F(0, t_n, u0), n = 0..N, marching one subinterval after another."""
     op = make_operator(w) if op is None else op
-    u, _ = fine_propagate(op, w.u0(), 0.0, prm.S0, prm.dt, tol=prm.lin_tol)
+    u, _ = fine_propagate(op, w.u0(), 0.0, prm.S0, prm.dt, tol=prm.lin_tol, prm=prm)
     out = [u]
     for n in range(prm.N):
-        u, _ = fine_propagate(op, u, prm.T0 + n * prm.DeltaT, prm.S, prm.dt, tol=prm.lin_tol)
+        u, _ = fine_propagate(op, u, prm.T0 + n * prm.DeltaT, prm.S, prm.dt, tol=prm.lin_tol,
+                              prm=prm)
         out.append(u)
     return out
 
@@ -123,7 +134,7 @@ def sequential_fine(w, prm: Params, op=None) -> List[np.ndarray]:
 def iteration0(w, prm: Params, op):
     """Case I: fine on [0, T0], V0 = POD_Mode(W, gamma1), U^0 by G_0 (eq. (formula4))."""
     u_hat0, W = fine_propagate(op, w.u0(), 0.0, prm.S0, prm.dt, prm.dM, prm.n_s0,
-                               tol=prm.lin_tol)
+                               tol=prm.lin_tol, prm=prm)
     V0, m0, _ = pod_mode(W, prm.gamma1, prm.m_cap, prm.tau)
     U = [u_hat0]
     for n in range(prm.N):
@@ -163,10 +174,10 @@ def parareal(w, prm: Params, k_max: int = 0, tol: float = 0.0, reference=None,
         for n in range(k - 1, N):
             if plain:
                 F[n], _ = fine_propagate(op, U_prev[n], prm.T0 + n * prm.DeltaT, prm.S, prm.dt,
-                                         tol=prm.lin_tol)
+                                         tol=prm.lin_tol, prm=prm)
                 continue
             Fn, Wn = fine_propagate(op, U_prev[n], prm.T0 + n * prm.DeltaT, prm.S, prm.dt,
-                                    prm.dM, prm.n_s, tol=prm.lin_tol)
+                                    prm.dM, prm.n_s, tol=prm.lin_tol, prm=prm)
             F[n] = Fn
             R1, m, _ = pod_mode(Wn, prm.gamma2, prm.m_cap, prm.tau)
             level1_store.setdefault(n, {})[k] = R1
