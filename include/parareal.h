@@ -97,7 +97,15 @@ typedef struct pr_opts {
     long long spin_limit;   /* polls of an in-kernel barrier before PR_ERR_TIMEOUT
                                (default 1<<22, about a second)                            */
     int method;             /* enum pr_method; default PR_METHOD_ADAPTIVE                 */
+    int fine;               /* enum pr_fine; default PR_FINE_IMPLICIT_EULER               */
 } pr_opts;
+
+/* Fine integrator.  PR_FINE_IMPLICIT_EULER: the paper's, eq. (semi-dis-eq), BiCGStab per
+ * step.  PR_FINE_RK4: the classical explicit fourth-order Runge-Kutta method on
+ * u' = f(t) - L_h(t) u with the same step (no counterpart in the paper; the caller keeps
+ * dt within its stability bound, about 2.78 / (12 eps / h^2) for diffusion and
+ * 2.8 h / (|b_x| + |b_y| + |b_z|) for advection). */
+enum pr_fine { PR_FINE_IMPLICIT_EULER = 0, PR_FINE_RK4 = 1 };
 
 /* PR_METHOD_ADAPTIVE: Algorithm 2.  PR_METHOD_PARAREAL_I: the comparator "Parareal-I" of
  * Sec. 4, plain parareal whose coarse space is the iteration-0 POD space V0 for every

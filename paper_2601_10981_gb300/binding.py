@@ -23,6 +23,7 @@ PR_FLOW_ABC, PR_FLOW_KOLMOGOROV, PR_FLOW_CONST = 0, 1, 2
 PR_FLOW_PAPER_KOLMOGOROV, PR_FLOW_PAPER_ABC = 3, 4
 PR_FP64, PR_FP32 = 0, 1
 PR_METHOD_ADAPTIVE, PR_METHOD_PARAREAL_I = 0, 1
+PR_FINE_IMPLICIT_EULER, PR_FINE_RK4 = 0, 1
 
 
 class pr_grid(C.Structure):
@@ -39,7 +40,8 @@ class pr_opts(C.Structure):
                 ("m_l", C.c_int), ("p", C.c_int), ("pod_tol3", C.c_double),
                 ("rank_tau", C.c_double), ("precision", C.c_int), ("lin_tol", C.c_double),
                 ("lin_maxit", C.c_int), ("aug_tol", C.c_double), ("group_ctas", C.c_int),
-                ("ctas_per_sm", C.c_int), ("spin_limit", C.c_longlong), ("method", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("spin_limit", C.c_longlong), ("method", C.c_int),
+                ("fine", C.c_int)]
 
 
 class pr_report(C.Structure):

@@ -458,6 +458,7 @@ pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int
     FineJob& J = a.jobs[0];
     J.tab = c->tab;
     J.tdep = c->tdep ? 1 : 0;
+    J.rk4 = c->o.fine == PR_FINE_RK4 ? 1 : 0;
     J.kind = c->flow.kind;
     J.w = c->flow.w;
     J.t0 = t0;
@@ -537,6 +538,7 @@ void pr_opts_init(pr_opts* o) {
     o->aug_tol = 1e-12;
     o->spin_limit = 1LL << 22;
     o->method = PR_METHOD_ADAPTIVE;
+    o->fine = PR_FINE_IMPLICIT_EULER;
 }
 
 const char* pr_status_string(pr_status s) {
@@ -574,6 +576,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (o.m_l < 0 || o.m_l > 1 || o.p < 0 || o.p > 1) return PR_ERR_UNSUPPORTED;
     if (o.precision != PR_FP64 && o.precision != PR_FP32) return PR_ERR_INVALID_ARG;
     if (o.method != PR_METHOD_ADAPTIVE && o.method != PR_METHOD_PARAREAL_I) return PR_ERR_INVALID_ARG;
+    if (o.fine != PR_FINE_IMPLICIT_EULER && o.fine != PR_FINE_RK4) return PR_ERR_INVALID_ARG;
     if (o.lin_maxit <= 0) o.lin_maxit = 200;
     if (o.spin_limit < 0) o.spin_limit = 1LL << 22;
     if (o.aug_tol <= 0) o.aug_tol = 1e-12;
@@ -830,8 +833,9 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         if (!c->ws_ready) return fail(c, PR_ERR_STATE, "workspace not initialised (pr_set_initial first)");
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return fail(c, PR_ERR_INVALID_ARG, "a context appears twice");
-        if (owner && (c->n != owner->n || c->L != owner->L || c->fp32 != owner->fp32))
-            return fail(c, PR_ERR_INVALID_ARG, "batched contexts need the same grid and precision");
+        if (owner && (c->n != owner->n || c->L != owner->L || c->fp32 != owner->fp32 ||
+                      c->o.fine != owner->o.fine))
+            return fail(c, PR_ERR_INVALID_ARG, "batched contexts need the same grid, precision and fine integrator");
         if (!owner || c->groups_max > owner->groups_max) owner = c;
     }
     FineArgs a{};
@@ -845,6 +849,7 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         FineJob& J = a.jobs[i];
         J.tab = c->tab;
         J.tdep = c->tdep ? 1 : 0;
+        J.rk4 = c->o.fine == PR_FINE_RK4 ? 1 : 0;
         J.kind = c->flow.kind;
         J.w = c->flow.w;
         J.t0 = c->T0 + (k - 1) * c->DeltaT;

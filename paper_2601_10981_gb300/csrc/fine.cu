@@ -432,7 +432,9 @@ template <typename T, int W> struct Nb7 { Vec<T, W> c, xp, xm, yp, ym, zp, zm; }
 
 // KT: Krylov type.  W: points per thread along x.  KF: ring rows each thread fills per
 // plane (ceil((TY+2)/RP)).  KS: owned rows per thread per plane (TY/RP).
-template <typename KT, int W, int KF, int KS>
+// RK: the explicit RK4 path instead of implicit Euler (a separate instantiation, so that
+// neither path's register allocation burdens the other).
+template <typename KT, int W, int KF, int KS, bool RK>
 __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ FineShared sh;
@@ -753,6 +755,187 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
 
         const bool tdep = J.tdep != 0;
         const double t_item = J.t0 + lb * J.DeltaT;   // start of this subinterval
+        if constexpr (RK) {
+            // ---------------- explicit alternative: classical RK4 on u' = f(t) - L(t) u.
+            // Stage s is the residual pass of the implicit setup on the operand
+            // v_s = u + a_s kappa_{s-1}: kappa_s = dt (f(t_s) - L(t_s) v_s), a = 0, 1/2,
+            // 1/2, 1 at t_s = t, t + dt/2, t + dt/2, t + dt; the last stage forms
+            // u_new = u + (kappa_1 + 2 kappa_2 + 2 kappa_3 + kappa_4) / 6 at owned points.
+            KT* kap[3] = {delta, r, rh};
+            const KT dtf = (KT)dt;
+            for (int j = 1; j <= S; ++j) {
+                const double tj = t_item + (j - 1) * dt;
+                const double* Pd = (j == 1) ? u_in : ust + (size_t)((j - 1) & 1) * Ng;   // u_{j-1}
+                double* Wd = (j == S) ? nullptr : ust + (size_t)(j & 1) * Ng;            // u_j
+                double* outS = (j == S) ? J.u_out + (size_t)lb * Ng : nullptr;
+                double* snap_prev = (snap_b && (j - 1) % dM == 0 && (j - 1) / dM < n_snap)
+                                        ? snap_b + (size_t)((j - 1) / dM) * Ng : nullptr;
+                double* snap_new = (j == S && snap_b && S % dM == 0 && S / dM < n_snap)
+                                       ? snap_b + (size_t)(S / dM) * Ng : nullptr;
+                for (int stg = 0; stg < 4; ++stg) {
+                    const double ts = tj + (stg == 0 ? 0.0 : (stg == 3 ? dt : 0.5 * dt));
+                    const KT ca = (KT)(stg == 0 ? 0.0 : (stg == 3 ? 1.0 : 0.5));
+                    if (tdep) step_tables(J, ts);
+                    const KT* kin = stg ? kap[stg - 1] : nullptr;
+                    KT* kout = stg < 3 ? kap[stg] : nullptr;
+                    const bool last = stg == 3;
+                    if constexpr (!DF) {
+                        const double* fp = J.f;
+                        march(false, ringd,
+                              [&](int i) -> RawSetup<double, KT, W> {
+                                  RawSetup<double, KT, W> o;
+                                  o.u = vload<double, W>(Pd + i);
+                                  if (kin) o.d = vload<KT, W>(kin + i);
+                                  else {
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                                  }
+                                  return o;
+                              },
+                              [&](const RawSetup<double, KT, W>& v) -> VD {
+                                  VD o;
+#pragma unroll
+                                  for (int e = 0; e < W; ++e) o.v[e] = v.u.v[e] + (double)ca * (double)v.d.v[e];
+                                  return o;
+                              },
+                              [&](int) -> NoOwn { return NoOwn{}; },
+                              [&](int i, int, int y, const NoOwn&, const double* rowc, const double* rowzp,
+                                  const double* rowzm) {
+                                  const int z = i / n2;
+                                  const double bx = tabd[TXY * n + y] + tabd[TXZ * n + z];
+                                  const double byz = tabd[TYZ * n + z], bzy = tabd[TZY * n + y];
+#pragma unroll 1
+                                  for (int e = 0; e < W; ++e) {
+                                      const int x = x0 + e;
+                                      const int xp = (e == W - 1) ? xr : x + 1;
+                                      const int xm = (e == 0) ? xl : x - 1;
+                                      const double c = rowc[x];
+                                      const double uxp = rowc[xp], uxm = rowc[xm];
+                                      const double uyp = rowc[n + x], uym = rowc[x - n];
+                                      const double uzp = rowzp[x], uzm = rowzm[x];
+                                      const double by = tabd[TYX * n + x] + byz;
+                                      const double bz = tabd[TZX * n + x] + bzy;
+                                      const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
+                                      const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * c;
+                                      double fi = fp ? fp[i + e] : 0.0;
+                                      if (tdep) fi += ftd[x] + ftd[n + y] + ftd[2 * n + z];
+                                      const double kp = dt * (fi - (adv * inv2h - epsh2 * lap));
+                                      if (stg == 0 && snap_prev) snap_prev[i + e] = c;
+                                      if (!last) {
+                                          kout[i + e] = (KT)kp;
+                                      } else {
+                                          const double un = Pd[i + e] +
+                                              ((double)kap[0][i + e] + 2.0 * (double)kap[1][i + e] +
+                                               2.0 * (double)kap[2][i + e] + kp) / 6.0;
+                                          if (Wd) Wd[i + e] = un;
+                                          if (outS) outS[i + e] = un;
+                                          if (snap_new) snap_new[i + e] = un;
+                                      }
+                                  }
+                              });
+                    } else {
+                        const float2* Pf = (j == 1) ? nullptr : reinterpret_cast<const float2*>(Pd);
+                        float2* Wf = reinterpret_cast<float2*>(Wd);
+                        const float* ff = J.f32;
+                        float* ringh = reinterpret_cast<float*>(ring_raw);
+                        march(true, ringh,
+                              [&](int i) -> RawSetup<float2, KT, W> {
+                                  RawSetup<float2, KT, W> o;
+                                  if (Pf) o.u = vload<float2, W>(Pf + i);
+                                  else {
+                                      const VD ud = vload<double, W>(u_in + i);
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) o.u.v[e] = df_split(ud.v[e]);
+                                  }
+                                  if (kin) o.d = vload<KT, W>(kin + i);
+                                  else {
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                                  }
+                                  return o;
+                              },
+                              [&](const RawSetup<float2, KT, W>& v) -> HiLo<W> {
+                                  HiLo<W> o;
+#pragma unroll
+                                  for (int e = 0; e < W; ++e) {
+                                      const float2 u = df_add(v.u.v[e], ca * v.d.v[e]);
+                                      o.hi.v[e] = u.x;
+                                      o.lo.v[e] = u.y;
+                                  }
+                                  return o;
+                              },
+                              [&](int i) -> VK {
+                                  VK fo;
+                                  if (ff) fo = vload<KT, W>(ff + i);
+                                  else {
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) fo.v[e] = (KT)0;
+                                  }
+                                  return fo;
+                              },
+                              [&](int i, int k, int yy, const VK& fv0, const float* rowc, const float* rowzp,
+                                  const float* rowzm) {
+                                  const auto q = nb7(rowc, rowzp, rowzm);
+                                  VK fv = fv0;
+                                  if (tdep) {
+                                      const KT fyz = ftk[n + yy] + ftk[2 * n + i / n2];
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) fv.v[e] += ftk[x0 + e] + fyz;
+                                  }
+                                  const KT ax = kx_y[k] + kx_z;
+                                  VK kv;
+#pragma unroll
+                                  for (int e = 0; e < W; ++e) {
+                                      const float c = q.c.v[e];
+                                      const KT ay = ky_x[e] + ky_z;
+                                      const KT az = kz_x[e] + kz_y[k];
+                                      const KT dx = __fsub_rn(q.xp.v[e], q.xm.v[e]);
+                                      const KT dy = __fsub_rn(q.yp.v[e], q.ym.v[e]);
+                                      const KT dz = __fsub_rn(q.zp.v[e], q.zm.v[e]);
+                                      const KT sx = __fsub_rn(__fsub_rn(q.xp.v[e], c), __fsub_rn(c, q.xm.v[e]));
+                                      const KT sy = __fsub_rn(__fsub_rn(q.yp.v[e], c), __fsub_rn(c, q.ym.v[e]));
+                                      const KT sz = __fsub_rn(__fsub_rn(q.zp.v[e], c), __fsub_rn(c, q.zm.v[e]));
+                                      kv.v[e] = dtf * fv.v[e] - (ax * dx + ay * dy + az * dz) + c1 * ((sx + sy) + sz);
+                                  }
+                                  if (stg == 0 && snap_prev) {
+                                      const VK clo = vload<float, W>(rowc + ring_lo + x0);
+                                      VD sd;
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) sd.v[e] = df_value_bits(q.c.v[e], clo.v[e]);
+                                      vstore(snap_prev + i, sd);
+                                  }
+                                  if (!last) {
+                                      vstore(kout + i, kv);
+                                      return;
+                                  }
+                                  // u_new = u + (k1 + 2 k2 + 2 k3 + k4) / 6, the state as a float pair
+                                  Vec<float2, W> u2;
+                                  if (Pf) u2 = vload<float2, W>(Pf + i);
+                                  else {
+                                      const VD ud = vload<double, W>(u_in + i);
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) u2.v[e] = df_split(ud.v[e]);
+                                  }
+                                  const VK k1 = vload<KT, W>(kap[0] + i), k2 = vload<KT, W>(kap[1] + i);
+                                  const VK k3 = vload<KT, W>(kap[2] + i);
+#pragma unroll
+                                  for (int e = 0; e < W; ++e)
+                                      u2.v[e] = df_add(u2.v[e], (k1.v[e] + 2.0f * k2.v[e] + 2.0f * k3.v[e] + kv.v[e]) *
+                                                                    (1.0f / 6.0f));
+                                  if (Wf) vstore(Wf + i, u2);
+                                  if (outS || snap_new) {
+                                      VD ud;
+#pragma unroll
+                                      for (int e = 0; e < W; ++e) ud.v[e] = df_value_bits(u2.v[e].x, u2.v[e].y);
+                                      if (outS) vstore(outS + i, ud);
+                                      if (snap_new) vstore(snap_new + i, ud);
+                                  }
+                              });
+                    }
+                    if (!group_barrier(bar, G, a.spin_limit, a.err)) return;
+                }
+            }
+        } else {
         for (int j = 1; j <= S; ++j) {
             if (tdep) step_tables(J, t_item + j * dt);
             // ---------------- setup: u_{j-1} = u_{j-2} + delta ; r = rhat = dt (f - L u_{j-1})
@@ -1184,6 +1367,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                       });
             }
         }
+        }   // implicit Euler
         if (q == 0 && threadIdx.x == 0) {
             J.status[lb] = sh.status;
             J.its_total[lb] = (int)its_total;
@@ -1226,9 +1410,9 @@ int fine_block_threads(int n) { return fine_geom(n, true).threads; }
 int fine_tile_rows(int n) { return fine_geom(n, true).TY; }
 
 using FineFn = void (*)(FineArgs);
-template <typename KT, int W>
+template <typename KT, int W, bool RK>
 static FineFn fine_fn(int KF, int KS) {
-#define PR_FINE_CASE(F, S_) if (KF <= F && KS <= S_) return fine_kernel<KT, W, F, S_>;
+#define PR_FINE_CASE(F, S_) if (KF <= F && KS <= S_) return fine_kernel<KT, W, F, S_, RK>;
     PR_FINE_CASE(2, 1)
     PR_FINE_CASE(3, 1)
     PR_FINE_CASE(3, 2)
@@ -1237,10 +1421,14 @@ static FineFn fine_fn(int KF, int KS) {
     return nullptr;
 }
 
-static FineFn fine_select(int n, bool fp32) {
+static FineFn fine_select(int n, bool fp32, bool rk = false) {
     const FineGeom g = fine_geom(n, fp32);
-    if (g.W == 4) return fp32 ? fine_fn<float, 4>(g.KF, g.KS) : fine_fn<double, 4>(g.KF, g.KS);
-    return fp32 ? fine_fn<float, 1>(g.KF, g.KS) : fine_fn<double, 1>(g.KF, g.KS);
+    if (rk) {
+        if (g.W == 4) return fp32 ? fine_fn<float, 4, true>(g.KF, g.KS) : fine_fn<double, 4, true>(g.KF, g.KS);
+        return fp32 ? fine_fn<float, 1, true>(g.KF, g.KS) : fine_fn<double, 1, true>(g.KF, g.KS);
+    }
+    if (g.W == 4) return fp32 ? fine_fn<float, 4, false>(g.KF, g.KS) : fine_fn<double, 4, false>(g.KF, g.KS);
+    return fp32 ? fine_fn<float, 1, false>(g.KF, g.KS) : fine_fn<double, 1, false>(g.KF, g.KS);
 }
 
 int fine_max_ctas(int n, bool fp32, int ctas_per_sm) {
@@ -1261,8 +1449,16 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     if (a.B <= 0) return cudaSuccess;
     const int n = a.g.n;
     if (n > 256 || n < 4) return cudaErrorInvalidValue;
-    FineFn fn = fine_select(n, fp32);
+    const bool rk = a.jobs[0].rk4 != 0;
+    for (int j = 1; j < a.njobs; ++j)
+        if ((a.jobs[j].rk4 != 0) != rk) return cudaErrorInvalidValue;   // one integrator per launch
+    FineFn fn = fine_select(n, fp32, rk);
     if (!fn) return cudaErrorInvalidValue;
+    if (rk) {
+        const FineGeom g2 = fine_geom(n, fp32);
+        if (g2.smem > 48 * 1024)
+            cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g2.smem);
+    }
     const FineGeom geo = fine_geom(n, fp32);
     const int max_ctas = fine_max_ctas(n, fp32, ctas_per_sm);
     a.TY = geo.TY;

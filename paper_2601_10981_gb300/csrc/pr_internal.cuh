@@ -160,6 +160,7 @@ struct FineJob {
     const double* tab;  // velocity tables [6][n]; time-dependent flows: the whole table
                         // buffer [b^0 | b^1 | g^0, g^1 | 0] (TAB_TOTAL x n)
     int tdep;           // time-dependent flow: tables rebuilt at every step
+    int rk4;            // explicit classical RK4 instead of implicit Euler + BiCGStab
     int kind;           // pr_flow_kind (time coefficients)
     double w;
     double t0, DeltaT;  // item lb of the job starts at t0 + lb DeltaT

@@ -49,9 +49,11 @@ struct Req {
     std::string err;
 };
 
-using ShapeKey = std::tuple<int, double, int>;   // n, box length, precision
+using ShapeKey = std::tuple<int, double, int, int>;   // n, box length, precision, fine integrator
 
-ShapeKey shape_of(const pr_request& r) { return ShapeKey(r.grid.n, r.grid.L, r.opts.precision); }
+ShapeKey shape_of(const pr_request& r) {
+    return ShapeKey(r.grid.n, r.grid.L, r.opts.precision, r.opts.fine);
+}
 
 }  // namespace
 
