@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "parareal wall time at rel L2<=1e-6; fine GDOF-steps/s vs HBM roof; p50/p99 lat"
 UNIT = "GDOF-steps/s"
-FINE_SRC = os.path.join(ROOT, "paper_2601_10981_gb300", "csrc", "fine.cu")
+FINE_SRC = os.path.join(ROOT, "paper_2601_10981_gb300", "csrc", "fine_kernel.cuh")
 
 
 def workload(subintervals: int = 0):
