@@ -59,3 +59,37 @@ def augment(R: np.ndarray, U: np.ndarray, aug_tol: float = 1e-12):
     if nd <= aug_tol * np.linalg.norm(u):
         return R, False
     return np.concatenate([R, (d / nd)[:, None]], axis=1), True
+
+
+# ------------------------------------------------------------------------------------
+# Coarse-grid propagator of the comparator "Parareal-II" (Sec. 4): the same problem on a
+# grid coarsened by a factor c in every direction (the paper coarsens the FEM mesh by
+# three bisections, i.e. a factor 2), implicit Euler with the coarse step dT, restriction
+# by injection and prolongation by trilinear interpolation on the periodic grid.
+
+def restrict(u: np.ndarray, c: int) -> np.ndarray:
+    """Injection: the values at the coarse points x_{c i}."""
+    return np.ascontiguousarray(u[::c, ::c, ::c])
+
+
+def prolong(uc: np.ndarray, c: int) -> np.ndarray:
+    """Trilinear interpolation from the coarse points to every fine point (periodic)."""
+    out = uc
+    for axis in range(3):
+        nc = out.shape[axis]
+        w = np.arange(c) / c                        # offset of fine point j*c + a is a/c
+        lo = np.repeat(out, c, axis=axis)           # u_c[j] at fine points j*c + a
+        hi = np.repeat(np.roll(out, -1, axis=axis), c, axis=axis)
+        shape = [1, 1, 1]
+        shape[axis] = nc * c
+        wt = np.tile(w, nc).reshape(shape)
+        out = (1.0 - wt) * lo + wt * hi
+    return out
+
+
+def coarse_grid_propagate(op_c, x: np.ndarray, t_a: float, n_steps: int, dT: float, c: int):
+    """P G_c(R x): n_steps implicit Euler steps of size dT on the coarse operator op_c
+    (with its forcing), from the restriction of x, interpolated back."""
+    from .fine import fine_propagate
+    uc, _ = fine_propagate(op_c, restrict(x, c), t_a, n_steps, dT, tol=1e-14)
+    return prolong(uc, c)

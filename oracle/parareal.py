@@ -21,7 +21,13 @@ Stop when max_n ||U^k_n - U^{k-1}_n|| / ||U^k_n|| <= tol, or k = N, or k = k_max
 The comparator "Parareal-I" of Sec. 4 (method = "parareal_I") is plain parareal with
 the POD space of iteration 0 as the coarse space for every subinterval and iteration:
 no level-1 or level-2 POD and no augmentation, U^k_{n+1} = G_{V0}(U^k_n) + F_n -
-G_{V0}(U^{k-1}_n); the paper gives it a longer Case-I window (T0 = 10).  The error of eq. (error) is measured against the sequential fine
+G_{V0}(U^{k-1}_n); the paper gives it a longer Case-I window (T0 = 10).
+
+The comparator "Parareal-II" (method = "parareal_II") is plain parareal whose coarse
+propagator is implicit Euler with step dT on a grid coarsened by coarse_factor (2):
+G(x) = P G_c(R x), restriction by injection, prolongation by trilinear interpolation
+(reading R18).  Iteration 0 keeps the Case-I window [0, T0] of the other methods
+(u_hat0 = F(0, T0, u0)) and then U^0_{n+1} = G(U^0_n).  The error of eq. (error) is measured against the sequential fine
 solution U_n = F(0, t_n, u0).
 
 Parameter readings (R3, R4, R15, R16): S = fine steps per subinterval is DeltaT/dt
@@ -37,7 +43,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from .coarse import augment, coarse_propagate
+from .coarse import augment, coarse_grid_propagate, coarse_propagate, restrict
+from .discretisation import Grid, Operator
 from .discretisation import make_operator
 from .fine import fine_propagate as _fine_implicit_euler, fine_propagate_rk4
 from .pod import level2_blocks, pod_mode
@@ -72,13 +79,15 @@ class Params:
     tau: float = 1e-13
     lin_tol: float = 1e-14
     aug_tol: float = 1e-12
-    method: str = "adaptive"      # or "parareal_I" (the comparator of Sec. 4)
+    method: str = "adaptive"      # or "parareal_I" / "parareal_II" (comparators of Sec. 4)
     fine: str = "implicit_euler"  # or "rk4": the explicit fine integrator (not the paper's)
+    coarse_factor: int = 2        # Parareal-II: grid coarsening factor
 
 
 def derive_params(w, T0: Optional[float] = None, dT: Optional[float] = None,
                   lin_tol: float = 1e-14, pod_tol3: Optional[float] = None,
-                  method: str = "adaptive", fine: str = "implicit_euler") -> Params:
+                  method: str = "adaptive", fine: str = "implicit_euler",
+                  coarse_factor: int = 2) -> Params:
     N = w.n_sub
     DeltaT = w.T / N
     S = steps_for(DeltaT, w.dt)
@@ -98,12 +107,13 @@ def derive_params(w, T0: Optional[float] = None, dT: Optional[float] = None,
         n_s0 = min(n_s0, w.n_snap)
     g12 = 1.0 - w.pod_tol
     g3 = 1.0 - (w.pod_tol * 4e-3 if pod_tol3 is None else pod_tol3)
-    if method not in ("adaptive", "parareal_I"):
+    if method not in ("adaptive", "parareal_I", "parareal_II"):
         raise ValueError(f"unknown method {method!r}")
     if fine not in ("implicit_euler", "rk4"):
         raise ValueError(f"unknown fine integrator {fine!r}")
     return Params(N, DeltaT, S, dt, T0, S0, DeltaT / Lc, Lc, dM, n_s, n_s0, g12, g12, g3,
-                  w.m_cap, w.m_l, w.p, lin_tol=lin_tol, method=method, fine=fine)
+                  w.m_cap, w.m_l, w.p, lin_tol=lin_tol, method=method, fine=fine,
+                  coarse_factor=coarse_factor)
 
 
 # The fine propagator selected by the parameters (the module-level name stays patchable).
@@ -131,8 +141,23 @@ def sequential_fine(w, prm: Params, op=None) -> List[np.ndarray]:
     return out
 
 
+def coarse_operator(op, c: int):
+    """The problem on the grid coarsened by c (Parareal-II): same flow and eps, the
+    forcing at the coarse points."""
+    f = None if op.f is None else restrict(op.f, c)
+    return Operator(Grid(op.grid.n // c, op.grid.L), op.flow, op.eps, f)
+
+
 def iteration0(w, prm: Params, op):
     """Case I: fine on [0, T0], V0 = POD_Mode(W, gamma1), U^0 by G_0 (eq. (formula4))."""
+    if prm.method == "parareal_II":
+        u_hat0, _ = fine_propagate(op, w.u0(), 0.0, prm.S0, prm.dt, tol=prm.lin_tol, prm=prm)
+        op_c = coarse_operator(op, prm.coarse_factor)
+        U = [u_hat0]
+        for n in range(prm.N):
+            U.append(coarse_grid_propagate(op_c, U[n], prm.T0 + n * prm.DeltaT, prm.Lc, prm.dT,
+                                           prm.coarse_factor))
+        return U, None, 0
     u_hat0, W = fine_propagate(op, w.u0(), 0.0, prm.S0, prm.dt, prm.dM, prm.n_s0,
                                tol=prm.lin_tol, prm=prm)
     V0, m0, _ = pod_mode(W, prm.gamma1, prm.m_cap, prm.tau)
@@ -167,7 +192,8 @@ def parareal(w, prm: Params, k_max: int = 0, tol: float = 0.0, reference=None,
         return store[max(cands)] if cands else None
 
     k_done = 0
-    plain = prm.method == "parareal_I"
+    plain = prm.method in ("parareal_I", "parareal_II")
+    op_c = coarse_operator(op, prm.coarse_factor) if prm.method == "parareal_II" else None
     for k in range(1, k_max + 1):
         F: Dict[int, np.ndarray] = {}
         m1 = {}
@@ -191,6 +217,12 @@ def parareal(w, prm: Params, k_max: int = 0, tol: float = 0.0, reference=None,
         for n in range(k, N):
             if plain:
                 t_n = prm.T0 + n * prm.DeltaT
+                if op_c is not None:
+                    g_new = coarse_grid_propagate(op_c, U[n], t_n, prm.Lc, prm.dT, prm.coarse_factor)
+                    g_old = coarse_grid_propagate(op_c, U_prev[n], t_n, prm.Lc, prm.dT,
+                                                  prm.coarse_factor)
+                    U[n + 1] = g_new + F[n] - g_old
+                    continue
                 g_new, _ = coarse_propagate(op, V0, U[n], t_n, prm.Lc, prm.dT)
                 g_old, _ = coarse_propagate(op, V0, U_prev[n], t_n, prm.Lc, prm.dT)
                 U[n + 1] = (g_new + F[n].reshape(-1) - g_old).reshape(shape)
