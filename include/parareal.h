@@ -110,8 +110,12 @@ enum pr_fine { PR_FINE_IMPLICIT_EULER = 0, PR_FINE_RK4 = 1 };
 /* PR_METHOD_ADAPTIVE: Algorithm 2.  PR_METHOD_PARAREAL_I: the comparator "Parareal-I" of
  * Sec. 4, plain parareal whose coarse space is the iteration-0 POD space V0 for every
  * subinterval and iteration (no level-1/2 POD, no augmentation; pr_pod_update does
- * nothing, snapshots are not taken); the paper gives it a longer window T0 = 10. */
-enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1 };
+ * nothing, snapshots are not taken); the paper gives it a longer window T0 = 10.
+ * PR_METHOD_PARAREAL_II: the comparator "Parareal-II", plain parareal whose coarse
+ * propagator is implicit Euler with step dT on the grid coarsened by 2 (n even, n/2 >= 4):
+ * G(x) = P G_c(R x), restriction by injection, trilinear prolongation; iteration 0 keeps
+ * the Case-I window [0, T0] and then U^0_{n+1} = G(U^0_n). */
+enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1, PR_METHOD_PARAREAL_II = 2 };
 
 /* Per-solve report (pr_solve).  Times are seconds measured with CUDA events. */
 typedef struct pr_report {

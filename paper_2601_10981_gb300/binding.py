@@ -22,7 +22,7 @@ STATUS = {0: "PR_OK", 1: "PR_ERR_INVALID_ARG", 2: "PR_ERR_OOM", 3: "PR_ERR_CUDA"
 PR_FLOW_ABC, PR_FLOW_KOLMOGOROV, PR_FLOW_CONST = 0, 1, 2
 PR_FLOW_PAPER_KOLMOGOROV, PR_FLOW_PAPER_ABC = 3, 4
 PR_FP64, PR_FP32 = 0, 1
-PR_METHOD_ADAPTIVE, PR_METHOD_PARAREAL_I = 0, 1
+PR_METHOD_ADAPTIVE, PR_METHOD_PARAREAL_I, PR_METHOD_PARAREAL_II = 0, 1, 2
 PR_FINE_IMPLICIT_EULER, PR_FINE_RK4 = 0, 1
 
 

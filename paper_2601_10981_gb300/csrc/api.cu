@@ -95,6 +95,21 @@ struct pr_ctx {
     double* qg = nullptr;         // V0^T g^0, V0^T g^1 (time-dependent flows)
     double* gq = nullptr;         // g^0, g^1 as grid functions (time-dependent flows)
     double* cA1 = nullptr;        // coarse-sweep scratch A1 d~
+    // Parareal-II: the grid coarsened by 2, its tables, forcing, fine-kernel workspace,
+    // the restricted input, the coarse output and iteration 0's coarse trajectory
+    int nc = 0;
+    long long Ngc = 0;
+    double* tabc = nullptr;
+    double* fc = nullptr;
+    float* fc32 = nullptr;
+    void* fwsc = nullptr;
+    double* ustc = nullptr;
+    double* fpartc = nullptr;
+    unsigned* fbarc = nullptr;
+    int max_ctas_c = 1;
+    double* xc = nullptr;
+    double* yc = nullptr;
+    double* trajc = nullptr;
     double* beta = nullptr;
     double* gout = nullptr;
     double* lam = nullptr;
@@ -191,6 +206,20 @@ size_t plan(pr_ctx* c, char* base) {
     c->qg = b.take<double>((size_t)2 * c->mcap0);
     c->gq = c->tdep ? b.take<double>((size_t)2 * Ng) : nullptr;
     c->cA1 = b.take<double>(Ng);
+    if (c->o.method == PR_METHOD_PARAREAL_II) {
+        const long long Ngc = c->Ngc;
+        const size_t kesz2 = c->fp32 ? sizeof(float) : sizeof(double);
+        c->tabc = b.take<double>((size_t)TAB_TOTAL * c->nc);
+        c->fc = b.take<double>(Ngc);
+        c->fc32 = b.take<float>(Ngc);
+        c->fwsc = b.take<char>(std::max((size_t)FINE_NVEC * Ngc * kesz2, (size_t)FINE_NVEC * Ngc * sizeof(double)));
+        c->ustc = b.take<double>((size_t)2 * Ngc);
+        c->fpartc = b.take<double>((size_t)8 * c->max_ctas_c);
+        c->fbarc = b.take<unsigned>(2);
+        c->xc = b.take<double>(Ngc);
+        c->yc = b.take<double>(Ngc);
+        c->trajc = b.take<double>((size_t)(N + 1) * Ngc);
+    }
     c->beta = b.take<double>((size_t)N * c->mcap0);
     c->gout = b.take<double>((size_t)N * c->maxK * c->maxK);
     c->lam = b.take<double>((size_t)N * c->maxK);
@@ -256,6 +285,11 @@ pr_status init_ws(pr_ctx* c) {
     int cn[8] = {c->ns, c->ns0, 0, 1, 0, 0, 0, 0};
     PR_CUDA(cudaMemcpy(c->cnst, cn, sizeof(cn), cudaMemcpyHostToDevice));
     PR_CUDA(launch_flow_tables(c->flow, c->n, c->L, c->tab, st));
+    if (c->o.method == PR_METHOD_PARAREAL_II) {
+        PR_CUDA(launch_flow_tables(c->flow, c->nc, c->L, c->tabc, st));
+        PR_CUDA(cudaMemsetAsync(c->fc, 0, sizeof(double) * c->Ngc, st));
+        PR_CUDA(cudaMemsetAsync(c->fc32, 0, sizeof(float) * c->Ngc, st));
+    }
     if (c->tdep) PR_CUDA(launch_g_fields(c->tab, c->n, c->gq, c->gq + c->Ng, st));
     if (!c->ev_ready) {
         for (auto& e : c->ev) PR_CUDA(cudaEventCreate(&e));
@@ -493,6 +527,55 @@ pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int
     return PR_OK;
 }
 
+// Parareal-II: implicit Euler with step dT on the grid coarsened by 2, one item, from
+// x_in at time t0 for `steps` steps (with or without the forcing), snapshots every dM.
+pr_status run_coarse_grid(pr_ctx* c, const double* x_in, double* y_out, double* snap, int steps, int n_snap,
+                          int dM, double t0, bool with_forcing) {
+    FineArgs a{};
+    a.g.n = c->nc;
+    a.g.Ng = c->Ngc;
+    a.g.h = c->L / c->nc;
+    a.g.eps = c->eps;
+    a.g.tab = c->tabc;
+    a.njobs = 1;
+    FineJob& J = a.jobs[0];
+    J.tab = c->tabc;
+    J.tdep = c->tdep ? 1 : 0;
+    J.rk4 = 0;
+    J.no_forcing = with_forcing ? 0 : 1;
+    J.kind = c->flow.kind;
+    J.w = c->flow.w;
+    J.t0 = t0;
+    J.DeltaT = 0.0;
+    J.eps = c->eps;
+    J.dt = c->dT;
+    J.S = steps;
+    J.dM = dM;
+    J.n_snap = snap ? n_snap : 0;
+    J.f = (with_forcing && c->has_f) ? c->fc : nullptr;
+    J.f32 = (with_forcing && c->has_f) ? c->fc32 : nullptr;
+    J.u_in = x_in;
+    J.u_out = y_out;
+    J.snap = snap;
+    J.tol = c->lin_tol;
+    J.maxit = c->o.lin_maxit;
+    J.status = c->fstatus + c->N;
+    J.its_total = c->fits + c->N;
+    J.its_max = c->fitsmax + c->N;
+    J.B = 1;
+    a.B = 1;
+    a.ws = c->fwsc;
+    a.ust = c->ustc;
+    a.part = c->fpartc;
+    a.bar = c->fbarc;
+    a.G = 0;
+    a.spin_limit = c->o.spin_limit;
+    a.err = c->derr;
+    PR_CUDA(cudaMemsetAsync(c->fbarc, 0, sizeof(unsigned) * 2, c->st));
+    PR_CUDA(launch_fine(a, c->fp32, c->o.ctas_per_sm, 1, c->st));
+    return PR_OK;
+}
+
 pr_status read_device_errors(pr_ctx* c) {
     int e = 0;
     PR_CUDA(cudaMemcpyAsync(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -575,7 +658,9 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (opts) o = *opts; else pr_opts_init(&o);
     if (o.m_l < 0 || o.m_l > 1 || o.p < 0 || o.p > 1) return PR_ERR_UNSUPPORTED;
     if (o.precision != PR_FP64 && o.precision != PR_FP32) return PR_ERR_INVALID_ARG;
-    if (o.method != PR_METHOD_ADAPTIVE && o.method != PR_METHOD_PARAREAL_I) return PR_ERR_INVALID_ARG;
+    if (o.method != PR_METHOD_ADAPTIVE && o.method != PR_METHOD_PARAREAL_I && o.method != PR_METHOD_PARAREAL_II)
+        return PR_ERR_INVALID_ARG;
+    if (o.method == PR_METHOD_PARAREAL_II && (grid->n % 2 != 0 || grid->n / 2 < 4)) return PR_ERR_UNSUPPORTED;
     if (o.fine != PR_FINE_IMPLICIT_EULER && o.fine != PR_FINE_RK4) return PR_ERR_INVALID_ARG;
     if (o.lin_maxit <= 0) o.lin_maxit = 200;
     if (o.spin_limit < 0) o.spin_limit = 1LL << 22;
@@ -635,6 +720,11 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (c->maxK > 96) {
         delete c;
         return PR_ERR_UNSUPPORTED;  // Gram eigenproblems up to 96 x 96 (one CTA each)
+    }
+    if (o.method == PR_METHOD_PARAREAL_II) {
+        c->nc = c->n / 2;
+        c->Ngc = (long long)c->nc * c->nc * c->nc;
+        c->max_ctas_c = std::max(fine_max_ctas(c->nc, c->fp32, o.ctas_per_sm), fine_max_ctas(c->nc, false, o.ctas_per_sm));
     }
     c->max_ctas = fine_max_ctas(c->n, c->fp32, o.ctas_per_sm);
     c->max_ctas = std::max(c->max_ctas, fine_max_ctas(c->n, false, o.ctas_per_sm));
@@ -706,6 +796,10 @@ pr_status pr_set_initial(pr_ctx* c, const double* u0, const double* f) {
     if (f) PR_CUDA(cudaMemcpyAsync(c->f, f, sizeof(double) * c->Ng, cudaMemcpyHostToDevice, c->st));
     else PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, c->st));
     PR_CUDA(launch_to_float(c->f, c->f32, c->Ng, c->st));
+    if (c->o.method == PR_METHOD_PARAREAL_II) {   // the forcing at the coarse points
+        PR_CUDA(launch_restrict_diff(c->f, nullptr, c->n, 2, c->fc, c->st));
+        PR_CUDA(launch_to_float(c->fc, c->fc32, c->Ngc, c->st));
+    }
     PR_CUDA(cudaStreamSynchronize(c->st));
     c->has_f = f != nullptr;
     c->initial_set = true;
@@ -721,6 +815,21 @@ pr_status pr_iteration0(pr_ctx* c) {
     const long long Ng = c->Ng;
     double* U = c->Ubuf[0];
     c->cur = 0;
+    if (c->o.method == PR_METHOD_PARAREAL_II) {
+        // u_hat0 = F(0, T0, u0); the coarse trajectory x_{n+1} = G_c(x_n) from x_0 = R u_hat0
+        // (R P = I), U^0_n = P x_n
+        s = run_fine(c, c->u0, U, nullptr, 1, c->S0, 0, 0, false, 0.0, 0.0);
+        if (s != PR_OK) return s;
+        PR_CUDA(launch_restrict_diff(U, nullptr, c->n, 2, c->xc, c->st));
+        s = run_coarse_grid(c, c->xc, c->yc, c->trajc, c->N * c->Lc, c->N + 1, c->Lc, c->T0, true);
+        if (s != PR_OK) return s;
+        PR_CUDA(launch_prolong_add(c->trajc + c->Ngc, c->Ngc, c->n, 2, nullptr, 0, U + Ng, Ng, c->N, c->st));
+        c->r1cur = 0;
+        c->k_done = 0;
+        c->phase = 0;
+        c->checked = true;
+        return PR_OK;
+    }
     // fine propagator on [0, T0] with snapshots (slot 0 of the snapshot store)
     s = run_fine(c, c->u0, U, c->snap, 1, c->S0, c->ns0, 0, false, 0.0, 0.0);
     if (s != PR_OK) return s;
@@ -811,7 +920,7 @@ pr_status pr_fine_sweep(pr_ctx* c, int k) {
     const long long Ng = c->Ng;
     const int B = c->N - k + 1;
     const double* Uprev = c->Ubuf[c->cur];
-    const bool plain = c->o.method == PR_METHOD_PARAREAL_I;   // no snapshots needed
+    const bool plain = c->o.method != PR_METHOD_ADAPTIVE;   // no snapshots needed
     pr_status s = run_fine(c, Uprev + (size_t)(k - 1) * Ng, c->Fend + (size_t)(k - 1) * Ng,
                            plain ? nullptr : c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S,
                            c->ns, k - 1, false, c->T0 + (k - 1) * c->DeltaT, c->DeltaT);
@@ -858,7 +967,7 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         J.dt = c->dt;
         J.S = c->S;
         J.dM = c->dM;
-        const bool plain = c->o.method == PR_METHOD_PARAREAL_I;
+        const bool plain = c->o.method != PR_METHOD_ADAPTIVE;
         J.n_snap = plain ? 0 : c->ns;
         J.f = c->has_f ? c->f : nullptr;
         J.f32 = c->has_f ? c->f32 : nullptr;
@@ -946,7 +1055,7 @@ pr_status pr_tune_fine(pr_ctx* c, int steps, int* best_group_ctas, double* best_
 pr_status pr_pod_update(pr_ctx* c, int k) {
     if (!c) return PR_ERR_INVALID_ARG;
     if (c->k_done != k - 1 || c->phase != 1) return fail(c, PR_ERR_STATE, "pr_pod_update out of order");
-    if (c->o.method == PR_METHOD_PARAREAL_I) {   // the coarse space stays V0
+    if (c->o.method != PR_METHOD_ADAPTIVE) {   // plain parareal: no POD bases
         c->phase = 2;
         return PR_OK;
     }
@@ -1045,6 +1154,22 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
     PR_CUDA(cudaMemcpyAsync(Unew, Uold, sizeof(double) * (size_t)k * Ng, cudaMemcpyDeviceToDevice, c->st));
     PR_CUDA(cudaMemcpyAsync(Unew + (size_t)k * Ng, c->Fend + (size_t)(k - 1) * Ng, sizeof(double) * Ng,
                             cudaMemcpyDeviceToDevice, c->st));
+    if (c->o.method == PR_METHOD_PARAREAL_II) {
+        // U^k_{n+1} = F_n + P Phi_c R (U^k_n - U^{k-1}_n): G is affine, so the forcing
+        // cancels and the coarse propagation of the difference is homogeneous
+        for (int n = k; n < c->N; ++n) {
+            PR_CUDA(launch_restrict_diff(Unew + (size_t)n * Ng, Uold + (size_t)n * Ng, c->n, 2, c->xc, c->st));
+            pr_status s = run_coarse_grid(c, c->xc, c->yc, nullptr, c->Lc, 0, 1, c->T0 + n * c->DeltaT, false);
+            if (s != PR_OK) return s;
+            PR_CUDA(launch_prolong_add(c->yc, 0, c->n, 2, c->Fend + (size_t)n * Ng, 0, Unew + (size_t)(n + 1) * Ng,
+                                       0, 1, c->st));
+        }
+        c->cur = 1 - c->cur;
+        c->k_done = k;
+        c->phase = 0;
+        c->checked = false;
+        return PR_OK;
+    }
     CoarseSweepArgs a = coarse_args(c);
     a.n0 = k;
     a.count = c->N - k;
@@ -1307,7 +1432,7 @@ pr_status pr_rewind(pr_ctx* c) {
     if (c->k_done < 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "no completed iteration to undo");
     PR_CUDA(cudaStreamSynchronize(c->st));
     c->cur = 1 - c->cur;
-    if (c->o.method != PR_METHOD_PARAREAL_I) c->r1cur = 1 - c->r1cur;
+    if (c->o.method == PR_METHOD_ADAPTIVE) c->r1cur = 1 - c->r1cur;
     c->k_done -= 1;
     c->phase = 0;
     return PR_OK;

@@ -95,6 +95,62 @@ cudaError_t launch_flow_tables(const pr_flow& flow, int n, double L, double* tab
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// Grid transfers of the Parareal-II comparator (restriction by injection, trilinear
+// prolongation on the periodic grid).
+__global__ void restrict_diff_kernel(const double* U, const double* Up, int n, int c, double* out_c) {
+    const int nc = n / c;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nc3 = (long long)nc * nc * nc;
+    if (i >= nc3) return;
+    const int x = (int)(i % nc), y = (int)((i / nc) % nc), z = (int)(i / ((long long)nc * nc));
+    const long long f = ((long long)z * c * n + (long long)y * c) * n + (long long)x * c;
+    out_c[i] = Up ? U[f] - Up[f] : U[f];
+}
+
+__global__ void prolong_add_kernel(const double* xc, long long sxc, int n, int c, const double* F, long long sF,
+                                   double* out, long long sout) {
+    const int nc = n / c;
+    const int b = blockIdx.y;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n3 = (long long)n * n * n;
+    if (i >= n3) return;
+    const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+    const double* X = xc + (size_t)b * sxc;
+    // the coarse cell and the offsets inside it along each axis
+    const int x0 = x / c, y0 = y / c, z0 = z / c;
+    const int x1 = (x0 + 1) % nc, y1 = (y0 + 1) % nc, z1 = (z0 + 1) % nc;
+    const double wx = (double)(x - x0 * c) / c, wy = (double)(y - y0 * c) / c, wz = (double)(z - z0 * c) / c;
+    auto at = [&](int zz, int yy, int xx) { return X[((long long)zz * nc + yy) * nc + xx]; };
+    // tensor-product (trilinear) interpolation: along x, then y, then z
+    const double a00 = (1.0 - wx) * at(z0, y0, x0) + wx * at(z0, y0, x1);
+    const double a01 = (1.0 - wx) * at(z0, y1, x0) + wx * at(z0, y1, x1);
+    const double a10 = (1.0 - wx) * at(z1, y0, x0) + wx * at(z1, y0, x1);
+    const double a11 = (1.0 - wx) * at(z1, y1, x0) + wx * at(z1, y1, x1);
+    const double b0 = (1.0 - wy) * a00 + wy * a01;
+    const double b1 = (1.0 - wy) * a10 + wy * a11;
+    const double v = (1.0 - wz) * b0 + wz * b1;
+    out[(size_t)b * sout + i] = (F ? F[(size_t)b * sF + i] : 0.0) + v;
+}
+
+cudaError_t launch_restrict_diff(const double* U, const double* Up, int n, int c, double* out_c,
+                                 cudaStream_t st) {
+    const long long nc3 = (long long)(n / c) * (n / c) * (n / c);
+    restrict_diff_kernel<<<(unsigned)((nc3 + 255) / 256), 256, 0, st>>>(U, Up, n, c, out_c);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(const double* xc, long long sxc, int n, int c, const double* F, long long sF,
+                               double* out, long long sout, int B, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    const long long n3 = (long long)n * n * n;
+    prolong_add_kernel<<<dim3((unsigned)((n3 + 255) / 256), (unsigned)B), 256, 0, st>>>(xc, sxc, n, c, F, sF, out,
+                                                                                       sout);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
 // g^q(x, y, z) = GX_q[x] + GY_q[y] + GZ_q[z] as grid functions (the forcing pieces of a
 // time-dependent flow, for their projections onto V0).
 __global__ void g_fields_kernel(const double* tab, int n, double* g0, double* g1) {

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             tabk[i] = (KT)(v * dt * 0.5 / h);
         }
         for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-            const double v = q0 * Gt[i] + q1 * Gt[3 * n + i];
+            const double v = J.no_forcing ? 0.0 : q0 * Gt[i] + q1 * Gt[3 * n + i];
             ftd[i] = v;
             ftk[i] = (KT)v;
         }

@@ -62,6 +62,13 @@ __device__ inline void flow_coeffs(int kind, double w, double t, double& c0, dou
 }
 // All TAB_TOTAL * n table entries of a flow (see above).
 cudaError_t launch_flow_tables(const pr_flow& flow, int n, double L, double* tab, cudaStream_t st);
+// Parareal-II transfers between the grid of n^3 points and the one coarsened by c:
+// out_c = R (U - Up) by injection (Up may be nullptr), and out = F + P x_c by trilinear
+// interpolation on the periodic grid (F may be nullptr); B items, item strides sF, sC.
+cudaError_t launch_restrict_diff(const double* U, const double* Up, int n, int c, double* out_c,
+                                 cudaStream_t st);
+cudaError_t launch_prolong_add(const double* xc, long long sxc, int n, int c, const double* F, long long sF,
+                               double* out, long long sout, int B, cudaStream_t st);
 // The forcing pieces g^0, g^1 of a table buffer as grid functions.
 cudaError_t launch_g_fields(const double* tab, int n, double* g0, double* g1, cudaStream_t st);
 
@@ -161,6 +168,7 @@ struct FineJob {
                         // buffer [b^0 | b^1 | g^0, g^1 | 0] (TAB_TOTAL x n)
     int tdep;           // time-dependent flow: tables rebuilt at every step
     int rk4;            // explicit classical RK4 instead of implicit Euler + BiCGStab
+    int no_forcing;     // homogeneous propagation: the flow's forcing pieces are left out
     int kind;           // pr_flow_kind (time coefficients)
     double w;
     double t0, DeltaT;  // item lb of the job starts at t0 + lb DeltaT

@@ -65,3 +65,53 @@ def test_parareal_I_finite_termination_with_a_long_window(gpu):
         assert rel(Us[-1][n], ref[n]) < TOL64, n
     assert rel(Us[0][w.n_sub], ref[w.n_sub]) > 1e-6
     s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Parareal-II: the coarse propagator is implicit Euler on the grid coarsened by 2.
+@pytest.mark.parametrize("wl,prec", [("tiny", 0), ("tiny_forced", 0), ("tiny", 1),
+                                     ("paper_abc", 0)])
+def test_parareal_II_iterates(gpu, wl, prec):
+    bd, torch = gpu
+    if wl == "paper_abc":
+        w = pi.tiny(n=8, n_sub=4, T=0.4, dt=0.01, flow=pi.Flow("paper_abc", w=1.3), f_seed=3)
+    else:
+        w = WORKLOADS[wl]()
+    prm = O.derive_params(w, method="parareal_II")
+    K = 3
+    if prec == 0:
+        hist, env = oracle_envelope(w, prm, K, 1e-13)
+        base = TOL64
+    else:
+        hist, env = oracle_envelope(w, prm, K, 1e-8, where="fine")
+        base = TOL32
+    s = bd.Parareal.from_workload(w, precision=prec, method=bd.PR_METHOD_PARAREAL_II)
+    s.set_initial(w.u0(), w.f())
+    s.iteration0()
+    Us = [s.interfaces()]
+    for k in range(1, K + 1):
+        s.iterate(k)
+        Us.append(s.interfaces())
+    worst = 0.0
+    for k in range(K + 1):
+        for n in range(w.n_sub + 1):
+            e = rel(Us[k][n], hist["U"][k][n])
+            tol = max(base, 10 * env[k][n])
+            worst = max(worst, e / tol)
+            assert e < tol, (k, n, e, env[k][n])
+    # finite termination on the sequential fine solution
+    ref = O.sequential_fine(w, prm)
+    for k in range(K + 1, w.n_sub + 1):
+        s.iterate(k)
+    U = s.interfaces()
+    for n in range(w.n_sub + 1):
+        assert rel(U[n], ref[n]) < base, n
+    s.close()
+    print(f"parareal_II {wl} prec {prec}: worst error / tolerance {worst:.3f}")
+
+
+def test_parareal_II_needs_an_even_grid(gpu):
+    bd, torch = gpu
+    w = pi.tiny(n=9, n_sub=2)
+    with pytest.raises(bd.PRError):
+        bd.Parareal.from_workload(w, method=bd.PR_METHOD_PARAREAL_II)
