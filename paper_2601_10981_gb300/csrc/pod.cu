@@ -315,7 +315,11 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
         if (threadIdx.x == 0) {
             double st = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) st += red[w];
-            s_stop = (offsum <= 1e-32 * st) || st == 0.0;
+            // converged when the off-diagonal part is at the rounding level of the Gram
+            // matrix itself, ||off||_F <= K eps ||A||_F: a tighter bound sits below the
+            // noise of the rotations (fused multiply-adds) and would never be met
+            const double tolK = (double)K * 2.220446049250313e-16;
+            s_stop = (offsum <= tolK * tolK * st) || st == 0.0;
         }
         __syncthreads();
         if (s_stop) break;
