@@ -22,6 +22,9 @@
 // factor of two (Sterbenz), so r keeps FP32 accuracy relative to the differences.
 // Snapshots are written in FP64 in both modes: the POD criterion keeps modes down to
 // lambda/lambda_1 ~ 1e-12, which FP32-rounded snapshots cannot resolve.
+// The FP32 mode starts BiCGStab from the previous step's increment (linear extrapolation
+// in time; r = dt (f - L (u_{j-1} + delta_{j-1})) - delta_{j-1}), which halves the
+// iterations per step at its 1e-9 tolerance; the FP64 mode starts from 0.
 // Stopping rule: ||r|| <= tol ||u_{j-1} + dt f||.
 //
 // BiCGStab phases (van der Vorst 1992), each followed by a group barrier:
@@ -244,6 +247,13 @@ __device__ __forceinline__ double df_value_bits(float hi, float lo) { return f2d
 template <int W> struct HiLo { Vec<float, W> hi, lo; };
 template <typename T> struct is_hilo : std::false_type {};
 template <int W> struct is_hilo<HiLo<W>> : std::true_type {};
+// The FP32-mode implicit setup ring: the stencil operand op (one float) and the state
+// u = hi + lo, in three planes.
+template <int W> struct OpHiLo { Vec<float, W> op, hi, lo; };
+template <typename T> struct is_ophilo : std::false_type {};
+template <int W> struct is_ophilo<OpHiLo<W>> : std::true_type {};
+// Owned-point inputs of the FP32-mode implicit setup: forcing and the initial increment.
+template <typename KT, int W> struct OwnFD { Vec<KT, W> f, d; };
 
 // Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
 template <typename ST, typename KT, int W> struct RawSetup { Vec<ST, W> u; Vec<KT, W> d; };
@@ -463,6 +473,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                     if constexpr (is_hilo<std::decay_t<decltype(val)>>::value) {
                         vstore(dst, val.hi);
                         vstore(dst + ring_lo, val.lo);
+                    } else if constexpr (is_ophilo<std::decay_t<decltype(val)>>::value) {
+                        vstore(dst, val.op);
+                        vstore(dst + ring_lo, val.hi);
+                        vstore(dst + 2 * ring_lo, val.lo);
                     } else {
                         vstore(dst, val);
                     }
@@ -770,6 +784,9 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
             const double* P = (j <= 2) ? u_in : ust + (size_t)((j - 2) & 1) * Ng;
             double* Wt = (j >= 2) ? ust + (size_t)((j - 1) & 1) * Ng : nullptr;
             const bool use_d = (j >= 2) && dvalid;
+            // FP32 mode: BiCGStab starts from the previous increment (the FP64 mode starts
+            // from 0, i.e. from u_{j-1}, like the plain definition)
+            const bool xg = DF && use_d;
             double* snap_j = nullptr;
             if (snap_b && (j - 1) % dM == 0 && (j - 1) / dM < n_snap)
                 snap_j = snap_b + (size_t)((j - 1) / dM) * Ng;
@@ -835,9 +852,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 float2* Wf = reinterpret_cast<float2*>(Wt);
                 const float* ff = J.f32;
                 const KT dtf = (KT)dt;
-                // residual from the hi parts (exact neighbour differences, Sterbenz); the
-                // neglected dt L(lo) is ~1e-7 of dt L(u), at the level of the solver
-                // tolerance; lo enters the state update and the snapshots
+                // residual from a one-float operand (exact neighbour differences, Sterbenz);
+                // the neglected dt L of its rounding is ~1e-7 of dt L(u), at the level of
+                // the solver tolerance; lo enters the state update and the snapshots.
+                // Initial guess: the previous increment (xg), i.e. the operand
+                // u_{j-1} + delta and r = dt (f - L (u_{j-1} + delta)) - delta; else 0.
                 float* ringh = reinterpret_cast<float*>(ring_raw);
                 march(true, ringh,
                       [&](int i) -> RawSetup<float2, KT, W> {
@@ -855,30 +874,38 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return o;
                       },
-                      [&](const RawSetup<float2, KT, W>& v) -> HiLo<W> {
-                          HiLo<W> o;
+                      [&](const RawSetup<float2, KT, W>& v) -> OpHiLo<W> {
+                          OpHiLo<W> o;
 #pragma unroll
                           for (int e = 0; e < W; ++e) {
                               const float2 u = df_add(v.u.v[e], v.d.v[e]);
                               o.hi.v[e] = u.x;
                               o.lo.v[e] = u.y;
+                              // u.x + (u.y + d): within ulp(op) / 2 of u_{j-1} + delta
+                              o.op.v[e] = xg ? u.x + (u.y + v.d.v[e]) : u.x;
                           }
                           return o;
                       },
-                      [&](int i) -> VK {
-                          VK fo;
-                          if (ff) fo = vload<KT, W>(ff + i);
+                      [&](int i) -> OwnFD<KT, W> {
+                          OwnFD<KT, W> o;
+                          if (ff) o.f = vload<KT, W>(ff + i);
                           else {
 #pragma unroll
-                              for (int e = 0; e < W; ++e) fo.v[e] = (KT)0;
+                              for (int e = 0; e < W; ++e) o.f.v[e] = (KT)0;
                           }
-                          return fo;
+                          if (xg) o.d = vload<KT, W>(delta + i);
+                          else {
+#pragma unroll
+                              for (int e = 0; e < W; ++e) o.d.v[e] = (KT)0;
+                          }
+                          return o;
                       },
-                      [&](int i, int k, int yy, const VK& fv0, const float* rowc, const float* rowzp,
+                      [&](int i, int k, int yy, const OwnFD<KT, W>& ow, const float* rowc, const float* rowzp,
                           const float* rowzm) {
                           const auto q = nb7(rowc, rowzp, rowzm);
-                          const VK clo = vload<float, W>(rowc + ring_lo + x0);
-                          VK fv = fv0;
+                          const VK chi = vload<float, W>(rowc + ring_lo + x0);
+                          const VK clo = vload<float, W>(rowc + 2 * ring_lo + x0);
+                          VK fv = ow.f;
                           if (tdep) {
                               const KT fyz = ftk[n + yy] + ftk[2 * n + i / n2];
 #pragma unroll
@@ -898,10 +925,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               const KT sy = __fsub_rn(__fsub_rn(q.yp.v[e], c), __fsub_rn(c, q.ym.v[e]));
                               const KT sz = __fsub_rn(__fsub_rn(q.zp.v[e], c), __fsub_rn(c, q.zm.v[e]));
                               const KT lap = (sx + sy) + sz;
-                              // r = dt (f - L u): dt b.grad(u) = a . (2h grad u), dt eps lap / h^2 = c1 lap
-                              const KT rk = dtf * fv.v[e] - (ax * dx + ay * dy + az * dz) + c1 * lap;
+                              // r = dt (f - L op) - delta: dt b.grad(op) = a . (2h grad op),
+                              // dt eps lap / h^2 = c1 lap
+                              const KT rk = (dtf * fv.v[e] - (ax * dx + ay * dy + az * dz) + c1 * lap) - ow.d.v[e];
                               rv.v[e] = rk;
-                              const KT bi = c + dtf * fv.v[e];
+                              const KT bi = chi.v[e] + dtf * fv.v[e];
                               acc.f[0] += rk * rk;
                               acc.f[1] += bi * bi;
                           }
@@ -910,13 +938,13 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           if (Wf) {
                               Vec<float2, W> u2;
 #pragma unroll
-                              for (int e = 0; e < W; ++e) u2.v[e] = make_float2(q.c.v[e], clo.v[e]);
+                              for (int e = 0; e < W; ++e) u2.v[e] = make_float2(chi.v[e], clo.v[e]);
                               vstore(Wf + i, u2);
                           }
                           if (snap_j) {
                               VD sd;
 #pragma unroll
-                              for (int e = 0; e < W; ++e) sd.v[e] = df_value_bits(q.c.v[e], clo.v[e]);
+                              for (int e = 0; e < W; ++e) sd.v[e] = df_value_bits(chi.v[e], clo.v[e]);
                               vstore(snap_j + i, sd);
                           }
                           acc.tick();
@@ -1061,7 +1089,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 // ---------------- ph3: delta += alpha p + omega s ; r = s - omega t
                 {
                     const KT al = (KT)sh.alpha, om = (KT)sh.omega;
-                    const bool first = (it == 1);
+                    const bool first = (it == 1) && !xg;   // delta holds the initial guess
                     const bool upd_r = !half && sh.status == 0;
                     Acc<KT, 2> acc;
                     acc.init();
@@ -1138,7 +1166,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                 }
                 if (sh.flag) break;
             }
-            dvalid = it > 0;
+            dvalid = it > 0 || xg;
             its_total += it;
             its_max = max(its_max, it);
             // a non-finite state would only propagate: skip the remaining steps
@@ -1210,7 +1238,8 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
 // ------------------------------------------------------------------------------------
 // Launch geometry.  W = 4 points per thread when n % 4 == 0, else 1.  A row has n/W
 // lanes; RP rows per pass of the CTA is the largest divisor of n with RP * n/W <= 256;
-// a tile has TY = KS * RP rows (KS in {1, 2}), its FINE_SLOTS-plane 8-byte ring within 64 KB.
+// a tile has TY = KS * RP rows (KS in {1, 2}), its FINE_SLOTS-plane ring (8 bytes a point)
+// within 64 KB.
 struct FineGeom {
     int W, lanes, RP, TY, KS, KF, threads;
     size_t smem;
@@ -1230,7 +1259,9 @@ inline FineGeom fine_geom(int n, bool fp32) {
     g.KF = (g.TY + 2 + g.RP - 1) / g.RP;
     g.threads = (g.lanes * g.RP + 31) / 32 * 32;   // whole warps (full-mask shuffles)
     const size_t tabs = ((size_t)9 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 31) / 32 * 32;
-    g.smem = tabs + (size_t)FINE_SLOTS * (g.TY + 2) * n * sizeof(double);
+    // ring: 8 bytes a point (FP64 value, or the float pair of the FP32 mode's RK4 stages),
+    // 12 in the FP32 mode's implicit setup (operand, hi, lo)
+    g.smem = tabs + (size_t)FINE_SLOTS * (g.TY + 2) * n * (fp32 ? 12 : 8);
     return g;
 }
 
