@@ -366,6 +366,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     ga.G = c->gout;
     ga.ldG = maxK;
     ga.ldG_b = (long long)maxK * maxK;
+    ga.df = c->fp32;   // FP32 mode: double-float Grams and projections on the FP32 pipe
     PR_CUDA(launch_gram(ga, in_f32, in_f32, st));
     // eigenpairs + dimension + C = Y_m Lambda_m^{-1/2}
     EigArgs ea{};
@@ -400,6 +401,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     ta.B = B;
     ta.maxKIN = maxK;
     ta.maxKOUT = mmax;
+    ta.df = c->fp32;
     PR_CUDA(launch_tsmm(ta, in_f32, f32, st));
     // one Cholesky QR pass (reading R7): scr[0] -> dest
     pr_status s = cols_contig(c, c->scr[0], (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB, c->esz);
@@ -458,6 +460,7 @@ pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B
     ga.G = Mo;
     ga.ldG = mmax;
     ga.ldG_b = (long long)mmax * mmax;
+    ga.df = c->fp32;
     PR_CUDA(launch_gram(ga, f32, f32, c->st));
     const Grid g = grid_of(c);
     Grid pieces[3] = {g, g, g};

@@ -192,55 +192,59 @@ cudaError_t launch_to_float(const double* in, float* out, long long n, cudaStrea
 // ------------------------------------------------------------------------------------
 // out = L u or L^T u on whole grid functions.  Every supported velocity has b_d
 // independent of x_d, so b_d(x +- e_d) = b_d(x) and L^T only flips the advection sign.
+// One thread per point runs over all columns of its batch item: the neighbour offsets and
+// the velocity terms are formed once (32-bit index arithmetic, no FP64 division), each
+// column costs its seven loads and a dozen FP64 operations.
 template <typename TI, typename TO>
-__global__ void apply_L_kernel(Grid g, const void* const* in_cols, void* const* out_cols,
-                               const int* count, int ldcols, bool transpose) {
-    const int b = blockIdx.z, c = blockIdx.y;
-    if (c >= count[b]) return;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.Ng) return;
-    const TI* in = (const TI*)in_cols[(size_t)b * ldcols + c];
-    TO* out = (TO*)out_cols[(size_t)b * ldcols + c];
-    const int n = g.n;
-    const long long n2 = (long long)n * n;
-    const int x = (int)(i % n);
-    const int y = (int)((i / n) % n);
-    const int z = (int)(i / n2);
-    const long long base = i - x;
-    const long long ixp = base + (x + 1 == n ? 0 : x + 1), ixm = base + (x == 0 ? n - 1 : x - 1);
-    const long long rowb = i - (long long)y * n;
-    const long long iyp = rowb + (long long)(y + 1 == n ? 0 : y + 1) * n;
-    const long long iym = rowb + (long long)(y == 0 ? n - 1 : y - 1) * n;
-    const long long plb = i - (long long)z * n2;
-    const long long izp = plb + (long long)(z + 1 == n ? 0 : z + 1) * n2;
-    const long long izm = plb + (long long)(z == 0 ? n - 1 : z - 1) * n2;
+__global__ void __launch_bounds__(256) apply_L_kernel(Grid g, const void* const* in_cols, void* const* out_cols,
+                                                      const int* count, int ldcols, bool transpose,
+                                                      double inv2h, double epsh2) {
+    const int b = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int)g.Ng) return;
+    const int n = g.n, n2 = n * n;
+    const int z = i / n2;
+    const int rem = i - z * n2;
+    const int y = rem / n;
+    const int x = rem - y * n;
+    const int ixp = i + (x + 1 == n ? 1 - n : 1), ixm = i + (x == 0 ? n - 1 : -1);
+    const int iyp = i + (y + 1 == n ? n - n2 : n), iym = i + (y == 0 ? n2 - n : -n);
+    const int izp = i + (z + 1 == n ? n2 - (int)g.Ng : n2), izm = i + (z == 0 ? (int)g.Ng - n2 : -n2);
     const double* tab = g.tab;
-    const double bx = tab[TXY * n + y] + tab[TXZ * n + z];
-    const double by = tab[TYX * n + x] + tab[TYZ * n + z];
-    const double bz = tab[TZX * n + x] + tab[TZY * n + y];
-    const double u0 = (double)in[i];
-    const double uxp = (double)in[ixp], uxm = (double)in[ixm];
-    const double uyp = (double)in[iyp], uym = (double)in[iym];
-    const double uzp = (double)in[izp], uzm = (double)in[izm];
-    double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
-    if (transpose) adv = -adv;
-    const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * u0;
-    out[i] = (TO)(adv * (0.5 / g.h) - g.eps * lap / (g.h * g.h));
+    const double sg = transpose ? -inv2h : inv2h;
+    const double ax = sg * (tab[TXY * n + y] + tab[TXZ * n + z]);
+    const double ay = sg * (tab[TYX * n + x] + tab[TYZ * n + z]);
+    const double az = sg * (tab[TZX * n + x] + tab[TZY * n + y]);
+    const int cnt = count[b];
+    for (int c = 0; c < cnt; ++c) {
+        const TI* in = (const TI*)in_cols[(size_t)b * ldcols + c];
+        TO* out = (TO*)out_cols[(size_t)b * ldcols + c];
+        const double u0 = (double)in[i];
+        const double uxp = (double)in[ixp], uxm = (double)in[ixm];
+        const double uyp = (double)in[iyp], uym = (double)in[iym];
+        const double uzp = (double)in[izp], uzm = (double)in[izm];
+        const double adv = ax * (uxp - uxm) + ay * (uyp - uym) + az * (uzp - uzm);
+        const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * u0;
+        out[i] = (TO)(adv - epsh2 * lap);
+    }
 }
 
 cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols, void* const* out_cols,
                            const int* count, int ldcols, int max_count, int B, bool in_f32,
                            bool out_f32, bool transpose, cudaStream_t st) {
     if (max_count <= 0 || B <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((g.Ng + 255) / 256), (unsigned)max_count, (unsigned)B);
+    if (g.Ng > (1LL << 30)) return cudaErrorInvalidValue;   // 32-bit point indices
+    dim3 grid((unsigned)((g.Ng + 255) / 256), (unsigned)B);
+    const double inv2h = 0.5 / g.h, epsh2 = g.eps / (g.h * g.h);
     if (in_f32 && out_f32)
-        apply_L_kernel<float, float><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose);
+        apply_L_kernel<float, float><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose, inv2h, epsh2);
     else if (in_f32)
-        apply_L_kernel<float, double><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose);
+        apply_L_kernel<float, double><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose, inv2h, epsh2);
     else if (out_f32)
-        apply_L_kernel<double, float><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose);
+        apply_L_kernel<double, float><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose, inv2h, epsh2);
     else
-        apply_L_kernel<double, double><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose);
+        apply_L_kernel<double, double><<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, transpose, inv2h,
+                                                             epsh2);
     ++g_launch_count;
     return cudaGetLastError();
 }

@@ -37,6 +37,7 @@
 // The persistent fine-sweep kernel (implicit Euler with BiCGStab per step, or explicit
 // RK4), shared by the translation units that instantiate it for each Krylov type.
 #pragma once
+#include "df.cuh"
 #include "pr_internal.cuh"
 
 #include <algorithm>
@@ -229,17 +230,8 @@ __device__ __forceinline__ float2 df_add(float2 u, float d) {
     return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
 }
 
-// float -> double by moving bits (exact; float denormals, |x| < 1.2e-38, read as zero):
-// keeps the FP64 pipe out of the snapshot conversion but for one addition.
-__device__ __forceinline__ double f2d_bits(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xffu;
-    const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
-    const unsigned long long ed = (e == 255u) ? 2047ull : (unsigned long long)(e + (1023u - 127u));
-    const unsigned long long m = (unsigned long long)(b & 0x7fffffu) << 29;
-    return __longlong_as_double(e == 0u ? sgn : (sgn | (ed << 52) | m));
-}
-__device__ __forceinline__ double df_value_bits(float hi, float lo) { return f2d_bits(hi) + f2d_bits(lo); }
+// snapshot value of the float-pair state: bits moved, one FP64 addition
+__device__ __forceinline__ double df_value_bits(float hi, float lo) { return df_to_double(hi, lo); }
 
 // Operand of the FP32-mode setup march: the float pair of the state, stored in the ring
 // as two float planes (hi, then lo at a fixed offset), so that the stencil reads the hi

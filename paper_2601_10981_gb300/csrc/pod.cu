@@ -5,6 +5,7 @@
 //   CholQR2 re-orthonormalisation   -> gram + chol_inv_kernel + tsmm, twice
 // The Gram and projection stream every snapshot once per use; the small dense steps stay
 // in FP64 because their stability needs it (Gram-based POD squares the conditioning).
+#include "df.cuh"
 #include "pr_internal.cuh"
 
 #include <algorithm>
@@ -42,6 +43,33 @@ __device__ __forceinline__ void out_index(int o, int KA, int KB, bool sym, int& 
     while (rem >= len) { rem -= len; ++row; --len; }
     i = row;
     j = row + rem;
+}
+
+// The last CTA of batch item b to finish adds the chunk partials in chunk order (a fixed
+// order: the result does not depend on scheduling) and writes G (both triangles if sym).
+__device__ void gram_finish(const GramArgs& a, int b, int chunks, int KA, int KB, int nout) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atom_add_acq_rel_u32(a.counter + b, 1u);
+        s_last = (ticket == (unsigned)chunks - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const size_t outsz = (size_t)a.maxKA * a.maxKB;
+    const double* bpart = a.part + (size_t)b * chunks * outsz;
+    double* Gb = a.G + (size_t)b * a.ldG_b;
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        int i, j;
+        out_index(o, KA, KB, a.sym, i, j);
+        double s = 0.0;
+        for (int cc = 0; cc < chunks; ++cc) s += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
+        Gb[(size_t)i * a.ldG + j] = s;
+        if (a.sym) Gb[(size_t)j * a.ldG + i] = s;
+    }
+    if (threadIdx.x == 0) st_relaxed_u32(a.counter + b, 0u);
 }
 
 template <typename TA, typename TB, typename TACC, int MAXO>
@@ -112,30 +140,209 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_kernel(GramArgs a, long lon
             mypart[(size_t)oi[k] * a.maxKB + oj[k]] = v;
         }
     }
-    // last CTA of this batch item reduces the chunk partials in chunk order
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atom_add_acq_rel_u32(a.counter + b, 1u);
-        s_last = (ticket == (unsigned)chunks - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const double* bpart = a.part + (size_t)b * chunks * outsz;
-    double* Gb = a.G + (size_t)b * a.ldG_b;
-    for (int o = threadIdx.x; o < nout; o += GRAM_THREADS) {
-        int i, j;
-        out_index(o, KA, KB, a.sym, i, j);
-        double s = 0.0;
-        for (int cc = 0; cc < chunks; ++cc) s += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
-        Gb[(size_t)i * a.ldG + j] = s;
-        if (a.sym) Gb[(size_t)j * a.ldG + i] = s;
-    }
-    if (threadIdx.x == 0) st_relaxed_u32(a.counter + b, 0u);
+    gram_finish(a, b, chunks, KA, KB, nout);
 }
 
+
+// ------------------------------------------------------------------------------------
+// Gram of FP64 columns in double-float arithmetic (FP32 mode).  The FP64 Gram of the
+// snapshots runs at the FP64 rate (1/64 of FP32 on GB300); here each staged value is
+// split into a float pair (d2df_bits) and every product-sum is an error-free df_mac2 on
+// the FP32 pipe, two rows per packed instruction.  Row partials fold into a df
+// accumulator about every 64 rows, so the chunk sums keep ~1e-15 relative accuracy (the
+// POD needs the Gram to ~1e-13 of its norm).
+//   load      cp.async of the next block of GDF_SUB rows of every column (raw FP64)
+//             while the current block is reduced
+//   convert   raw -> column-major float planes hi, lo (quads of four rows XOR-swizzled by
+//             column so that the 16-byte reads of neighbouring tiles hit different banks)
+//   compute   one thread per 2 x 2 output tile and row group: the CTA has ntiles x P
+//             threads, group g takes the row quads g, g + P, ...; the groups' FP64 sums
+//             meet in shared memory at the end of the chunk.
+constexpr int GDF_SUB = 64;              // rows per staged block (16 quads)
+constexpr int GDF_LDP = GDF_SUB + 4;     // floats per staged column plane
+constexpr int GDF_MAXTHR = 384;
+
+__device__ __forceinline__ int gdf_pos(int col, int r) {
+    return col * GDF_LDP + ((((r >> 2) ^ ((col >> 3) & 1)) << 2) | (r & 3));
+}
+__host__ __device__ __forceinline__ int gdf_cols(int K) { return (K + 1) & ~1; }
+__host__ __device__ __forceinline__ int gdf_tiles(int KA, int KB, bool sym) {
+    const int nbA = (KA + 1) / 2, nbB = (KB + 1) / 2;
+    return sym ? nbA * (nbA + 1) / 2 : nbA * nbB;
+}
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 fills zeros without reading
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long long CH, int chunks) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int b = blockIdx.y, c = blockIdx.x;
+    const int KA = a.KA[b];
+    const int KB = a.sym ? KA : a.KB[b];
+    const int nout = a.sym ? KA * (KA + 1) / 2 : KA * KB;
+    const long long p_lo = (long long)c * CH;
+    const long long p_hi = min(a.Ng, p_lo + CH);
+    const int ncA = gdf_cols(a.maxKA), ncB = a.sym ? 0 : gdf_cols(a.maxKB);
+    const int plA = ncA * GDF_LDP, plB = ncB * GDF_LDP;
+    double* rawA = reinterpret_cast<double*>(smem_raw);             // [ncA][GDF_SUB]
+    double* rawB = rawA + (size_t)ncA * GDF_SUB;                     // [ncB][GDF_SUB]
+    float* sA = reinterpret_cast<float*>(rawB + (size_t)ncB * GDF_SUB);   // planes hi, lo
+    float* sB = a.sym ? sA : sA + 2 * plA;
+    const int plb = a.sym ? plA : plB;
+    const void* const* colsA = a.colsA + (size_t)b * a.ldcols;
+    const void* const* colsB = (a.sym ? a.colsA : a.colsB) + (size_t)b * a.ldcols;
+
+    const int nbA = (KA + 1) / 2, nbB = (KB + 1) / 2;
+    const int ntiles = gdf_tiles(KA, KB, a.sym);
+    const int P = ntiles > 0 ? max(1, nthr / ntiles) : 1;
+    const int grp = ntiles > 0 ? tid / ntiles : P;
+    const bool active = grp < P;
+    int ti = 0, tj = 0;
+    if (active) {
+        int bi, bj;
+        out_index(tid - grp * ntiles, nbA, nbB, a.sym, bi, bj);
+        ti = 2 * bi;
+        tj = 2 * bj;
+    }
+    f2p sh[2][2], sl[2][2], Ah[2][2], Al[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) sh[r][q] = sl[r][q] = Ah[r][q] = Al[r][q] = 0ull;
+    auto load = [&](double* raw, int ncols, int K, const void* const* cols, long long p0) {
+        for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
+            const int col = e / GDF_SUB, r = e - col * GDF_SUB;
+            const long long p = p0 + r;
+            const bool ok = col < K && p < p_hi;
+            const double* src = ok ? reinterpret_cast<const double*>(cols[col]) + p : reinterpret_cast<const double*>(a.part);
+            cp_async8(raw + e, src, ok ? 8 : 0);
+        }
+    };
+    auto convert = [&](const double* raw, float* dst, int pl, int ncols) {
+        for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
+            const int col = e / GDF_SUB, r = e - col * GDF_SUB;
+            const float2 v = d2df_bits(raw[e]);
+            const int o = gdf_pos(col, r);
+            dst[o] = v.x;
+            dst[pl + o] = v.y;
+        }
+    };
+    auto quad = [&](const float* pln, int col, int q) {
+        return *reinterpret_cast<const ulonglong2*>(pln + col * GDF_LDP + ((q ^ ((col >> 3) & 1)) << 2));
+    };
+    load(rawA, ncA, KA, colsA, p_lo);
+    if (!a.sym) load(rawB, ncB, KB, colsB, p_lo);
+    cp_async_commit();
+    int nblk = 0;
+    for (long long p0 = p_lo; p0 < p_hi; p0 += GDF_SUB) {
+        cp_async_wait_all();
+        __syncthreads();   // this block's rows landed; every thread is done with the planes
+        convert(rawA, sA, plA, ncA);
+        if (!a.sym) convert(rawB, sB, plB, ncB);
+        __syncthreads();   // planes ready, raw buffers free
+        if (p0 + GDF_SUB < p_hi) {
+            load(rawA, ncA, KA, colsA, p0 + GDF_SUB);
+            if (!a.sym) load(rawB, ncB, KB, colsB, p0 + GDF_SUB);
+        }
+        cp_async_commit();
+        if (active) {
+#pragma unroll 1
+            for (int q = grp; q < GDF_SUB / 4; q += P) {
+                ulonglong2 bh[2], bl[2];
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    bh[s2] = quad(sB, tj + s2, q);
+                    bl[s2] = quad(sB + plb, tj + s2, q);
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const ulonglong2 ah = quad(sA, ti + r, q), al = quad(sA + plA, ti + r, q);
+                    const f2p nx = neg2(ah.x), ny = neg2(ah.y);
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        df_mac2(sh[r][s2], sl[r][s2], ah.x, nx, al.x, bh[s2].x, bl[s2].x);
+                        df_mac2(sh[r][s2], sl[r][s2], ah.y, ny, al.y, bh[s2].y, bl[s2].y);
+                    }
+                }
+            }
+        }
+        if (++nblk == P) {   // ~64 rows a thread since the last fold
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    df_add2(Ah[r][s2], Al[r][s2], sh[r][s2], sl[r][s2]);
+                    sh[r][s2] = sl[r][s2] = 0ull;
+                }
+            nblk = 0;
+        }
+    }
+    cp_async_wait_all();   // the last (empty) group
+    double acc[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            df_add2(Ah[r][s2], Al[r][s2], sh[r][s2], sl[r][s2]);
+            const float2 h = upk2(Ah[r][s2]), l = upk2(Al[r][s2]);
+            acc[r][s2] = df_to_double(h.x, l.x) + df_to_double(h.y, l.y);   // even + odd rows
+        }
+    // groups > 0 hand their sums to group 0 through shared memory
+    double* sacc = reinterpret_cast<double*>(smem_raw);
+    if (P > 1) {
+        __syncthreads();
+        if (active && grp > 0) {
+            double* d = sacc + ((size_t)(grp - 1) * ntiles + (tid - grp * ntiles)) * 4;
+            d[0] = acc[0][0];
+            d[1] = acc[0][1];
+            d[2] = acc[1][0];
+            d[3] = acc[1][1];
+        }
+        __syncthreads();
+        if (active && grp == 0) {
+            for (int gg = 1; gg < P; ++gg) {
+                const double* d = sacc + ((size_t)(gg - 1) * ntiles + tid) * 4;
+                acc[0][0] += d[0];
+                acc[0][1] += d[1];
+                acc[1][0] += d[2];
+                acc[1][1] += d[3];
+            }
+        }
+    }
+    const size_t outsz = (size_t)a.maxKA * a.maxKB;
+    double* mypart = a.part + ((size_t)b * chunks + c) * outsz;
+    if (active && grp == 0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int i = ti + r, j = tj + s2;
+                if (i < KA && j < KB && (!a.sym || i <= j)) mypart[(size_t)i * a.maxKB + j] = acc[r][s2];
+            }
+    }
+    gram_finish(a, b, chunks, KA, KB, nout);
+}
+
+// Threads of gram_df_kernel: every tile of the largest batch item once, times the row
+// groups that fit in 256 threads; 0 when the df kernel does not apply.
+static int gram_df_threads(const GramArgs& a) {
+    const int tiles = gdf_tiles(a.maxKA, a.maxKB, a.sym);
+    if (tiles <= 0 || tiles > GDF_MAXTHR) return 0;
+    const int P = std::max(1, 256 / tiles);
+    return (tiles * P + 31) / 32 * 32;
+}
+// Shared memory of gram_df_kernel: raw blocks and float planes, at least the group sums.
+static size_t gram_df_smem(const GramArgs& a, int threads) {
+    const size_t cols = (size_t)gdf_cols(a.maxKA) + (a.sym ? 0 : gdf_cols(a.maxKB));
+    const size_t stage = cols * GDF_SUB * sizeof(double) + cols * 2 * GDF_LDP * sizeof(float);
+    const size_t sums = (size_t)threads * 4 * sizeof(double);
+    return std::max(stage, sums);
+}
 template <typename TA, typename TB, typename TACC>
 static cudaError_t gram_dispatch(const GramArgs& a, cudaStream_t st) {
     const int chunks = gram_chunks(a.Ng);
@@ -162,6 +369,20 @@ static cudaError_t gram_dispatch(const GramArgs& a, cudaStream_t st) {
 
 cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t st) {
     if (a.B <= 0 || a.maxKA <= 0 || (!a.sym && a.maxKB <= 0)) return cudaSuccess;
+    if (a.df && !a_f32 && !b_f32) {
+        const int thr = gram_df_threads(a);
+        const size_t smem = thr > 0 ? gram_df_smem(a, thr) : 0;
+        if (thr > 0 && smem <= 160 * 1024) {
+            const int chunks = gram_chunks(a.Ng);
+            const long long CH = gram_chunk_len(a.Ng);
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute((const void*)gram_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            gram_df_kernel<<<dim3(chunks, a.B), thr, smem, st>>>(a, CH, chunks);
+            ++g_launch_count;
+            return cudaGetLastError();
+        }
+    }
     // FP32 accumulation only when both operands are FP32.
     if (a_f32 && (b_f32 || a.sym)) return gram_dispatch<float, float, float>(a, st);
     if (a_f32) return gram_dispatch<float, double, double>(a, st);
@@ -224,11 +445,77 @@ __global__ void __launch_bounds__(256) tsmm_kernel(TsmmArgs a) {
     }
 }
 
+// Out_b = In_b C_b with FP64 input and output in double-float arithmetic (FP32 mode):
+// one thread per point, blocks of J <= 16 outputs.  C sits in shared memory as float-pair
+// planes hi, lo (rows padded to a multiple of 4, read as warp-wide broadcasts); each input
+// is split once per block (d2df_bits) and broadcast into both lanes of a packed pair, so
+// one df_mac2 serves two outputs.  Four inputs are loaded ahead (memory-level parallelism).
+template <int J>
+__device__ __forceinline__ void tsmm_df_block(const void* const* cols, int KIN, const float* sC, int pl, int KP,
+                                              int j0, int jn, long long p, long long Ng, double* out) {
+    constexpr int H = J / 2;
+    f2p sh[H], sl[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) sh[h] = sl[h] = 0ull;
+#pragma unroll 4
+    for (int i = 0; i < KIN; ++i) {
+        const float2 x = d2df_bits(reinterpret_cast<const double*>(cols[i])[p]);
+        const f2p xh = pk2(x.x, x.x), nxh = pk2(-x.x, -x.x), xl = pk2(x.y, x.y);
+        const float* row = sC + (size_t)i * KP + j0;
+#pragma unroll
+        for (int h4 = 0; h4 < J / 4; ++h4) {
+            const ulonglong2 ch = *reinterpret_cast<const ulonglong2*>(row + 4 * h4);
+            const ulonglong2 cl = *reinterpret_cast<const ulonglong2*>(row + pl + 4 * h4);
+            df_mac2(sh[2 * h4], sl[2 * h4], xh, nxh, xl, ch.x, cl.x);
+            df_mac2(sh[2 * h4 + 1], sl[2 * h4 + 1], xh, nxh, xl, ch.y, cl.y);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const float2 vh = upk2(sh[h]), vl = upk2(sl[h]);
+        if (2 * h < jn) out[(size_t)(j0 + 2 * h) * Ng + p] = df_to_double(vh.x, vl.x);
+        if (2 * h + 1 < jn) out[(size_t)(j0 + 2 * h + 1) * Ng + p] = df_to_double(vh.y, vl.y);
+    }
+}
+
+__global__ void __launch_bounds__(256) tsmm_df_kernel(TsmmArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sC = reinterpret_cast<float*>(smem_raw);
+    const int b = blockIdx.y;
+    const int KIN = a.KIN[b], KOUT = a.KOUT[b];
+    if (KOUT <= 0) return;
+    const int KP = (KOUT + 3) / 4 * 4;
+    const int pl = a.maxKIN * ((a.maxKOUT + 3) / 4 * 4);   // floats per plane
+    const double* Cb = a.C + (size_t)b * a.ldC_b;
+    for (int e = threadIdx.x; e < KIN * KP; e += blockDim.x) {
+        const int i = e / KP, j = e - i * KP;
+        const float2 v = (j < KOUT) ? d2df_bits(Cb[(size_t)i * a.ldC + j]) : make_float2(0.0f, 0.0f);
+        sC[e] = v.x;
+        sC[pl + e] = v.y;
+    }
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.Ng) return;
+    const void* const* cols = a.colsIn + (size_t)b * a.ldcols;
+    double* out = reinterpret_cast<double*>(a.out) + (size_t)b * a.ld_out_b;
+    for (int j0 = 0; j0 < KOUT; j0 += 16) {
+        const int jn = min(16, KOUT - j0);
+        switch ((jn + 3) / 4) {
+        case 1: tsmm_df_block<4>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
+        case 2: tsmm_df_block<8>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
+        case 3: tsmm_df_block<12>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
+        default: tsmm_df_block<16>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
+        }
+    }
+}
+
 cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream_t st) {
     if (a.B <= 0 || a.maxKOUT <= 0) return cudaSuccess;
     dim3 grid((unsigned)((a.Ng + 255) / 256), a.B);
     const size_t cells = (size_t)a.maxKIN * ((a.maxKOUT + 3) / 4 * 4);
-    if (in_f32 && out_f32) {
+    if (a.df && !in_f32 && !out_f32) {
+        tsmm_df_kernel<<<grid, 256, 2 * cells * sizeof(float), st>>>(a);
+    } else if (in_f32 && out_f32) {
         tsmm_kernel<float, float, float><<<grid, 256, cells * sizeof(float), st>>>(a);
     } else if (!in_f32 && out_f32) {
         // FP64 input (snapshots): accumulate in FP64 and round only the output, the

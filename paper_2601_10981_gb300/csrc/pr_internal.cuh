@@ -252,6 +252,7 @@ struct GramArgs {
     int ldG;                  // row stride
     long long ldG_b;          // batch stride
     double scaleB;            // unused (1.0)
+    bool df;                  // FP64 operands in double-float arithmetic (FP32 mode)
 };
 int gram_chunks(long long Ng);
 size_t gram_part_doubles(long long Ng, int B, int maxKA, int maxKB);
@@ -272,6 +273,7 @@ struct TsmmArgs {
     long long Ng;
     int B;
     int maxKIN, maxKOUT;
+    bool df;                   // FP64 in and out, double-float arithmetic (FP32 mode)
 };
 cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream_t st);
 

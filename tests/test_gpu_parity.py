@@ -170,7 +170,9 @@ def test_pod_mode_matches_oracle(gpu, precision, w_f32):
     wdt = np.float32 if w_f32 else np.float64
     Wt = np.stack([W.T for W in Ws]).astype(wdt).reshape(3, 13, n, n, n)
     tau = 1e-6 if w_f32 else 1e-13
-    eps_in = 6e-8 if w_f32 else 1.1e-16
+    # input rounding: FP32 snapshots, or FP64 ones reduced in double-float arithmetic (48
+    # significant bits) by the FP32 mode, or FP64
+    eps_in = 6e-8 if w_f32 else (3.6e-15 if precision == 1 else 1.1e-16)
     for gamma in (0.99, 0.999999):
         R, m = s.op_pod(dev(torch, Wt), gamma, cap=0)
         R = R.cpu().numpy().reshape(3, -1, w.Ng).astype(np.float64)
