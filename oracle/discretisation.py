@@ -53,7 +53,19 @@ def velocity(flow, grid: Grid, t: float = 0.0):
     const: constant (b0, b1, b2), used by the Fourier-symbol check.
     paper_kolmogorov: (cos y, cos z, cos x) + (sin z, sin x, sin y) cos t, eq. (koleq).
     paper_abc: ABC with all arguments shifted by sin(w t), Sec. 4.2.
+    A steady kind with flow.pert_seed > 0 carries the seeded divergence-free perturbation
+    b' of the input recipe on top (a stored 3 x n^3 field).
     """
+    base = _analytic_velocity(flow, grid, t)
+    pert = flow.pert(grid.n) if getattr(flow, "pert_seed", 0) > 0 else None
+    if pert is None:
+        return base
+    if time_dependent(flow):
+        raise ValueError("the velocity perturbation applies to steady flows only")
+    return tuple(b + p for b, p in zip(base, pert))
+
+
+def _analytic_velocity(flow, grid: Grid, t: float):
     X, Y, Z = grid.coords()
     one = np.ones((grid.n,) * 3)
     kind = flow.kind

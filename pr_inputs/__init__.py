@@ -4,7 +4,8 @@ This module builds the inputs that both the CUDA library and the CPU oracle rece
 
 * the workload recipes (grid size, velocity field, viscosity, horizon, number of time
   subintervals, fine step, snapshot count, POD rank cap), and
-* the seeded fields: the initial state ``u0`` and the forcing ``f``.
+* the seeded fields: the initial state ``u0``, the forcing ``f`` and the optional
+  divergence-free velocity perturbation ``b'``.
 
 It holds none of the method's arithmetic (no operator, no time stepping, no POD); it
 only draws random numbers and evaluates finite Fourier sums on the periodic grid.
@@ -104,6 +105,29 @@ def forcing(n: int, seed: int, L: float = TWO_PI) -> np.ndarray:
     return fourier_field(n, 4, seed, 0.1, L)
 
 
+def perturbation(n: int, seed: int, amp: float = 0.05, L: float = TWO_PI) -> np.ndarray:
+    """Seeded velocity perturbation b' = curl_h Psi, shape (3, n, n, n) = (b'_x, b'_y, b'_z).
+
+    Psi = (Psi_x, Psi_y, Psi_z) are three seeded fields with |k| <= 4 (seeds 3*seed,
+    3*seed + 1, 3*seed + 2), and curl_h takes central differences (f_{i+1} - f_{i-1})/(2h).
+    Central differences along different axes commute, so the central-difference
+    divergence of b' vanishes (up to rounding): the field is discretely divergence-free
+    for the advection stencil.  b' is scaled so that max_{d, i} |b'_d(x_i)| = amp.
+    This is part of the field's definition, not of the method.
+    """
+    h = L / n
+    psi = [fourier_field(n, 4, 3 * seed + c, 1.0, L) for c in range(3)]
+
+    def d(f, axis):   # axis: 2 = x, 1 = y, 0 = z of a [z][y][x] array
+        return (np.roll(f, -1, axis=axis) - np.roll(f, 1, axis=axis)) / (2.0 * h)
+
+    bx = d(psi[2], 1) - d(psi[1], 0)
+    by = d(psi[0], 0) - d(psi[2], 2)
+    bz = d(psi[1], 2) - d(psi[0], 1)
+    b = np.stack([bx, by, bz])
+    return b * (amp / np.max(np.abs(b)))
+
+
 @dataclasses.dataclass(frozen=True)
 class Flow:
     """Velocity field b(x, t) of the advection term.
@@ -113,6 +137,8 @@ class Flow:
           'const' b = (b0, b1, b2)
           'paper_kolmogorov'  b = (cos y, cos z, cos x) + (sin z, sin x, sin y) cos t
           'paper_abc'  ABC with every argument shifted by sin(w t)
+    pert_seed > 0 adds the steady divergence-free perturbation
+    perturbation(n, pert_seed, pert_amp) to a steady kind.
     """
     kind: str = "abc"
     A: float = 1.0
@@ -123,6 +149,12 @@ class Flow:
     b0: float = 0.0
     b1: float = 0.0
     b2: float = 0.0
+    pert_seed: int = 0
+    pert_amp: float = 0.05
+
+    def pert(self, n: int) -> Optional[np.ndarray]:
+        """The perturbation on an n^3 grid, or None."""
+        return perturbation(n, self.pert_seed, self.pert_amp) if self.pert_seed > 0 else None
 
 
 @dataclasses.dataclass(frozen=True)
