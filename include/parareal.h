@@ -70,6 +70,12 @@ typedef struct pr_flow {
     int k;                  /* Kolmogorov wave number                                   */
     double b[3];            /* constant velocity                                        */
     double w;               /* time frequency of PR_FLOW_PAPER_ABC                       */
+    const double* pert;     /* optional stored velocity perturbation added to a steady
+                               kind: host array [3][n^3] (b'_x, b'_y, b'_z, each [z][y][x],
+                               x fastest), copied by pr_create, caller keeps ownership;
+                               NULL: none.  Time-dependent kinds and PR_FINE_RK4 with a
+                               perturbation return PR_ERR_UNSUPPORTED.  The advection
+                               stencil reads it per point (no skew-symmetry is assumed).  */
 } pr_flow;
 
 /* Options; pr_opts_init fills the defaults.  Values marked "0: derive" are computed from

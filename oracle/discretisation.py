@@ -44,7 +44,7 @@ class Grid:
         return s[None, None, :], s[None, :, None], s[:, None, None]
 
 
-def velocity(flow, grid: Grid, t: float = 0.0):
+def velocity(flow, grid: Grid, t: float = 0.0, pert: Optional[np.ndarray] = None):
     """The three components (b_x, b_y, b_z) of the advection field at time t.
 
     abc:  (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x); the paper's ABC flow
@@ -54,10 +54,12 @@ def velocity(flow, grid: Grid, t: float = 0.0):
     paper_kolmogorov: (cos y, cos z, cos x) + (sin z, sin x, sin y) cos t, eq. (koleq).
     paper_abc: ABC with all arguments shifted by sin(w t), Sec. 4.2.
     A steady kind with flow.pert_seed > 0 carries the seeded divergence-free perturbation
-    b' of the input recipe on top (a stored 3 x n^3 field).
+    b' of the input recipe on top (a stored 3 x n^3 field); `pert` overrides it with a
+    given stored field (the injected one on a coarser grid).
     """
     base = _analytic_velocity(flow, grid, t)
-    pert = flow.pert(grid.n) if getattr(flow, "pert_seed", 0) > 0 else None
+    if pert is None and getattr(flow, "pert_seed", 0) > 0:
+        pert = flow.pert(grid.n)
     if pert is None:
         return base
     if time_dependent(flow):
@@ -147,14 +149,26 @@ def assemble_L_dense(grid: Grid, vel, eps: float) -> np.ndarray:
 
 @dataclasses.dataclass
 class Operator:
-    """The problem data the propagators need: grid, flow, eps, forcing f(x) (or None)."""
+    """The problem data the propagators need: grid, flow, eps, forcing f(x) (or None) and
+    an explicit stored velocity perturbation (None: the flow's own, if any)."""
     grid: Grid
     flow: object
     eps: float
     f: Optional[np.ndarray] = None
+    pert: Optional[np.ndarray] = None
+
+    def __post_init__(self):
+        # the stored field is built once, not at every operator application
+        if self.pert is None and getattr(self.flow, "pert_seed", 0) > 0:
+            self.pert = self.flow.pert(self.grid.n)
 
     def vel(self, t: float):
-        return velocity(self.flow, self.grid, t)
+        return velocity(self.flow, self.grid, t, self.pert)
+
+    def stored_perturbation(self) -> Optional[np.ndarray]:
+        if self.pert is not None:
+            return self.pert
+        return self.flow.pert(self.grid.n) if getattr(self.flow, "pert_seed", 0) > 0 else None
 
     def L(self, u: np.ndarray, t: float) -> np.ndarray:
         return apply_L(u, self.vel(t), self.eps, self.grid.h)

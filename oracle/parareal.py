@@ -143,9 +143,12 @@ def sequential_fine(w, prm: Params, op=None) -> List[np.ndarray]:
 
 def coarse_operator(op, c: int):
     """The problem on the grid coarsened by c (Parareal-II): same flow and eps, the
-    forcing at the coarse points."""
+    forcing and a stored velocity perturbation at the coarse points (injection, like the
+    states)."""
     f = None if op.f is None else restrict(op.f, c)
-    return Operator(Grid(op.grid.n // c, op.grid.L), op.flow, op.eps, f)
+    bp = op.stored_perturbation()
+    pc = None if bp is None else np.stack([restrict(b, c) for b in bp])
+    return Operator(Grid(op.grid.n // c, op.grid.L), op.flow, op.eps, f, pc)
 
 
 def iteration0(w, prm: Params, op):

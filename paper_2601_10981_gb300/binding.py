@@ -32,7 +32,8 @@ class pr_grid(C.Structure):
 
 class pr_flow(C.Structure):
     _fields_ = [("kind", C.c_int), ("A", C.c_double), ("B", C.c_double), ("C", C.c_double),
-                ("k", C.c_int), ("b", C.c_double * 3), ("w", C.c_double)]
+                ("k", C.c_int), ("b", C.c_double * 3), ("w", C.c_double),
+                ("pert", C.POINTER(C.c_double))]
 
 
 class pr_opts(C.Structure):
@@ -168,14 +169,26 @@ def opts(**kw) -> pr_opts:
     return o
 
 
-def flow_struct(kind: str, A=1.0, B=1.0, Cc=1.0, k=1, b=(0.0, 0.0, 0.0), w=1.0) -> pr_flow:
+def flow_struct(kind: str, A=1.0, B=1.0, Cc=1.0, k=1, b=(0.0, 0.0, 0.0), w=1.0, pert=None) -> pr_flow:
+    """pr_flow; pert: optional stored velocity perturbation, array (3, n, n, n) float64
+    (kept alive by the returned struct; pr_create copies it)."""
     f = pr_flow()
     f.kind = {"abc": PR_FLOW_ABC, "kolmogorov": PR_FLOW_KOLMOGOROV, "const": PR_FLOW_CONST,
               "paper_kolmogorov": PR_FLOW_PAPER_KOLMOGOROV, "paper_abc": PR_FLOW_PAPER_ABC}[kind]
     f.A, f.B, f.C, f.k = A, B, Cc, k
     f.b[0], f.b[1], f.b[2] = b
     f.w = w
+    if pert is not None:
+        arr = np.ascontiguousarray(pert, dtype=np.float64)
+        f._pert_keep = arr
+        f.pert = arr.ctypes.data_as(C.POINTER(C.c_double))
     return f
+
+
+def flow_of(fl, n: int) -> pr_flow:
+    """pr_flow of a pr_inputs.Flow on an n^3 grid (with its stored perturbation, if any)."""
+    pert = fl.pert(n) if getattr(fl, "pert_seed", 0) > 0 else None
+    return flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2), fl.w, pert)
 
 
 class Parareal:
@@ -217,7 +230,7 @@ class Parareal:
     @classmethod
     def from_workload(cls, w, precision: int = PR_FP64, **opt_kw):
         fl = w.flow
-        flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2), fl.w)
+        flow = flow_of(fl, w.n)
         o = opts(n_snap=w.n_snap, m_cap=w.m_cap, m_l=w.m_l, p=w.p, precision=precision, **opt_kw)
         obj = cls(w.n, flow, w.eps, w.T, w.n_sub, w.dt, w.pod_tol, o)
         return obj
@@ -425,7 +438,8 @@ class Server:
         fl = w.flow
         r = pr_request()
         r.grid = pr_grid(w.n, 0.0)
-        r.flow = flow_struct(fl.kind, fl.A, fl.B, fl.C, fl.k, (fl.b0, fl.b1, fl.b2), fl.w)
+        flow = flow_of(fl, w.n)   # alive through pr_server_submit, which copies the perturbation
+        r.flow = flow
         r.eps, r.T, r.n_sub, r.dt_fine, r.pod_tol = w.eps, w.T, w.n_sub, w.dt, w.pod_tol
         r.opts = opts(n_snap=w.n_snap, m_cap=w.m_cap, m_l=w.m_l, p=w.p, precision=precision, **opt_kw)
         u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)

@@ -62,6 +62,7 @@ struct pr_ctx {
     int max_ctas = 1;
     bool has_f = false;
     bool tdep = false;   // time-dependent flow of Sec. 4 (tables and Galerkin pieces per time)
+    std::vector<double> pert_host;   // stored velocity perturbation [3][Ng] (empty: none)
     // device
     cudaStream_t st = nullptr;
     bool own_ws = false;
@@ -92,6 +93,10 @@ struct pr_ctx {
     double* L0 = nullptr;
     double* p0 = nullptr;
     double* q0 = nullptr;
+    double* pert = nullptr;       // stored velocity perturbation [3][Ng], FP64
+    float* pert32 = nullptr;      // the same in float (FP32-mode Krylov operator)
+    double* pertc = nullptr;      // injected onto the Parareal-II coarse grid [3][Ngc]
+    float* pertc32 = nullptr;
     double* qg = nullptr;         // V0^T g^0, V0^T g^1 (time-dependent flows)
     double* gq = nullptr;         // g^0, g^1 as grid functions (time-dependent flows)
     double* cA1 = nullptr;        // coarse-sweep scratch A1 d~
@@ -205,6 +210,12 @@ size_t plan(pr_ctx* c, char* base) {
     c->q0 = b.take<double>(c->mcap0);
     c->qg = b.take<double>((size_t)2 * c->mcap0);
     c->gq = c->tdep ? b.take<double>((size_t)2 * Ng) : nullptr;
+    const bool pt = !c->pert_host.empty();
+    c->pert = pt ? b.take<double>((size_t)3 * Ng) : nullptr;
+    c->pert32 = pt && c->fp32 ? b.take<float>((size_t)3 * Ng) : nullptr;
+    const bool pt2 = pt && c->o.method == PR_METHOD_PARAREAL_II;
+    c->pertc = pt2 ? b.take<double>((size_t)3 * c->Ngc) : nullptr;
+    c->pertc32 = pt2 && c->fp32 ? b.take<float>((size_t)3 * c->Ngc) : nullptr;
     c->cA1 = b.take<double>(Ng);
     if (c->o.method == PR_METHOD_PARAREAL_II) {
         const long long Ngc = c->Ngc;
@@ -264,6 +275,7 @@ Grid grid_of(const pr_ctx* c) {
     g.h = c->h;
     g.eps = c->eps;
     g.tab = c->tab;
+    g.pert = c->pert;
     return g;
 }
 
@@ -291,6 +303,23 @@ pr_status init_ws(pr_ctx* c) {
         PR_CUDA(cudaMemsetAsync(c->fc32, 0, sizeof(float) * c->Ngc, st));
     }
     if (c->tdep) PR_CUDA(launch_g_fields(c->tab, c->n, c->gq, c->gq + c->Ng, st));
+    if (c->pert) {
+        PR_CUDA(cudaMemcpy(c->pert, c->pert_host.data(), sizeof(double) * 3 * c->Ng, cudaMemcpyHostToDevice));
+        if (c->pert32) PR_CUDA(launch_to_float(c->pert, c->pert32, 3 * c->Ng, st));
+        if (c->pertc) {
+            // injection onto the coarse grid (the restriction of the coarse propagator)
+            const int n = c->n, nc = c->nc;
+            std::vector<double> pc((size_t)3 * c->Ngc);
+            for (int d = 0; d < 3; ++d)
+                for (int z = 0; z < nc; ++z)
+                    for (int y = 0; y < nc; ++y)
+                        for (int x = 0; x < nc; ++x)
+                            pc[(size_t)d * c->Ngc + ((size_t)z * nc + y) * nc + x] =
+                                c->pert_host[(size_t)d * c->Ng + ((size_t)(2 * z) * n + 2 * y) * n + 2 * x];
+            PR_CUDA(cudaMemcpy(c->pertc, pc.data(), sizeof(double) * pc.size(), cudaMemcpyHostToDevice));
+            if (c->pertc32) PR_CUDA(launch_to_float(c->pertc, c->pertc32, 3 * c->Ngc, st));
+        }
+    }
     if (!c->ev_ready) {
         for (auto& e : c->ev) PR_CUDA(cudaEventCreate(&e));
         c->ev_ready = true;
@@ -516,6 +545,7 @@ pr_status run_fine(pr_ctx* c, const double* u_in, double* u_out, char* snap, int
     J.its_total = c->fits + stat_off;
     J.its_max = c->fitsmax + stat_off;
     J.B = B;
+    J.pert = c->pert ? (f32 ? (const void*)c->pert32 : (const void*)c->pert) : nullptr;
     a.B = B;
     a.ws = c->fws;
     a.ust = c->ust;
@@ -540,6 +570,7 @@ pr_status run_coarse_grid(pr_ctx* c, const double* x_in, double* y_out, double* 
     a.g.h = c->L / c->nc;
     a.g.eps = c->eps;
     a.g.tab = c->tabc;
+    a.g.pert = c->pertc;
     a.njobs = 1;
     FineJob& J = a.jobs[0];
     J.tab = c->tabc;
@@ -566,6 +597,7 @@ pr_status run_coarse_grid(pr_ctx* c, const double* x_in, double* y_out, double* 
     J.its_total = c->fits + c->N;
     J.its_max = c->fitsmax + c->N;
     J.B = 1;
+    J.pert = c->pertc ? (c->fp32 ? (const void*)c->pertc32 : (const void*)c->pertc) : nullptr;
     a.B = 1;
     a.ws = c->fwsc;
     a.ust = c->ustc;
@@ -674,7 +706,21 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     c->h = c->L / c->n;
     c->Ng = (long long)c->n * c->n * c->n;
     c->flow = *flow;
+    c->flow.pert = nullptr;   // the caller's array is copied below, never kept
     c->tdep = flow_time_dependent(flow->kind);
+    if (flow->pert) {
+        if (c->tdep || o.fine == PR_FINE_RK4) {
+            delete c;
+            return PR_ERR_UNSUPPORTED;   // the perturbation is a steady field of the implicit path
+        }
+        const size_t np = (size_t)3 * grid->n * grid->n * grid->n;
+        c->pert_host.assign(flow->pert, flow->pert + np);
+        for (double v : c->pert_host)
+            if (!std::isfinite(v)) {
+                delete c;
+                return PR_ERR_INVALID_ARG;
+            }
+    }
     c->eps = eps;
     c->T = T;
     c->N = n_sub;
@@ -946,8 +992,10 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return fail(c, PR_ERR_INVALID_ARG, "a context appears twice");
         if (owner && (c->n != owner->n || c->L != owner->L || c->fp32 != owner->fp32 ||
-                      c->o.fine != owner->o.fine))
-            return fail(c, PR_ERR_INVALID_ARG, "batched contexts need the same grid, precision and fine integrator");
+                      c->o.fine != owner->o.fine || (c->pert != nullptr) != (owner->pert != nullptr)))
+            return fail(c, PR_ERR_INVALID_ARG,
+                        "batched contexts need the same grid, precision, fine integrator and stencil kind "
+                        "(with or without a stored perturbation)");
         if (!owner || c->groups_max > owner->groups_max) owner = c;
     }
     FineArgs a{};
@@ -983,6 +1031,7 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         J.its_total = c->fits + (k - 1);
         J.its_max = c->fitsmax + (k - 1);
         J.B = c->N - k + 1;
+        J.pert = c->pert ? (c->fp32 ? (const void*)c->pert32 : (const void*)c->pert) : nullptr;
         a.B += J.B;
     }
     a.ws = owner->fws;
@@ -1577,7 +1626,11 @@ pr_status pr_op_apply_L_noalloc(pr_ctx* c, const double* d_in, double* d_out, in
         return fail(c, PR_ERR_INVALID_ARG, "pr_op_apply_L_noalloc: more than " +
                                                std::to_string(pr::noalloc_max_count()) +
                                                " grid functions in one call");
-    PR_CUDA(pr::apply_L_noalloc(c->n, c->L, c->flow, c->eps, d_in, d_out, count, transpose != 0, c->st));
+    if (!c->pert_host.empty() && !c->ws_ready)
+        return fail(c, PR_ERR_UNSUPPORTED,
+                    "pr_op_apply_L_noalloc: a stored velocity perturbation lives in the workspace "
+                    "(bind it and call pr_set_initial first)");
+    PR_CUDA(pr::apply_L_noalloc(c->n, c->L, c->flow, c->pert, c->eps, d_in, d_out, count, transpose != 0, c->st));
     PR_CUDA(cudaStreamSynchronize(c->st));
     return PR_OK;
 }

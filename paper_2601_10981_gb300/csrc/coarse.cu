@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             });
             buf ^= 1;
         }
-        // ---- D: L d~, L^T d~ (b_d does not depend on x_d, so L^T flips the advection) ;
+        // ---- D: L d~, L^T d~ (an analytic b_d does not depend on x_d, so L^T flips the
+        //         advection; a stored perturbation is read at the neighbours) ;
         //         R^T L d~, R^T L^T d~, d~.L d~.  Time-dependent flows: the pieces D d~,
         //         A0 d~, A1 d~ and their projections instead, combined per coarse step.
         if (a.tdep) {
@@ -599,11 +600,29 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
                 const double bx = tab[TXY * n_ + y] + tab[TXZ * n_ + z];
                 const double by = tab[TYX * n_ + x] + tab[TYZ * n_ + z];
                 const double bz = tab[TZX * n_ + x] + tab[TZY * n_ + y];
-                const double adv = (bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm)) * inv2h;
                 const double dif = epsh2 * ((uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * uc);
+                double adv, advt;   // (b . grad d)_i and the advection part of (L^T d)_i
+                if (!a.g.pert) {
+                    adv = (bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm)) * inv2h;
+                    advt = -adv;
+                } else {
+                    // a stored perturbation varies along every axis: column i of the
+                    // advection matrix holds +B_d(x_{i-e_d})/(2h) and -B_d(x_{i+e_d})/(2h)
+                    const double* P = a.g.pert;
+                    const long long ixp = base + (x + 1 == n_ ? 0 : x + 1), ixm = base + (x == 0 ? n_ - 1 : x - 1);
+                    const long long iyp = rowb + (long long)(y + 1 == n_ ? 0 : y + 1) * n_;
+                    const long long iym = rowb + (long long)(y == 0 ? n_ - 1 : y - 1) * n_;
+                    const long long izp = plb + (long long)(z + 1 == n_ ? 0 : z + 1) * n2;
+                    const long long izm = plb + (long long)(z == 0 ? n_ - 1 : z - 1) * n2;
+                    adv = ((bx + P[i]) * (uxp - uxm) + (by + P[Ng + i]) * (uyp - uym) +
+                           (bz + P[2 * Ng + i]) * (uzp - uzm)) * inv2h;
+                    advt = (((bx + P[ixm]) * uxm - (bx + P[ixp]) * uxp) +
+                            ((by + P[Ng + iym]) * uym - (by + P[Ng + iyp]) * uyp) +
+                            ((bz + P[2 * Ng + izm]) * uzm - (bz + P[2 * Ng + izp]) * uzp)) * inv2h;
+                }
                 const double Ld = adv - dif;
                 a.Ld[i] = Ld;
-                a.Ltd[i] = -adv - dif;
+                a.Ltd[i] = advt - dif;
                 v[0] += uc * Ld;
             }
             csw_block_sums(v, 1, sh, part() + (size_t)(2 * m) * G, G);

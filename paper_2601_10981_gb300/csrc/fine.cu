@@ -211,10 +211,29 @@ __global__ void __launch_bounds__(256) apply_L_kernel(Grid g, const void* const*
     const int iyp = i + (y + 1 == n ? n - n2 : n), iym = i + (y == 0 ? n2 - n : -n);
     const int izp = i + (z + 1 == n ? n2 - (int)g.Ng : n2), izm = i + (z == 0 ? (int)g.Ng - n2 : -n2);
     const double* tab = g.tab;
-    const double sg = transpose ? -inv2h : inv2h;
-    const double ax = sg * (tab[TXY * n + y] + tab[TXZ * n + z]);
-    const double ay = sg * (tab[TYX * n + x] + tab[TYZ * n + z]);
-    const double az = sg * (tab[TZX * n + x] + tab[TZY * n + y]);
+    const double bx = tab[TXY * n + y] + tab[TXZ * n + z];
+    const double by = tab[TYX * n + x] + tab[TYZ * n + z];
+    const double bz = tab[TZX * n + x] + tab[TZY * n + y];
+    // Row i of the advection part holds +-b_d(x_i)/(2h) at i +- e_d.  L^T: column i holds
+    // +b_d(x_{i-e_d})/(2h) at i - e_d and -b_d(x_{i+e_d})/(2h) at i + e_d; the analytic
+    // b_d does not vary along x_d, a stored perturbation does.
+    double cxp, cxm, cyp, cym, czp, czm;   // advection coefficients of u at the neighbours
+    if (!g.pert) {
+        const double sg = transpose ? -inv2h : inv2h;
+        cxp = sg * bx, cyp = sg * by, czp = sg * bz;
+        cxm = -cxp, cym = -cyp, czm = -czp;
+    } else if (!transpose) {
+        const long long N = g.Ng;
+        cxp = inv2h * (bx + g.pert[i]);
+        cyp = inv2h * (by + g.pert[N + i]);
+        czp = inv2h * (bz + g.pert[2 * N + i]);
+        cxm = -cxp, cym = -cyp, czm = -czp;
+    } else {
+        const long long N = g.Ng;
+        cxp = -inv2h * (bx + g.pert[ixp]), cxm = inv2h * (bx + g.pert[ixm]);
+        cyp = -inv2h * (by + g.pert[N + iyp]), cym = inv2h * (by + g.pert[N + iym]);
+        czp = -inv2h * (bz + g.pert[2 * N + izp]), czm = inv2h * (bz + g.pert[2 * N + izm]);
+    }
     const int cnt = count[b];
     for (int c = 0; c < cnt; ++c) {
         const TI* in = (const TI*)in_cols[(size_t)b * ldcols + c];
@@ -223,7 +242,11 @@ __global__ void __launch_bounds__(256) apply_L_kernel(Grid g, const void* const*
         const double uxp = (double)in[ixp], uxm = (double)in[ixm];
         const double uyp = (double)in[iyp], uym = (double)in[iym];
         const double uzp = (double)in[izp], uzm = (double)in[izm];
-        const double adv = ax * (uxp - uxm) + ay * (uyp - uym) + az * (uzp - uzm);
+        double adv;
+        if (!(transpose && g.pert))   // cd_m = -cd_p: differences first, exact for close values
+            adv = cxp * (uxp - uxm) + cyp * (uyp - uym) + czp * (uzp - uzm);
+        else
+            adv = (cxp * uxp + cxm * uxm) + (cyp * uyp + cym * uym) + (czp * uzp + czm * uzm);
         const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * u0;
         out[i] = (TO)(adv - epsh2 * lap);
     }
@@ -276,12 +299,17 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     const int n = a.g.n;
     if (n > 256 || n < 4) return cudaErrorInvalidValue;
     const bool rk = a.jobs[0].rk4 != 0;
+    const bool pt = a.jobs[0].pert != nullptr;
     bool td = false;
     for (int j = 0; j < a.njobs; ++j) {
         if ((a.jobs[j].rk4 != 0) != rk) return cudaErrorInvalidValue;   // one integrator per launch
+        if ((a.jobs[j].pert != nullptr) != pt) return cudaErrorInvalidValue;   // one stencil kind
         td = td || a.jobs[j].tdep != 0;
     }
-    const int mode = rk ? FINE_MODE_RK4 : (td ? FINE_MODE_IMPLICIT_TD : FINE_MODE_IMPLICIT);
+    // the perturbation is a steady field of the implicit propagator
+    if (pt && (rk || td)) return cudaErrorInvalidValue;
+    const int mode = rk ? FINE_MODE_RK4
+                        : (td ? FINE_MODE_IMPLICIT_TD : (pt ? FINE_MODE_IMPLICIT_PERT : FINE_MODE_IMPLICIT));
     FineFn fn = fine_select(n, fp32, mode);
     if (!fn) return cudaErrorInvalidValue;
     if (mode != FINE_MODE_IMPLICIT) {   // fine_max_ctas configured the steady instantiation

@@ -21,6 +21,7 @@ static FineFn pick_mode(int KF, int KS, int mode) {
         case FINE_MODE_IMPLICIT: return pick<W, FINE_MODE_IMPLICIT>(KF, KS);
         case FINE_MODE_IMPLICIT_TD: return pick<W, FINE_MODE_IMPLICIT_TD>(KF, KS);
         case FINE_MODE_RK4: return pick<W, FINE_MODE_RK4>(KF, KS);
+        case FINE_MODE_IMPLICIT_PERT: return fine_fn_pert(false, W, KF, KS);
     }
     return nullptr;
 }

@@ -46,7 +46,7 @@
 
 namespace pr {
 
-enum FineMode { FINE_MODE_IMPLICIT = 0, FINE_MODE_IMPLICIT_TD = 1, FINE_MODE_RK4 = 2 };
+enum FineMode { FINE_MODE_IMPLICIT = 0, FINE_MODE_IMPLICIT_TD = 1, FINE_MODE_RK4 = 2, FINE_MODE_IMPLICIT_PERT = 3 };
 
 // ------------------------------------------------------------------------------------
 // Fine sweep kernel.
@@ -245,7 +245,11 @@ template <int W> struct OpHiLo { Vec<float, W> op, hi, lo; };
 template <typename T> struct is_ophilo : std::false_type {};
 template <int W> struct is_ophilo<OpHiLo<W>> : std::true_type {};
 // Owned-point inputs of the FP32-mode implicit setup: forcing and the initial increment.
-template <typename KT, int W> struct OwnFD { Vec<KT, W> f, d; };
+// The stored velocity perturbation at W points (empty unless P).
+template <typename KT, int W, bool P> struct PertV { Vec<KT, W> x, y, z; };
+template <typename KT, int W> struct PertV<KT, W, false> {};
+template <typename KT, int W, bool P> struct OwnFD { Vec<KT, W> f, d; PertV<KT, W, P> b; };
+template <typename KT, int W, bool P> struct OwnH { Vec<KT, W> h; PertV<KT, W, P> b; };
 
 // Raw inputs of the stencil operand, loaded one plane ahead (software pipelining).
 template <typename ST, typename KT, int W> struct RawSetup { Vec<ST, W> u; Vec<KT, W> d; };
@@ -261,11 +265,14 @@ template <typename T, int W> struct Nb7 { Vec<T, W> c, xp, xm, yp, ym, zp, zm; }
 // KT: Krylov type.  W: points per thread along x.  KF: ring rows each thread fills per
 // plane (ceil((TY+2)/RP)).  KS: owned rows per thread per plane (TY/RP).
 // MODE: FINE_MODE_IMPLICIT (steady flow), FINE_MODE_IMPLICIT_TD (time-dependent flow:
-// tables rebuilt per step) or FINE_MODE_RK4 (explicit RK4, either flow).  Each mode is its
-// own instantiation, so that no path's register allocation burdens another.
+// tables rebuilt per step), FINE_MODE_RK4 (explicit RK4, either flow) or
+// FINE_MODE_IMPLICIT_PERT (steady flow plus a stored per-point velocity perturbation,
+// three more loads per point and stencil).  Each mode is its own instantiation, so that
+// no path's register allocation burdens another.
 template <typename KT, int W, int KF, int KS, int MODE>
 __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     constexpr bool RK = MODE == FINE_MODE_RK4;
+    constexpr bool PT = MODE == FINE_MODE_IMPLICIT_PERT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ FineShared sh;
 
@@ -310,6 +317,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     const double inv2h = 0.5 / h;
     double dt = 0.0, epsh2 = 0.0;
     KT c1 = (KT)0, c0 = (KT)1;
+    const KT* bpk = nullptr;   // stored velocity perturbation (FINE_MODE_IMPLICIT_PERT)
+    KT kp = (KT)0;             // its Krylov scale dt / (2h)
+    (void)bpk;
+    (void)kp;
 
     KT* Wk = reinterpret_cast<KT*>(a.ws) + (size_t)g * FINE_NVEC * Ng;
     KT* delta = Wk;
@@ -341,6 +352,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         }
         __syncthreads();
         dt = J.dt;
+        if constexpr (PT) {
+            bpk = reinterpret_cast<const KT*>(J.pert);
+            kp = (KT)(J.dt * 0.5 / h);
+        }
         epsh2 = J.eps / (h * h);
         c1 = (KT)(dt * J.eps / (h * h));
         c0 = (KT)(1.0 + 6.0 * dt * J.eps / (h * h));
@@ -554,16 +569,31 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         o.zm = vload<T, W>(rowzm + x0);
         return o;
     };
-    // A = I + dt L at the W points of row slot k
+    // The stored perturbation at the W points from index i (FINE_MODE_IMPLICIT_PERT).
+    auto load_pert = [&](int i) -> PertV<KT, W, PT> {
+        PertV<KT, W, PT> o;
+        if constexpr (PT) {
+            o.x = vload<KT, W>(bpk + i);
+            o.y = vload<KT, W>(bpk + Ng + i);
+            o.z = vload<KT, W>(bpk + 2 * Ng + i);
+        }
+        return o;
+    };
+    // A = I + dt L at the W points of row slot k (pb: the perturbation there)
     auto applyA = [&](int k, const Vec<KT, W>& c, const Vec<KT, W>& xp, const Vec<KT, W>& xm,
                       const Vec<KT, W>& yp, const Vec<KT, W>& ym, const Vec<KT, W>& zp,
-                      const Vec<KT, W>& zm) -> Vec<KT, W> {
-        const KT ax = kx_y[k] + kx_z;
+                      const Vec<KT, W>& zm, const PertV<KT, W, PT>& pb) -> Vec<KT, W> {
         Vec<KT, W> o;
 #pragma unroll
         for (int e = 0; e < W; ++e) {
-            const KT ay = ky_x[e] + ky_z;
-            const KT az = kz_x[e] + kz_y[k];
+            KT ax = kx_y[k] + kx_z;
+            KT ay = ky_x[e] + ky_z;
+            KT az = kz_x[e] + kz_y[k];
+            if constexpr (PT) {
+                ax += kp * pb.x.v[e];
+                ay += kp * pb.y.v[e];
+                az += kp * pb.z.v[e];
+            }
             o.v[e] = c0 * c.v[e] + (ax - c1) * xp.v[e] - (ax + c1) * xm.v[e] + (ay - c1) * yp.v[e] -
                      (ay + c1) * ym.v[e] + (az - c1) * zp.v[e] - (az + c1) * zm.v[e];
         }
@@ -820,9 +850,16 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               const double uxp = rowc[xp], uxm = rowc[xm];
                               const double uyp = rowc[n + x], uym = rowc[x - n];
                               const double uzp = rowzp[x], uzm = rowzm[x];
-                              const double by = tabd[TYX * n + x] + byz;
-                              const double bz = tabd[TZX * n + x] + bzy;
-                              const double adv = bx * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
+                              double bxe = bx;
+                              double by = tabd[TYX * n + x] + byz;
+                              double bz = tabd[TZX * n + x] + bzy;
+                              if constexpr (PT) {
+                                  const double* bpd = reinterpret_cast<const double*>(bpk);
+                                  bxe += bpd[i + e];
+                                  by += bpd[Ng + i + e];
+                                  bz += bpd[2 * Ng + i + e];
+                              }
+                              const double adv = bxe * (uxp - uxm) + by * (uyp - uym) + bz * (uzp - uzm);
                               const double lap = (uxp + uxm) + (uyp + uym) + (uzp + uzm) - 6.0 * c;
                               const double Lu = adv * inv2h - epsh2 * lap;
                               double fi = fp ? fp[i + e] : 0.0;
@@ -878,8 +915,9 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return o;
                       },
-                      [&](int i) -> OwnFD<KT, W> {
-                          OwnFD<KT, W> o;
+                      [&](int i) -> OwnFD<KT, W, PT> {
+                          OwnFD<KT, W, PT> o;
+                          o.b = load_pert(i);
                           if (ff) o.f = vload<KT, W>(ff + i);
                           else {
 #pragma unroll
@@ -892,7 +930,7 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           }
                           return o;
                       },
-                      [&](int i, int k, int yy, const OwnFD<KT, W>& ow, const float* rowc, const float* rowzp,
+                      [&](int i, int k, int yy, const OwnFD<KT, W, PT>& ow, const float* rowc, const float* rowzp,
                           const float* rowzm) {
                           const auto q = nb7(rowc, rowzp, rowzm);
                           const VK chi = vload<float, W>(rowc + ring_lo + x0);
@@ -903,13 +941,18 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
 #pragma unroll
                               for (int e = 0; e < W; ++e) fv.v[e] += ftk[x0 + e] + fyz;
                           }
-                          const KT ax = kx_y[k] + kx_z;
                           VK rv;
 #pragma unroll
                           for (int e = 0; e < W; ++e) {
                               const float c = q.c.v[e];
-                              const KT ay = ky_x[e] + ky_z;
-                              const KT az = kz_x[e] + kz_y[k];
+                              KT ax = kx_y[k] + kx_z;
+                              KT ay = ky_x[e] + ky_z;
+                              KT az = kz_x[e] + kz_y[k];
+                              if constexpr (PT) {
+                                  ax += kp * ow.b.x.v[e];
+                                  ay += kp * ow.b.y.v[e];
+                                  az += kp * ow.b.z.v[e];
+                              }
                               const KT dx = __fsub_rn(q.xp.v[e], q.xm.v[e]);
                               const KT dy = __fsub_rn(q.yp.v[e], q.ym.v[e]);
                               const KT dz = __fsub_rn(q.zp.v[e], q.zm.v[e]);
@@ -996,11 +1039,12 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               for (int e = 0; e < W; ++e) o.v[e] = v.r.v[e] + bk * (v.p.v[e] - ok * v.v.v[e]);
                               return o;
                           },
-                          [&](int i) -> VK { return vload<KT, W>(rh + i); },
-                          [&](int i, int k, int, const VK& rhv, const KT* rowc, const KT* rowzp,
+                          [&](int i) -> OwnH<KT, W, PT> { return {vload<KT, W>(rh + i), load_pert(i)}; },
+                          [&](int i, int k, int, const OwnH<KT, W, PT>& ow, const KT* rowc, const KT* rowzp,
                               const KT* rowzm) {
+                              const VK& rhv = ow.h;
                               const auto q7 = nb7(rowc, rowzp, rowzm);
-                              const VK av = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm);
+                              const VK av = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm, ow.b);
                               vstore(pn + i, q7.c);
                               vstore(vn + i, av);
 #pragma unroll
@@ -1040,11 +1084,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               for (int e = 0; e < W; ++e) o.v[e] = v.r.v[e] - al * v.v.v[e];
                               return o;
                           },
-                          [&](int) -> NoOwn { return NoOwn{}; },
-                          [&](int i, int k, int, const NoOwn&, const KT* rowc, const KT* rowzp,
+                          [&](int i) -> PertV<KT, W, PT> { return load_pert(i); },
+                          [&](int i, int k, int, const PertV<KT, W, PT>& pb, const KT* rowc, const KT* rowzp,
                               const KT* rowzm) {
                               const auto q7 = nb7(rowc, rowzp, rowzm);
-                              const VK tv = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm);
+                              const VK tv = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm, pb);
                               vstore(t + i, tv);
 #pragma unroll
                               for (int e = 0; e < W; ++e) {
@@ -1263,5 +1307,6 @@ using FineFn = void (*)(FineArgs);
 // nullptr (defined in fine_f32.cu and fine_f64.cu).
 FineFn fine_fn_f32(int W, int KF, int KS, int mode);
 FineFn fine_fn_f64(int W, int KF, int KS, int mode);
+FineFn fine_fn_pert(bool fp32, int W, int KF, int KS);   // FINE_MODE_IMPLICIT_PERT (fine_pert.cu)
 
 }  // namespace pr

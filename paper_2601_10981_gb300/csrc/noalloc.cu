@@ -63,8 +63,8 @@ int noalloc_max_n() { return NOALLOC_MAX_N; }
 int noalloc_max_count() { return NOALLOC_MAX_COLS; }
 size_t noalloc_scratch_bytes() { return NOALLOC_SCRATCH_BYTES; }
 
-cudaError_t apply_L_noalloc(int n, double L, const pr_flow& flow, double eps, const double* d_in,
-                            double* d_out, int count, bool transpose, cudaStream_t st) {
+cudaError_t apply_L_noalloc(int n, double L, const pr_flow& flow, const double* d_pert, double eps,
+                            const double* d_in, double* d_out, int count, bool transpose, cudaStream_t st) {
     if (n > NOALLOC_MAX_N || count > NOALLOC_MAX_COLS) return cudaErrorInvalidValue;
     if (count <= 0) return cudaSuccess;
     unsigned char* base = nullptr;
@@ -82,6 +82,7 @@ cudaError_t apply_L_noalloc(int n, double L, const pr_flow& flow, double eps, co
     g.h = L / n;
     g.eps = eps;
     g.tab = tab;
+    g.pert = d_pert;
     void* hin[NOALLOC_MAX_COLS];
     void* hout[NOALLOC_MAX_COLS];
     for (int i = 0; i < count; ++i) {

@@ -33,6 +33,7 @@ struct Grid {
     double h;
     double eps;
     const double* tab; // 6*n
+    const double* pert; // stored velocity perturbation [3][Ng] (b'_x, b'_y, b'_z), or nullptr
 };
 
 enum TabIdx { TXY = 0, TXZ = 1, TYX = 2, TYZ = 3, TZX = 4, TZY = 5 };
@@ -187,6 +188,8 @@ struct FineJob {
     int* its_total;     // [B]
     int* its_max;       // [B]
     int B;
+    const void* pert;   // stored velocity perturbation [3][Ng] in the Krylov type (float in
+                        // the FP32 mode, double in FP64), unscaled, or nullptr
 };
 constexpr int FINE_MAX_JOBS = 16;
 
@@ -373,7 +376,8 @@ cudaError_t launch_norms(const double* a, const double* b, const double* r, long
 size_t norms_part_doubles(long long Ng, int cnt);
 
 // Operator on caller buffers with its scratch in a static device array (noalloc.cu).
-cudaError_t apply_L_noalloc(int n, double L, const pr_flow& flow, double eps, const double* d_in,
+cudaError_t apply_L_noalloc(int n, double L, const pr_flow& flow, const double* d_pert, double eps,
+                            const double* d_in,
                             double* d_out, int count, bool transpose, cudaStream_t st);
 int noalloc_max_n();
 int noalloc_max_count();

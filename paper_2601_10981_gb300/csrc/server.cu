@@ -37,7 +37,7 @@ struct Req {
     int id = 0;
     int state = PR_REQ_PENDING;
     pr_request r{};
-    std::vector<double> u0, f;
+    std::vector<double> u0, f, pert;   // host copies; r.flow.pert points into pert
     pr_ctx* ctx = nullptr;
     void* ws = nullptr;
     size_t bytes = 0;
@@ -49,10 +49,12 @@ struct Req {
     std::string err;
 };
 
-using ShapeKey = std::tuple<int, double, int, int>;   // n, box length, precision, fine integrator
+// n, box length, precision, fine integrator, stored perturbation (one launch runs one
+// stencil kind)
+using ShapeKey = std::tuple<int, double, int, int, int>;
 
 ShapeKey shape_of(const pr_request& r) {
-    return ShapeKey(r.grid.n, r.grid.L, r.opts.precision, r.opts.fine);
+    return ShapeKey(r.grid.n, r.grid.L, r.opts.precision, r.opts.fine, r.flow.pert ? 1 : 0);
 }
 
 }  // namespace
@@ -218,6 +220,10 @@ pr_status pr_server_submit(pr_server* s, const pr_request* r, int* id) {
     q->r = *r;
     q->u0.assign(r->u0, r->u0 + Ng);
     if (r->f) q->f.assign(r->f, r->f + Ng);
+    if (r->flow.pert) {
+        q->pert.assign(r->flow.pert, r->flow.pert + 3 * Ng);
+        q->r.flow.pert = q->pert.data();
+    }
     q->r.u0 = nullptr;
     q->r.f = nullptr;
     q->k_max = (r->k_max <= 0 || r->k_max > r->n_sub) ? r->n_sub : r->k_max;

@@ -80,15 +80,22 @@ def fourier_field(n: int, kmax: int, seed: int, amp: float = 0.1,
     """sum_k a_k cos(k.x) + b_k sin(k.x) over K(kmax), coefficients from SplitMix64(seed)."""
     rng = SplitMix64(seed)
     x = grid_1d(n, L) * (TWO_PI / L)  # phase per unit wave number
-    out = np.zeros((n, n, n), dtype=np.float64)
+    # a cos(k.x) + b sin(k.x) = Re((a - i b) e^{i k.x}); the coefficients are drawn mode by
+    # mode in half-space order and the sum is taken per kz over (ky, kx) planes, so that
+    # the n^3 work is one product per distinct kz
+    coef = {}
     for (kx, ky, kz) in half_space_modes(kmax):
         a = rng.uniform_pm(amp)
         b = rng.uniform_pm(amp)
-        ex = np.exp(1j * kx * x)
-        ey = np.exp(1j * ky * x)
-        ez = np.exp(1j * kz * x)
-        e = ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
-        out += a * e.real + b * e.imag
+        coef.setdefault(kz, {}).setdefault(ky, []).append((kx, a - 1j * b))
+    e = lambda k: np.exp(1j * k * x)
+    out = np.zeros((n, n, n), dtype=np.float64)
+    for kz, rows in coef.items():
+        plane = np.zeros((n, n), dtype=np.complex128)   # [y][x]
+        for ky, terms in rows.items():
+            cx = sum(c * e(kx) for kx, c in terms)
+            plane += e(ky)[:, None] * cx[None, :]
+        out += (e(kz)[:, None, None] * plane[None, :, :]).real
     return out
 
 

@@ -103,10 +103,12 @@ def test_fine_steps_at_128(gpu, prec):
 
 @pytest.mark.parametrize("prec", [1, 0], ids=["fp32", "fp64"])
 def test_fine_steps_at_256(gpu, prec):
+    # the 256^3 case: Kolmogorov sin(8y) plus the seeded divergence-free perturbation of
+    # amplitude 0.05 (stored per point, FINE_MODE_IMPLICIT_PERT)
     bd, torch = gpu
     from test_gpu_parity import dev
-    w = pi.Workload("kol256", 256, pi.Flow("kolmogorov", k=8), 0.002, 1.0, 8, 2.5e-4, n_snap=16,
-                    m_cap=8)
+    w = pi.Workload("kol256", 256, pi.Flow("kolmogorov", k=8, pert_seed=4, pert_amp=0.05), 0.002, 1.0,
+                    8, 2.5e-4, n_snap=16, m_cap=8)
     s = bd.Parareal.from_workload(w, precision=prec)
     op = O.make_operator(w)
     u = pi.initial_state(256, seed=60)[None]

@@ -85,3 +85,17 @@ def test_perturbation_changes_the_solution():
     a, _ = fine_propagate(Operator(g, Flow("kolmogorov", k=2), 0.01, None), u, 0.0, 10, 0.02)
     b, _ = fine_propagate(Operator(g, KOL8P, 0.01, None), u, 0.0, 10, 0.02)
     assert np.linalg.norm(a - b) > 1e-4 * np.linalg.norm(a)
+
+
+def test_parareal_II_coarse_operator_injects_the_stored_perturbation():
+    from oracle.coarse import restrict
+    from oracle.parareal import coarse_operator
+    g = O.Grid(8)
+    op = Operator(g, KOL8P, 0.02, None)
+    opc = coarse_operator(op, 2)
+    full = perturbation(8, KOL8P.pert_seed, KOL8P.pert_amp)
+    base_c = velocity(Flow("kolmogorov", k=2), opc.grid)
+    for d, v in enumerate(opc.vel(0.0)):
+        assert np.array_equal(v, base_c[d] + restrict(full[d], 2))
+    # not the field drawn afresh on the coarse grid
+    assert np.max(np.abs(opc.pert - perturbation(4, KOL8P.pert_seed, KOL8P.pert_amp))) > 1e-3
