@@ -506,8 +506,11 @@ pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B
     ga.KB = c->KB;
     ga.ldG_b = (long long)3 * mmax * mmax;
     for (int q = 0; q < np; ++q) {
-        PR_CUDA(launch_apply_L(pieces[q], c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, f32, f32,
-                               false, c->st));
+        if (c->fp32)   // FP32 mode: double-float on the FP32 pipe
+            PR_CUDA(launch_apply_L_df(pieces[q], c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, c->st));
+        else
+            PR_CUDA(launch_apply_L(pieces[q], c->colsA, (void* const*)c->colsB, c->KA, c->ldcols, mmax, B, f32, f32,
+                                   false, c->st));
         ga.G = Lo + (size_t)q * mmax * mmax;
         PR_CUDA(launch_gram(ga, f32, f32, c->st));
     }

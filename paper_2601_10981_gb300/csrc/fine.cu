@@ -252,6 +252,70 @@ __global__ void __launch_bounds__(256) apply_L_kernel(Grid g, const void* const*
     }
 }
 
+// FP32 mode: L u of FP64 columns in double-float arithmetic on the FP32 pipe (GB300 runs
+// FP64 at 1/64 of the FP32 rate).  L u at a point is the weighted sum of the seven stencil
+// values; the weights (formed in FP64 once per point) and the values are split into float
+// pairs by moving bits, and the sum is taken with error-free products and TwoSums
+// (df_mac), ~1e-15 relative to the sum of the terms' magnitudes.
+__global__ void __launch_bounds__(256) apply_L_df_kernel(Grid g, const void* const* in_cols, void* const* out_cols,
+                                                         const int* count, int ldcols, double inv2h, double epsh2) {
+    const int b = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int)g.Ng) return;
+    const int n = g.n, n2 = n * n;
+    const int z = i / n2;
+    const int rem = i - z * n2;
+    const int y = rem / n;
+    const int x = rem - y * n;
+    int nb[7];
+    nb[0] = i;
+    nb[1] = i + (x + 1 == n ? 1 - n : 1);
+    nb[2] = i + (x == 0 ? n - 1 : -1);
+    nb[3] = i + (y + 1 == n ? n - n2 : n);
+    nb[4] = i + (y == 0 ? n2 - n : -n);
+    nb[5] = i + (z + 1 == n ? n2 - (int)g.Ng : n2);
+    nb[6] = i + (z == 0 ? (int)g.Ng - n2 : -n2);
+    const double* tab = g.tab;
+    double bx = tab[TXY * n + y] + tab[TXZ * n + z];
+    double by = tab[TYX * n + x] + tab[TYZ * n + z];
+    double bz = tab[TZX * n + x] + tab[TZY * n + y];
+    if (g.pert) {
+        bx += g.pert[i];
+        by += g.pert[g.Ng + i];
+        bz += g.pert[2 * g.Ng + i];
+    }
+    const double ax = inv2h * bx, ay = inv2h * by, az = inv2h * bz;
+    const double wd[7] = {6.0 * epsh2, ax - epsh2, -ax - epsh2, ay - epsh2, -ay - epsh2, az - epsh2, -az - epsh2};
+    float2 w[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) w[k] = d2df_bits(wd[k]);
+    const int cnt = count[b];
+    for (int c = 0; c < cnt; ++c) {
+        const double* in = (const double*)in_cols[(size_t)b * ldcols + c];
+        double* out = (double*)out_cols[(size_t)b * ldcols + c];
+        double u[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) u[k] = in[nb[k]];
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const float2 v = d2df_bits(u[k]);
+            df_mac(sh, sl, w[k].x, w[k].y, v.x, v.y);
+        }
+        out[i] = df_to_double(sh, sl);
+    }
+}
+
+cudaError_t launch_apply_L_df(const Grid& g, const void* const* in_cols, void* const* out_cols, const int* count,
+                              int ldcols, int max_count, int B, cudaStream_t st) {
+    if (max_count <= 0 || B <= 0) return cudaSuccess;
+    if (g.Ng > (1LL << 30)) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((g.Ng + 255) / 256), (unsigned)B);
+    apply_L_df_kernel<<<grid, 256, 0, st>>>(g, in_cols, out_cols, count, ldcols, 0.5 / g.h, g.eps / (g.h * g.h));
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols, void* const* out_cols,
                            const int* count, int ldcols, int max_count, int B, bool in_f32,
                            bool out_f32, bool transpose, cudaStream_t st) {

@@ -228,6 +228,9 @@ cudaError_t launch_tables(const pr_flow& flow, int n, double L, double* tab,
 // out[c] = L u[c] (transpose: L^T) for columns c < count[b] of each batch item b;
 // columns given as pointer arrays in_cols[b*ldcols + c], out_cols[...]; TI/TO = float
 // or double selected by the flags.
+// FP32 mode: L u of FP64 columns in double-float arithmetic (no transpose).
+cudaError_t launch_apply_L_df(const Grid& g, const void* const* in_cols, void* const* out_cols, const int* count,
+                              int ldcols, int max_count, int B, cudaStream_t st);
 cudaError_t launch_apply_L(const Grid& g, const void* const* in_cols,
                            void* const* out_cols, const int* count, int ldcols,
                            int max_count, int B, bool in_f32, bool out_f32, bool transpose,
