@@ -132,6 +132,27 @@ def test_fine_propagator_fp32(gpu):
             assert rel(snap[b, j], W[:, j]) < TOL32
 
 
+@pytest.mark.parametrize("n,prec", [(6, 0), (6, 1), (10, 1), (96, 0), (96, 1)])
+def test_fine_propagator_every_kernel_shape(gpu, n, prec):
+    # n = 6, 10: one point a thread (n % 4 != 0) with ragged rows per pass; n = 96: two
+    # owned rows a thread and three ring rows (the (KF, KS) = (3, 2) instantiation)
+    bd, torch = gpu
+    w = pi.Workload("shape", n, pi.Flow("abc"), 0.03, 1.0, 8, 1e-3, f_seed=9, m_cap=8)
+    s = solver(bd, w, precision=prec)
+    op = O.make_operator(w)
+    B, steps = (2, 2) if n == 96 else (3, 11)
+    u = np.stack([pi.initial_state(n, seed=70 + b) for b in range(B)])
+    s.set_initial(u[0], w.f())
+    out, snap = s.op_fine(dev(torch, u), steps, 1, 2)
+    out, snap = out.cpu().numpy(), snap.cpu().numpy()
+    tol = TOL64 if prec == 0 else TOL32
+    for b in range(B):
+        ue, W = O.fine_propagate(op, u[b], 0.0, steps, s.dt_eff, 1, 2, tol=1e-14)
+        assert rel(out[b], ue) < tol, (b, rel(out[b], ue))
+        assert rel(snap[b, 1], W[:, 1]) < tol
+    s.close()
+
+
 def test_fine_propagator_ragged_groups(gpu):
     # B not a multiple of the group count, explicit odd group size, non-power-of-two grid
     bd, torch = gpu
@@ -183,6 +204,31 @@ def test_pod_mode_matches_oracle(gpu, precision, w_f32):
             assert np.max(np.abs(Rg.T @ Rg - np.eye(m[b]))) < 1e-13
             tol = davis_kahan_tol(lam, m[b], eps_in)
             assert span_dist(Rg, Ro) < tol, (b, gamma, span_dist(Rg, Ro), tol)
+
+
+def test_pod_mode_wide_snapshot_matrices(gpu):
+    # 50 snapshot columns: 325 Gram tiles, more than 256 threads a CTA in the FP32 mode's
+    # double-float Gram (one row group), and 13 columns: 7 row groups of 28 threads; both
+    # modes against the oracle, spans within the Davis-Kahan bound
+    bd, torch = gpu
+    n = 8
+    rng = np.random.default_rng(3)
+    for ncol in (50, 13):
+        Q1, _ = np.linalg.qr(rng.standard_normal((n ** 3, ncol)))
+        Q2, _ = np.linalg.qr(rng.standard_normal((ncol, ncol)))
+        W = Q1 @ np.diag(np.logspace(0, -5.3, ncol)) @ Q2
+        for prec, eps_in in ((0, 1.1e-16), (1, 3.6e-15)):
+            # POD dimensions capped at 30 (the reduced systems hold at most 33 unknowns)
+            w = pi.Workload("podw", n, pi.Flow("abc"), 0.05, 1.0, 2, 1e-3, n_snap=ncol, m_cap=30)
+            s = solver(bd, w, precision=prec)
+            Wt = W.T.reshape(1, ncol, n, n, n)
+            R, m = s.op_pod(dev(torch, Wt), 0.999999, cap=30)
+            Ro, mo, lam = O.pod_mode(W, 0.999999, 30, 1e-13)
+            assert m[0] == mo, (ncol, prec, m[0], mo)
+            Rg = R.cpu().numpy().reshape(1, -1, n ** 3)[0, :m[0]].T
+            assert np.max(np.abs(Rg.T @ Rg - np.eye(m[0]))) < 1e-13
+            assert span_dist(Rg, Ro) < davis_kahan_tol(lam, m[0], eps_in), (ncol, prec)
+            s.close()
 
 
 # ---------------------------------------------------------------------- coarse update
