@@ -239,6 +239,23 @@ __device__ __forceinline__ double df_value_bits(float hi, float lo) { return df_
 template <int W> struct HiLo { Vec<float, W> hi, lo; };
 template <typename T> struct is_hilo : std::false_type {};
 template <int W> struct is_hilo<HiLo<W>> : std::true_type {};
+// Asynchronous global -> shared copy of B bytes (4, 8 or 16; both addresses aligned to
+// B), one commit group, and the wait for all but the newest n groups.
+template <int B>
+__device__ __forceinline__ void cp_async_b(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_newest() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// FP32-mode pointwise update phase: planes of its six inputs staged per thread in shared
+// memory (over the idle ring), FINE_PH3_SLOTS - 1 planes ahead.
+constexpr int FINE_PH3_SLOTS = 3;
+
 // The FP32-mode implicit setup ring: the stencil operand op (one float) and the state
 // u = hi + lo, in three planes.
 template <int W> struct OpHiLo { Vec<float, W> op, hi, lo; };
@@ -1129,7 +1146,78 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                     const bool upd_r = !half && sh.status == 0;
                     Acc<KT, 2> acc;
                     acc.init();
-                    if (upd_r) {
+                    // the update of the owned points from their six inputs
+                    auto p3_fn = [&](int i, const Raw6<KT, W>& v) {
+                        VK dn, rn;
+#pragma unroll
+                        for (int e = 0; e < W; ++e) {
+                            const KT sc_ = v.r.v[e] - al * v.v.v[e];
+                            dn.v[e] = v.d.v[e] + al * v.p.v[e] + om * sc_;
+                            rn.v[e] = sc_ - om * v.t.v[e];
+                            acc.f[0] += v.h.v[e] * rn.v[e];
+                            acc.f[1] += rn.v[e] * rn.v[e];
+                        }
+                        vstore(delta + i, dn);
+                        vstore(r + i, rn);
+                        acc.tick();
+                    };
+                    bool staged3 = false;
+                    if constexpr (DF && KS == 1) {
+                        if (upd_r) {
+                            // inputs of plane z staged by cp.async while planes z-2, z-1 are
+                            // updated; each thread reads back only what it copied, so no
+                            // barrier is needed; layout [slot][input][thread][W] (no bank
+                            // conflicts).  The ring is idle in this phase.
+                            staged3 = true;
+                            constexpr int NS = FINE_PH3_SLOTS;
+                            float* stg = reinterpret_cast<float*>(ring_raw);
+                            const int nthr = blockDim.x;
+                            const bool act = ty < TY;
+                            auto sad = [&](int sl, int q) { return stg + ((size_t)(sl * 6 + q) * nthr + threadIdx.x) * W; };
+                            for (int tt = t_lo; tt < t_hi; ++tt) {
+                                int y0, zlo, zhi;
+                                geo.tile(tt, y0, zlo, zhi);
+                                const int rowoff = (y0 + ty) * n + x0;
+                                auto issue = [&](int z, int sl) {
+                                    if (act && z < zhi) {
+                                        const long long i = (long long)z * n2 + rowoff;
+                                        if (!first) cp_async_b<4 * W>(sad(sl, 0), delta + i);
+                                        cp_async_b<4 * W>(sad(sl, 1), pn + i);
+                                        cp_async_b<4 * W>(sad(sl, 2), r + i);
+                                        cp_async_b<4 * W>(sad(sl, 3), vn + i);
+                                        cp_async_b<4 * W>(sad(sl, 4), t + i);
+                                        cp_async_b<4 * W>(sad(sl, 5), rh + i);
+                                    }
+                                    cp_async_commit_group();
+                                };
+#pragma unroll
+                                for (int d = 0; d < NS - 1; ++d) issue(zlo + d, d);
+                                int sl = 0;
+                                for (int z = zlo; z < zhi; ++z) {
+                                    // refill the slot of plane z - 1 (read last iteration)
+                                    issue(z + NS - 1, sl == 0 ? NS - 1 : sl - 1);
+                                    cp_async_wait_newest<NS - 1>();
+                                    if (act) {
+                                        Raw6<KT, W> v;
+                                        if (!first) v.d = vload<float, W>(sad(sl, 0));
+                                        else {
+#pragma unroll
+                                            for (int e = 0; e < W; ++e) v.d.v[e] = 0.0f;
+                                        }
+                                        v.p = vload<float, W>(sad(sl, 1));
+                                        v.r = vload<float, W>(sad(sl, 2));
+                                        v.v = vload<float, W>(sad(sl, 3));
+                                        v.t = vload<float, W>(sad(sl, 4));
+                                        v.h = vload<float, W>(sad(sl, 5));
+                                        p3_fn(z * n2 + rowoff, v);
+                                    }
+                                    sl = (sl + 1 == NS) ? 0 : sl + 1;
+                                }
+                                cp_async_wait_newest<0>();
+                            }
+                        }
+                    }
+                    if (upd_r && !staged3) {
                         owned([&](int i) -> Raw6<KT, W> {
                                   Raw6<KT, W> o;
                                   if (!first) o.d = vload<KT, W>(delta + i);
@@ -1144,21 +1232,8 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                                   o.h = vload<KT, W>(rh + i);
                                   return o;
                               },
-                              [&](int i, const Raw6<KT, W>& v) {
-                                  VK dn, rn;
-#pragma unroll
-                                  for (int e = 0; e < W; ++e) {
-                                      const KT sc_ = v.r.v[e] - al * v.v.v[e];
-                                      dn.v[e] = v.d.v[e] + al * v.p.v[e] + om * sc_;
-                                      rn.v[e] = sc_ - om * v.t.v[e];
-                                      acc.f[0] += v.h.v[e] * rn.v[e];
-                                      acc.f[1] += rn.v[e] * rn.v[e];
-                                  }
-                                  vstore(delta + i, dn);
-                                  vstore(r + i, rn);
-                                  acc.tick();
-                              });
-                    } else {
+                              p3_fn);
+                    } else if (!upd_r) {
                         owned([&](int i) -> RawP2<KT, W> {
                                   RawP2<KT, W> o;
                                   if (!first) o.d = vload<KT, W>(delta + i);
@@ -1297,7 +1372,11 @@ inline FineGeom fine_geom(int n, bool fp32) {
     const size_t tabs = ((size_t)9 * n * (sizeof(double) + (fp32 ? sizeof(float) : sizeof(double))) + 31) / 32 * 32;
     // ring: 8 bytes a point (FP64 value, or the float pair of the FP32 mode's RK4 stages),
     // 12 in the FP32 mode's implicit setup (operand, hi, lo)
-    g.smem = tabs + (size_t)FINE_SLOTS * (g.TY + 2) * n * (fp32 ? 12 : 8);
+    const size_t ring = (size_t)FINE_SLOTS * (g.TY + 2) * n * (fp32 ? 12 : 8);
+    // FP32 mode, one owned row a thread: the pointwise phase stages FINE_PH3_SLOTS planes of
+    // six float inputs per thread over the ring
+    const size_t ph3 = (fp32 && g.KS == 1) ? (size_t)FINE_PH3_SLOTS * 6 * g.threads * g.W * sizeof(float) : 0;
+    g.smem = tabs + std::max(ring, ph3);
     return g;
 }
 
