@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
     auto barrier = [&]() -> bool { return group_barrier(a.bar, (unsigned)G, a.spin_limit, a.err); };
     const int n_ = a.g.n;
     const long long n2 = (long long)n_ * n_;
+    const int n2i = n_ * n_;
     const double inv2h = 0.5 / a.g.h, epsh2 = a.g.eps / (a.g.h * a.g.h);
 
     for (int t = 0; t < a.count; ++t) {
@@ -546,7 +547,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             const double* d = a.d;
             double v[3] = {0.0, 0.0, 0.0};
             for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const int x = (int)(i % n_), y = (int)((i / n_) % n_), z = (int)(i / n2);
+                // 32-bit index arithmetic (n^3 < 2^31): 64-bit division costs ~70 instructions
+                const int i32 = (int)i, z = i32 / n2i, rz = i32 - z * n2i, y = rz / n_, x = rz - y * n_;
                 const long long base = i - x, rowb = i - (long long)y * n_, plb = i - (long long)z * n2;
                 const double uc = d[i];
                 const double uxp = d[base + (x + 1 == n_ ? 0 : x + 1)], uxm = d[base + (x == 0 ? n_ - 1 : x - 1)];
@@ -589,7 +591,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             const double* d = a.d;
             double v[1] = {0.0};
             for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const int x = (int)(i % n_), y = (int)((i / n_) % n_), z = (int)(i / n2);
+                // 32-bit index arithmetic (n^3 < 2^31): 64-bit division costs ~70 instructions
+                const int i32 = (int)i, z = i32 / n2i, rz = i32 - z * n2i, y = rz / n_, x = rz - y * n_;
                 const long long base = i - x, rowb = i - (long long)y * n_, plb = i - (long long)z * n2;
                 const double uc = d[i];
                 const double uxp = d[base + (x + 1 == n_ ? 0 : x + 1)], uxm = d[base + (x == 0 ? n_ - 1 : x - 1)];

@@ -177,6 +177,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_by
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long long CH, int chunks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -449,27 +450,50 @@ __global__ void __launch_bounds__(256) tsmm_kernel(TsmmArgs a) {
 // one thread per point, blocks of J <= 16 outputs.  C sits in shared memory as float-pair
 // planes hi, lo (rows padded to a multiple of 4, read as warp-wide broadcasts); each input
 // is split once per block (d2df_bits) and broadcast into both lanes of a packed pair, so
-// one df_mac2 serves two outputs.  Four inputs are loaded ahead (memory-level parallelism).
+// one df_mac2 serves two outputs.  The inputs travel by cp.async in groups of TSMM_TG into
+// the thread's own shared-memory slots, one group ahead (no registers held, no barrier:
+// each thread reads back only its own copies).
+constexpr int TSMM_TG = 8;
 template <int J>
 __device__ __forceinline__ void tsmm_df_block(const void* const* cols, int KIN, const float* sC, int pl, int KP,
-                                              int j0, int jn, long long p, long long Ng, double* out) {
+                                              int j0, int jn, long long p, long long Ng, double* out,
+                                              double* stg, int nthr) {
     constexpr int H = J / 2;
     f2p sh[H], sl[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) sh[h] = sl[h] = 0ull;
-#pragma unroll 4
-    for (int i = 0; i < KIN; ++i) {
-        const float2 x = d2df_bits(reinterpret_cast<const double*>(cols[i])[p]);
-        const f2p xh = pk2(x.x, x.x), nxh = pk2(-x.x, -x.x), xl = pk2(x.y, x.y);
-        const float* row = sC + (size_t)i * KP + j0;
+    // stg: this thread's slots, [slot][k][thread] (thread-contiguous: no bank conflicts)
+    auto slot_of = [&](int sl2, int k) { return stg + (size_t)(sl2 * TSMM_TG + k) * nthr; };
+    auto issue = [&](int g, int sl2) {
 #pragma unroll
-        for (int h4 = 0; h4 < J / 4; ++h4) {
-            const ulonglong2 ch = *reinterpret_cast<const ulonglong2*>(row + 4 * h4);
-            const ulonglong2 cl = *reinterpret_cast<const ulonglong2*>(row + pl + 4 * h4);
-            df_mac2(sh[2 * h4], sl[2 * h4], xh, nxh, xl, ch.x, cl.x);
-            df_mac2(sh[2 * h4 + 1], sl[2 * h4 + 1], xh, nxh, xl, ch.y, cl.y);
+        for (int k = 0; k < TSMM_TG; ++k) {
+            const int i = g * TSMM_TG + k;
+            if (i < KIN) cp_async8(slot_of(sl2, k), reinterpret_cast<const double*>(cols[i]) + p, 8);
+        }
+        cp_async_commit();
+    };
+    const int ng = (KIN + TSMM_TG - 1) / TSMM_TG;
+    issue(0, 0);
+    for (int g = 0; g < ng; ++g) {
+        issue(g + 1, (g + 1) & 1);   // the slot of group g - 1, read in the previous pass
+        cp_async_wait1();            // group g landed
+#pragma unroll 2
+        for (int k = 0; k < TSMM_TG; ++k) {
+            const int i = g * TSMM_TG + k;
+            if (i >= KIN) break;
+            const float2 x = d2df_bits(*slot_of(g & 1, k));
+            const f2p xh = pk2(x.x, x.x), nxh = pk2(-x.x, -x.x), xl = pk2(x.y, x.y);
+            const float* row = sC + (size_t)i * KP + j0;
+#pragma unroll
+            for (int h4 = 0; h4 < J / 4; ++h4) {
+                const ulonglong2 ch = *reinterpret_cast<const ulonglong2*>(row + 4 * h4);
+                const ulonglong2 cl = *reinterpret_cast<const ulonglong2*>(row + pl + 4 * h4);
+                df_mac2(sh[2 * h4], sl[2 * h4], xh, nxh, xl, ch.x, cl.x);
+                df_mac2(sh[2 * h4 + 1], sl[2 * h4 + 1], xh, nxh, xl, ch.y, cl.y);
+            }
         }
     }
+    cp_async_wait_all();
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         const float2 vh = upk2(sh[h]), vl = upk2(sl[h]);
@@ -498,13 +522,16 @@ __global__ void __launch_bounds__(256) tsmm_df_kernel(TsmmArgs a) {
     if (p >= a.Ng) return;
     const void* const* cols = a.colsIn + (size_t)b * a.ldcols;
     double* out = reinterpret_cast<double*>(a.out) + (size_t)b * a.ld_out_b;
+    // per-thread input slots after the C planes (16-byte aligned)
+    double* stg = reinterpret_cast<double*>(smem_raw + ((size_t)2 * pl * sizeof(float) + 15) / 16 * 16) + threadIdx.x;
+    const int nthr = blockDim.x;
     for (int j0 = 0; j0 < KOUT; j0 += 16) {
         const int jn = min(16, KOUT - j0);
         switch ((jn + 3) / 4) {
-        case 1: tsmm_df_block<4>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
-        case 2: tsmm_df_block<8>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
-        case 3: tsmm_df_block<12>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
-        default: tsmm_df_block<16>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out); break;
+        case 1: tsmm_df_block<4>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out, stg, nthr); break;
+        case 2: tsmm_df_block<8>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out, stg, nthr); break;
+        case 3: tsmm_df_block<12>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out, stg, nthr); break;
+        default: tsmm_df_block<16>(cols, KIN, sC, pl, KP, j0, jn, p, a.Ng, out, stg, nthr); break;
         }
     }
 }
@@ -514,7 +541,10 @@ cudaError_t launch_tsmm(const TsmmArgs& a, bool in_f32, bool out_f32, cudaStream
     dim3 grid((unsigned)((a.Ng + 255) / 256), a.B);
     const size_t cells = (size_t)a.maxKIN * ((a.maxKOUT + 3) / 4 * 4);
     if (a.df && !in_f32 && !out_f32) {
-        tsmm_df_kernel<<<grid, 256, 2 * cells * sizeof(float), st>>>(a);
+        const size_t smem = (2 * cells * sizeof(float) + 15) / 16 * 16 + (size_t)2 * TSMM_TG * 256 * sizeof(double);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute((const void*)tsmm_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tsmm_df_kernel<<<grid, 256, smem, st>>>(a);
     } else if (in_f32 && out_f32) {
         tsmm_kernel<float, float, float><<<grid, 256, cells * sizeof(float), st>>>(a);
     } else if (!in_f32 && out_f32) {
