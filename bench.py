@@ -396,7 +396,7 @@ def run_ours(args):
         s.rewind()
         s.set_interfaces(U0, 0)
         s.iterate(1)
-        Uout[:] = s.interfaces().reshape(w.n_sub + 1, -1)
+        s.interfaces(out=Uout)   # device -> pinned host, no staging copy
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     e2e_ms = reduce_max(e2e_ms, dist, "cuda")

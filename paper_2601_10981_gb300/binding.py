@@ -301,8 +301,13 @@ class Parareal:
             a = np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
             self._check(self._lib.pr_set_reference(self.ctx, a.ctypes.data_as(C.c_void_p), 0))
 
-    def interfaces(self) -> np.ndarray:
-        out = np.empty((self.N + 1, self.n, self.n, self.n))
+    def interfaces(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """U^k_0..U^k_N; out: an optional C-contiguous float64 host array of N+1 grid
+        functions to fill (e.g. pinned memory, for a direct device-to-host copy)."""
+        if out is None:
+            out = np.empty((self.N + 1, self.n, self.n, self.n))
+        elif not (out.dtype == np.float64 and out.flags.c_contiguous and out.size == (self.N + 1) * self.Ng):
+            raise ValueError("out must be a C-contiguous float64 array of (N+1) n^3 values")
         self._check(self._lib.pr_get_interfaces(self.ctx, _dptr(out)))
         return out
 
