@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
     double* cs = V + (size_t)Kp * ld;           // [Kp/2][2]
     double* lam = cs + Kp;                       // [Kp]
     int* perm = reinterpret_cast<int*>(lam + Kp);  // [Kp]
+    int* pq = perm + Kp;                         // [Kp/2][2]: the round's pairs
     __shared__ double red[32];
     __shared__ int s_stop;
     const double* Gb = a.G + (size_t)b * a.ldG_b;
@@ -604,6 +605,9 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
     }
     __syncthreads();
     const int npair = Kp / 2;
+    // fixed thread -> (pair, first row) map of the rotation updates: no divisions per element
+    const int ti = threadIdx.x % npair, kst = blockDim.x / npair;
+    const int tk0 = threadIdx.x / npair;
     for (int sweep = 0; sweep < EIG_MAX_SWEEPS; ++sweep) {
         // convergence: off-diagonal Frobenius norm against the whole matrix
         double off = 0.0, tot = 0.0;
@@ -657,33 +661,32 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
                 }
                 cs[2 * i] = c;
                 cs[2 * i + 1] = s;
+                pq[2 * i] = p;
+                pq[2 * i + 1] = q;
             }
             __syncthreads();
-            // A <- A J, V <- V J (columns p, q)
-            for (int w = threadIdx.x; w < Kp * npair; w += blockDim.x) {
-                const int i = w % npair, k = w / npair;
-                int p, q;
-                rr_pair(r, i, Kp, p, q);
-                const double c = cs[2 * i], s = cs[2 * i + 1];
-                if (s == 0.0) continue;
-                const double akp = A[k * ld + p], akq = A[k * ld + q];
-                A[k * ld + p] = c * akp - s * akq;
-                A[k * ld + q] = s * akp + c * akq;
-                const double vkp = V[k * ld + p], vkq = V[k * ld + q];
-                V[k * ld + p] = c * vkp - s * vkq;
-                V[k * ld + q] = s * vkp + c * vkq;
+            const bool upd = tk0 < kst && cs[2 * ti + 1] != 0.0;
+            const double c = cs[2 * ti], s = cs[2 * ti + 1];
+            const int p = pq[2 * ti], q = pq[2 * ti + 1];
+            if (upd) {
+                // A <- A J, V <- V J (columns p, q)
+                for (int k = tk0; k < Kp; k += kst) {
+                    const double akp = A[k * ld + p], akq = A[k * ld + q];
+                    A[k * ld + p] = c * akp - s * akq;
+                    A[k * ld + q] = s * akp + c * akq;
+                    const double vkp = V[k * ld + p], vkq = V[k * ld + q];
+                    V[k * ld + p] = c * vkp - s * vkq;
+                    V[k * ld + q] = s * vkp + c * vkq;
+                }
             }
             __syncthreads();
-            // A <- J^T A (rows p, q)
-            for (int w = threadIdx.x; w < Kp * npair; w += blockDim.x) {
-                const int i = w % npair, k = w / npair;
-                int p, q;
-                rr_pair(r, i, Kp, p, q);
-                const double c = cs[2 * i], s = cs[2 * i + 1];
-                if (s == 0.0) continue;
-                const double apk = A[p * ld + k], aqk = A[q * ld + k];
-                A[p * ld + k] = c * apk - s * aqk;
-                A[q * ld + k] = s * apk + c * aqk;
+            if (upd) {
+                // A <- J^T A (rows p, q)
+                for (int k = tk0; k < Kp; k += kst) {
+                    const double apk = A[p * ld + k], aqk = A[q * ld + k];
+                    A[p * ld + k] = c * apk - s * aqk;
+                    A[q * ld + k] = s * apk + c * aqk;
+                }
             }
             __syncthreads();
         }
@@ -736,7 +739,7 @@ cudaError_t launch_eig_pod(const EigArgs& a, cudaStream_t st) {
     if (a.B <= 0) return cudaSuccess;
     const int Kp = a.maxK + (a.maxK & 1);
     const size_t smem = (size_t)2 * Kp * (Kp + 1) * sizeof(double) + (size_t)2 * Kp * sizeof(double) +
-                        (size_t)Kp * sizeof(int) + 16;
+                        (size_t)2 * Kp * sizeof(int) + 16;
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
         cudaFuncSetAttribute(eig_pod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
