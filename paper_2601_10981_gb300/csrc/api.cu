@@ -467,7 +467,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
 // 3 mmax^2 in Lo, R^T L R (steady flows) or the pieces R^T D R, R^T A0 R, R^T A1 R
 // (time-dependent flows, L(t) = D + c0(t) A0 + c1(t) A1, D = -eps Lap_h).
 pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B, int mmax, double* Mo,
-                   double* Lo) {
+                   double* Lo, bool orthonormal = false) {
     const bool f32 = false;
     pr_status s = cols_contig(c, R, bstride_elems * c->esz, m, 1, B, c->colsA, c->KA, c->esz);
     if (s != PR_OK) return s;
@@ -490,7 +490,12 @@ pr_status galerkin(pr_ctx* c, char* R, size_t bstride_elems, const int* m, int B
     ga.ldG = mmax;
     ga.ldG_b = (long long)mmax * mmax;
     ga.df = c->fp32;
-    PR_CUDA(launch_gram(ga, f32, f32, c->st));
+    if (c->fp32 && orthonormal)
+        // FP32 mode: the bases come out of a Cholesky-QR pass (orthonormal to ~1e-15), so
+        // their mass matrix V^T V is the identity to that level; the FP64 mode forms it
+        PR_CUDA(launch_identity(Mo, mmax, (long long)mmax * mmax, m, B, c->st));
+    else
+        PR_CUDA(launch_gram(ga, f32, f32, c->st));
     const Grid g = grid_of(c);
     Grid pieces[3] = {g, g, g};
     int np = 1;
@@ -1167,7 +1172,8 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
                          c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k);
         if (s != PR_OK) return s;
         s = galerkin(c, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k, B2,
-                     c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * 3 * c->mcap2 * c->mcap2);
+                     c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * 3 * c->mcap2 * c->mcap2,
+                     true);
         if (s != PR_OK) return s;
     }
     c->r1cur = nw;

@@ -818,6 +818,24 @@ cudaError_t launch_chol_inv(const double* G, int ldG, long long ldG_b, const int
 }
 
 // ------------------------------------------------------------------------------------
+// M_b = I_{m[b]} (the Galerkin mass matrix V^T V of an orthonormal basis, M = I).
+__global__ void identity_kernel(double* M, int ld, long long ld_b, const int* m) {
+    const int b = blockIdx.x, mb = m[b];
+    double* Mb = M + (size_t)b * ld_b;
+    for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
+        const int i = e / mb, j = e - i * mb;
+        Mb[(size_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+cudaError_t launch_identity(double* M, int ld, long long ld_b, const int* m, int B, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    identity_kernel<<<B, 256, 0, st>>>(M, ld, ld_b, m);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
 __global__ void assemble_cols_kernel(const void* const* bases, const int* const* cnt_ptrs, int nb,
                                      long long Ng, int esize, const void** cols, int ld, int* K) {
     const int b = blockIdx.x;

@@ -263,6 +263,8 @@ struct GramArgs {
 int gram_chunks(long long Ng);
 size_t gram_part_doubles(long long Ng, int B, int maxKA, int maxKB);
 cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t st);
+// M_b = I_{m[b]} for b < B (row stride ld, batch stride ld_b).
+cudaError_t launch_identity(double* M, int ld, long long ld_b, const int* m, int B, cudaStream_t st);
 
 // Tall-skinny multiply: Out_b[:, j] = sum_i In_b[:, i] C_b[i][j], i < KIN[b], j < KOUT[b];
 // inputs as column pointers, output contiguous columns out + b*ld_out_b + j*Ng.
