@@ -125,6 +125,7 @@ struct pr_ctx {
     unsigned* counters = nullptr;  // [N + 64]
     const void** colsA = nullptr;
     const void** colsB = nullptr;
+    int* colblk = nullptr;         // [N + 1][ldcols] block of each colsA column (level 2)
     const void** bases = nullptr;  // [N][4]
     const int** cntp = nullptr;    // [N][4]
     int* KA = nullptr;
@@ -241,6 +242,7 @@ size_t plan(pr_ctx* c, char* base) {
     c->counters = b.take<unsigned>((size_t)N + 64);
     c->colsA = b.take<const void*>((size_t)(N + 1) * c->ldcols);
     c->colsB = b.take<const void*>((size_t)(N + 1) * c->ldcols);
+    c->colblk = b.take<int>((size_t)(N + 1) * c->ldcols);
     c->bases = b.take<const void*>((size_t)(N + 1) * 4);
     c->cntp = b.take<const int*>((size_t)(N + 1) * 4);
     c->KA = b.take<int>(N + 1);
@@ -348,14 +350,14 @@ pr_status ensure_ws(pr_ctx* c) {
 // and expanded on the device into column pointer arrays.
 pr_status upload_blocks(pr_ctx* c, const std::vector<const void*>& bases,
                         const std::vector<const int*>& cnts, int nb, int B, const void** cols,
-                        int* K, int esize) {
+                        int* K, int esize, int* blk = nullptr) {
     PR_CUDA(cudaMemcpyAsync(c->bases, bases.data(), sizeof(void*) * bases.size(),
                             cudaMemcpyHostToDevice, c->st));
     PR_CUDA(cudaMemcpyAsync(c->cntp, cnts.data(), sizeof(int*) * cnts.size(),
                             cudaMemcpyHostToDevice, c->st));
     // pageable async copies are staged before returning and stream-ordered, so the host
     // vectors may go out of scope and the next upload cannot overtake this expansion
-    PR_CUDA(launch_assemble_cols(c->bases, c->cntp, nb, B, c->Ng, esize, cols, c->ldcols, K, c->st));
+    PR_CUDA(launch_assemble_cols(c->bases, c->cntp, nb, B, c->Ng, esize, cols, c->ldcols, K, blk, c->st));
     return PR_OK;
 }
 
@@ -374,8 +376,11 @@ pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const i
 
 // POD_Mode + CholQR2 on B batch items whose snapshot columns are already in
 // (c->colsA, c->KA).  Result: dest + b*dest_bstride (columns of Ng), dims m_dest[b].
+// ortho_blocks: the snapshot columns are blocks of orthonormal bases (c->colblk says
+// which); the FP32 mode then takes their diagonal Gram blocks as the identity.
 pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, bool in_f32, int cap,
-                       int mmax, char* dest, size_t dest_bstride_elems, int* m_dest) {
+                       int mmax, char* dest, size_t dest_bstride_elems, int* m_dest,
+                       bool ortho_blocks = false) {
     const bool f32 = false;  // bases and their Grams are FP64
     cudaStream_t st = c->st;
     // Gram W^T W
@@ -396,6 +401,8 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     ga.ldG = maxK;
     ga.ldG_b = (long long)maxK * maxK;
     ga.df = c->fp32;   // FP32 mode: double-float Grams and projections on the FP32 pipe
+    // the bases leave Cholesky QR orthonormal to ~1e-15, far below the FP32 mode's accuracy
+    ga.colblk = (c->fp32 && ortho_blocks && !in_f32) ? c->colblk : nullptr;
     PR_CUDA(launch_gram(ga, in_f32, in_f32, st));
     // eigenpairs + dimension + C = Y_m Lambda_m^{-1/2}
     EigArgs ea{};
@@ -436,6 +443,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     pr_status s = cols_contig(c, c->scr[0], (size_t)mmax * c->Ng * c->esz, m_dest, 1, B, c->colsB, c->KB, c->esz);
     if (s != PR_OK) return s;
     GramArgs gb = ga;
+    gb.colblk = nullptr;
     gb.colsA = c->colsB;
     gb.colsB = c->colsB;
     gb.KA = c->KB;
@@ -1166,10 +1174,11 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
                 cs.push_back(nullptr);
             }
         }
-        s = upload_blocks(c, bs, cs, nb, B2, c->colsA, c->KA, c->esz);
+        s = upload_blocks(c, bs, cs, nb, B2, c->colsA, c->KA, c->esz, c->colblk);
         if (s != PR_OK) return s;
         s = pod_pipeline(c, B2, c->w2, c->gamma3, c->tau, false, c->o.m_cap, c->mcap2,
-                         c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k);
+                         c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k,
+                         true);
         if (s != PR_OK) return s;
         s = galerkin(c, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k, B2,
                      c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * 3 * c->mcap2 * c->mcap2,

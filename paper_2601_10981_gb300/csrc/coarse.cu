@@ -2,8 +2,8 @@
 // eq. (formula4), swept over the subintervals in order (Algorithm 2 and the remark after
 // it: U^k_{n+1} needs U^k_n).
 //
-// For V = [R, d] with d~ = U - R R^T U orthogonalised once more against R and
-// d = d~ / ||d~|| (eqs. (eqaug), (eq12)), the bordered reduced matrices of eq. (eq13) are
+// For V = [R, d] with d~ = U - R R^T U and d = d~ / ||d~|| (eqs. (eqaug), (eq12)), the
+// bordered reduced matrices of eq. (eq13) are
 // assembled from the level-2 Galerkin blocks R^T R, R^T L R (computed once per
 // subinterval by the POD update) and the border terms R^T d~, R^T L d~, (L^T d~)^T R,
 // d~^T L d~.  Because G is affine and both G terms of eq. (formula4) use the same space,
@@ -11,10 +11,9 @@
 // so the forcing cancels and one reduced propagation of the difference suffices.
 //
 // The whole sweep is one persistent cooperative launch (one CTA per SM, each owning a
-// fixed contiguous range of grid points).  Per subinterval, four grid-wide barriers:
+// fixed contiguous range of grid points).  Per subinterval, three grid-wide barriers:
 //   A  R^T U, R^T U', U.U
-//   B  d1 = U - R (R^T U)                       ; R^T d1
-//   C  d~ = d1 - R (R^T d1)                     ; R^T d~, d~.d~, d~.U, d~.U'
+//   C  d~ = U - R (R^T U)                       ; R^T d~, d~.d~, d~.(U - U')
 //   D  L d~, L^T d~ at owned points             ; R^T L d~, R^T L^T d~, d~.L d~
 //   E  reduced solve, repeated by every CTA on identical inputs (no barrier)
 //   F  U^k_{n+1} = F_n + R g + d~ g_d at owned points (read back by the next A)
@@ -142,8 +141,8 @@ constexpr int CSW_MAX_GRID = 1024;
 size_t coarse_part_doubles(long long, int) { return (size_t)2 * CSW_MAXQ * CSW_MAX_GRID; }
 
 struct CswShared {
-    double RU[CSW_MAXM], RUp[CSW_MAXM], RD1[CSW_MAXM], RD[CSW_MAXM], RL[CSW_MAXM], RLt[CSW_MAXM];
-    double UU, DD, DU, DUp, DLD;
+    double RU[CSW_MAXM], RUp[CSW_MAXM], RD[CSW_MAXM], RL[CSW_MAXM], RLt[CSW_MAXM];
+    double UU, DD, DdU, DLD;   // DdU = d~ . (U - U')
     // time-dependent flows: R^T D d~, R^T A_q d~ and d~.D d~, d~.A_q d~
     double RPD[CSW_MAXM], RPA0[CSW_MAXM], RPA1[CSW_MAXM];
     double PDD, PDA0, PDA1;
@@ -258,7 +257,7 @@ __device__ void csw_small(CswShared& sh, const CoarseSweepArgs& a, int m, const 
         sh.A[i * CSW_LDA + K + j] = mv;
     }
     for (int i = threadIdx.x; i < K; i += blockDim.x)
-        sh.A[i * CSW_LDA + 2 * K] = (i < m) ? sh.RU[i] - sh.RUp[i] : (sh.DU - sh.DUp) / nd;
+        sh.A[i * CSW_LDA + 2 * K] = (i < m) ? sh.RU[i] - sh.RUp[i] : sh.DdU / nd;
     __syncthreads();
     for (int j = 0; j < K; ++j) {
         if (threadIdx.x < 32) {
@@ -384,7 +383,7 @@ __device__ void csw_small_tdep(CswShared& sh, const CoarseSweepArgs& a, int m, c
     const long long PL = (long long)a.ldM * a.ldM;
     // Mv in the x slot area: keep it in sh.y? use the RHS column for b, Mv read from Mr
     for (int i = threadIdx.x; i < K; i += blockDim.x)
-        sh.x[i] = (i < m) ? sh.RU[i] - sh.RUp[i] : (sh.DU - sh.DUp) / nd;
+        sh.x[i] = (i < m) ? sh.RU[i] - sh.RUp[i] : sh.DdU / nd;
     __syncthreads();
     auto mv = [&](int i, int j) -> double {
         if (i < m && j < m) return Mr[(size_t)i * a.ldM + j];
@@ -487,8 +486,7 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             // plain coarse space: no augmentation direction
             if (threadIdx.x == 0) {
                 sh.DD = 0.0;
-                sh.DU = 0.0;
-                sh.DUp = 0.0;
+                sh.DdU = 0.0;
                 sh.DLD = 0.0;
             }
             __syncthreads();
@@ -501,39 +499,28 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             }
             continue;
         }
-        // ---- B: d1 = U - R (R^T U) ; R^T d1
+        // ---- C: d~ = U - R (R^T U) ; R^T d~, d~.d~, d~.(U - U').  One projection: the
+        //         Galerkin space span{R, d~} = span{R, U} does not depend on how much of R
+        //         is taken out of U, and the mass-matrix column R^T d~ carries whatever
+        //         rounding leaves in span R (at most ~eps ||U|| / ||d~|| of d~ / ||d~||).
         {
+            double v[2] = {0.0, 0.0};
             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                double v = U[p];
-                for (int i = 0; i < m; ++i) v -= sh.RU[i] * R[(size_t)i * Ng + p];
-                a.d[p] = v;
-            }
-            __syncthreads();
-            csw_dots(R, Ng, m, a.d, 0, nullptr, 0, lo, hi, part(), G);
-            if (!barrier()) return;
-            csw_reduce(part(), m, G, [&](int q, double s) { sh.RD1[q] = s; });
-            buf ^= 1;
-        }
-        // ---- C: d~ = d1 - R (R^T d1) ; R^T d~, d~.d~, d~.U, d~.U'
-        {
-            double v[3] = {0.0, 0.0, 0.0};
-            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                double d = a.d[p];
-                for (int i = 0; i < m; ++i) d -= sh.RD1[i] * R[(size_t)i * Ng + p];
+                const double u = U[p];
+                double d = u;
+                for (int i = 0; i < m; ++i) d -= sh.RU[i] * R[(size_t)i * Ng + p];
                 a.d[p] = d;
                 v[0] += d * d;
-                v[1] += d * U[p];
-                v[2] += d * Up[p];
+                v[1] += d * (u - Up[p]);
             }
-            csw_block_sums(v, 3, sh, part() + (size_t)m * G, G);
+            csw_block_sums(v, 2, sh, part() + (size_t)m * G, G);
             __syncthreads();
             csw_dots(R, Ng, m, a.d, 0, nullptr, 0, lo, hi, part(), G);
             if (!barrier()) return;
-            csw_reduce(part(), m + 3, G, [&](int q, double s) {
+            csw_reduce(part(), m + 2, G, [&](int q, double s) {
                 if (q < m) sh.RD[q] = s;
                 else if (q == m) sh.DD = s;
-                else if (q == m + 1) sh.DU = s;
-                else sh.DUp = s;
+                else sh.DdU = s;
             });
             buf ^= 1;
         }

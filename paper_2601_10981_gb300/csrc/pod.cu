@@ -199,14 +199,55 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
     const void* const* colsB = (a.sym ? a.colsA : a.colsB) + (size_t)b * a.ldcols;
 
     const int nbA = (KA + 1) / 2, nbB = (KB + 1) / 2;
-    const int ntiles = gdf_tiles(KA, KB, a.sym);
+    int ntiles = gdf_tiles(KA, KB, a.sym);
+    const size_t outsz = (size_t)a.maxKA * a.maxKB;
+    double* mypart = a.part + ((size_t)b * chunks + c) * outsz;
+    // Blocks with orthonormal columns: a tile inside one diagonal block is the identity
+    // (written here: 1 on the diagonal from chunk 0, 0 elsewhere); the remaining tiles
+    // are listed in order and shared out as usual.
+    __shared__ short s_tile[GDF_MAXTHR];
+    __shared__ int s_wcnt[GDF_MAXTHR / 32 + 1];
+    const bool compact = a.sym && a.colblk != nullptr;
+    if (compact) {
+        const int* blk = a.colblk + (size_t)b * a.ldcols;
+        bool need = false;
+        if (tid < ntiles) {
+            int bi, bj;
+            out_index(tid, nbA, nbB, true, bi, bj);
+            const int i0 = 2 * bi, j0 = 2 * bj, q = blk[i0];
+            const bool same = (i0 + 1 >= KA || blk[i0 + 1] == q) && blk[j0] == q && (j0 + 1 >= KA || blk[j0 + 1] == q);
+            need = !same;
+            if (same) {
+                for (int r = 0; r < 2; ++r)
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const int i = i0 + r, j = j0 + s2;
+                        if (i < KA && j < KA && i <= j)
+                            mypart[(size_t)i * a.maxKB + j] = (i == j && c == 0) ? 1.0 : 0.0;
+                    }
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, need);
+        const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int cw = s_wcnt[w];
+            off += (w < warp) ? cw : 0;
+            tot += cw;
+        }
+        if (need) s_tile[off + __popc(bal & ((1u << lane) - 1u))] = (short)tid;
+        ntiles = tot;
+        __syncthreads();
+    }
     const int P = ntiles > 0 ? max(1, nthr / ntiles) : 1;
     const int grp = ntiles > 0 ? tid / ntiles : P;
     const bool active = grp < P;
     int ti = 0, tj = 0;
     if (active) {
         int bi, bj;
-        out_index(tid - grp * ntiles, nbA, nbB, a.sym, bi, bj);
+        const int t = tid - grp * ntiles;
+        out_index(compact ? (int)s_tile[t] : t, nbA, nbB, a.sym, bi, bj);
         ti = 2 * bi;
         tj = 2 * bj;
     }
@@ -315,8 +356,6 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
             }
         }
     }
-    const size_t outsz = (size_t)a.maxKA * a.maxKB;
-    double* mypart = a.part + ((size_t)b * chunks + c) * outsz;
     if (active && grp == 0) {
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -837,7 +876,8 @@ cudaError_t launch_identity(double* M, int ld, long long ld_b, const int* m, int
 
 // ------------------------------------------------------------------------------------
 __global__ void assemble_cols_kernel(const void* const* bases, const int* const* cnt_ptrs, int nb,
-                                     long long Ng, int esize, const void** cols, int ld, int* K) {
+                                     long long Ng, int esize, const void** cols, int ld, int* K,
+                                     int* blk) {
     const int b = blockIdx.x;
     if (threadIdx.x != 0) return;
     int k = 0;
@@ -845,16 +885,19 @@ __global__ void assemble_cols_kernel(const void* const* bases, const int* const*
         const char* base = reinterpret_cast<const char*>(bases[(size_t)b * nb + j]);
         const int* cp = cnt_ptrs[(size_t)b * nb + j];
         const int c = (base && cp) ? *cp : 0;
-        for (int i = 0; i < c && k < ld; ++i) cols[(size_t)b * ld + k++] = base + (size_t)i * Ng * esize;
+        for (int i = 0; i < c && k < ld; ++i) {
+            if (blk) blk[(size_t)b * ld + k] = j;
+            cols[(size_t)b * ld + k++] = base + (size_t)i * Ng * esize;
+        }
     }
     K[b] = k;
 }
 
 cudaError_t launch_assemble_cols(const void* const* bases, const int* const* cnt_ptrs, int nb, int B,
-                                 long long Ng, int esize, const void** cols, int ld, int* K,
+                                 long long Ng, int esize, const void** cols, int ld, int* K, int* blk,
                                  cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
-    assemble_cols_kernel<<<B, 32, 0, st>>>(bases, cnt_ptrs, nb, Ng, esize, cols, ld, K);
+    assemble_cols_kernel<<<B, 32, 0, st>>>(bases, cnt_ptrs, nb, Ng, esize, cols, ld, K, blk);
     ++g_launch_count;
     return cudaGetLastError();
 }

@@ -259,6 +259,10 @@ struct GramArgs {
     long long ldG_b;          // batch stride
     double scaleB;            // unused (1.0)
     bool df;                  // FP64 operands in double-float arithmetic (FP32 mode)
+    // [B][ldcols] block index of each column, or null.  With sym and df, output tiles whose
+    // rows and columns all lie in one block are not computed but set to the identity: the
+    // caller asserts that every block has orthonormal columns (Cholesky-QR'd bases).
+    const int* colblk;
 };
 int gram_chunks(long long Ng);
 size_t gram_part_doubles(long long Ng, int B, int maxKA, int maxKB);
@@ -310,10 +314,11 @@ cudaError_t launch_chol_inv(const double* G, int ldG, long long ldG_b, const int
 
 // Fill column pointer arrays: for batch b, cols[b*ld + ...] = concatenation of nb blocks
 // (block j: base pointer bases[b*nb + j], count cnt[b*nb + j] read on the device,
-// column stride Ng elements of esize bytes); K[b] = total.
+// column stride Ng elements of esize bytes); K[b] = total; blk[b*ld + k] (if not null) =
+// the block of column k.
 cudaError_t launch_assemble_cols(const void* const* bases, const int* const* cnt_ptrs,
                                  int nb, int B, long long Ng, int esize, const void** cols,
-                                 int ld, int* K, cudaStream_t st);
+                                 int ld, int* K, int* blk, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------
 // Coarse sweep pieces (one subinterval, sequential in n).
