@@ -97,8 +97,9 @@ typedef struct pr_opts {
                                0: derive = 1e-14 (FP64) or 1e-9 (FP32)                   */
     int lin_maxit;          /* BiCGStab iteration cap per fine step; default 200         */
     double aug_tol;         /* no augmentation if ||d~|| <= aug_tol ||U||; default 1e-12  */
-    int group_ctas;         /* CTAs cooperating on one subinterval in the fine sweep;
-                               0: chosen from the SM count                               */
+    int group_ctas;         /* CTAs cooperating on one subinterval in the fine sweep (its
+                               tile-planes split evenly over them; capped at their count);
+                               0: every co-resident CTA slot over the subintervals        */
     int ctas_per_sm;        /* resident CTAs per SM for the fine sweep; 0: occupancy max  */
     long long spin_limit;   /* polls of an in-kernel barrier before PR_ERR_TIMEOUT
                                (default 1<<22, about a second)                            */
@@ -201,8 +202,9 @@ pr_status pr_coarse_sweep(pr_ctx* ctx, int k);
 pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count);
 
 /* Autotuner of the fine launch shape (no counterpart in the paper): times `steps` fine
- * steps of all n_sub subintervals from the current iterate for CTA-group sizes
- * G = (n / tile rows) * 2^j up to the co-resident CTA count, keeps the fastest in the
+ * steps of all n_sub subintervals from the current iterate for CTA-group sizes G = the
+ * co-resident CTA count / n_sub and G = (n / tile rows) * 2^j up to the co-resident CTA
+ * count, keeps the fastest in the
  * context (pr_opts.group_ctas) and returns it (best_ms: its time, may be NULL).  Needs
  * iteration 0 done and no phase of the next iteration started; leaves the iterate
  * unchanged.  Synchronises. */

@@ -1091,8 +1091,13 @@ pr_status pr_tune_fine(pr_ctx* c, int steps, int* best_group_ctas, double* best_
     const int B = c->N;
     double best = 1e300;
     int bestG = 0;
-    for (int z = 1; NY * z <= maxc && z <= c->n; z *= 2) {
-        c->o.group_ctas = NY * z;
+    // candidates: the even split of every CTA slot over the subintervals, then whole
+    // multiples of the y-block columns
+    std::vector<int> cand{std::max(1, maxc / B)};
+    for (int z = 1; NY * z <= maxc && z <= c->n; z *= 2)
+        if (NY * z != cand[0]) cand.push_back(NY * z);
+    for (int Gc : cand) {
+        c->o.group_ctas = Gc;
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
             PR_CUDA(cudaEventRecord(c->ev[0], c->st));

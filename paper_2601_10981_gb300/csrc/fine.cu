@@ -386,18 +386,11 @@ cudaError_t launch_fine(FineArgs a, bool fp32, int ctas_per_sm, int max_groups, 
     a.TY = geo.TY;
     a.RP = geo.RP;
     a.NY = n / a.TY;
-    // CTAs per subinterval: as many as fit beside the other active subintervals, a whole
-    // number of slabs per y-block column (one tile per CTA), at most one slab per plane
+    // CTAs per subinterval: as many as fit beside the other active subintervals (the
+    // tile-planes split evenly over any count), at most one tile-plane each
     int G = a.G;
     if (G <= 0) G = std::max(1, max_ctas / a.B);
-    G = std::min(G, max_ctas);
-    int NZ = std::max(1, std::min(n, G / a.NY));
-    if (G < a.NY) {
-        NZ = 1;             // fewer CTAs than y-blocks: several tiles per CTA
-    } else {
-        G = a.NY * NZ;
-    }
-    a.NZ = NZ;
+    G = std::min(std::min(G, max_ctas), a.NY * n);
     int groups = std::min(a.B, std::max(1, max_ctas / G));
     groups = std::min(groups, max_groups);
     a.G = G;

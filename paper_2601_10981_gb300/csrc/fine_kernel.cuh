@@ -51,13 +51,16 @@ enum FineMode { FINE_MODE_IMPLICIT = 0, FINE_MODE_IMPLICIT_TD = 1, FINE_MODE_RK4
 // ------------------------------------------------------------------------------------
 // Fine sweep kernel.
 //
-// Ownership: the n^3 points of a subinterval are cut into NY x NZ tiles of TY rows (y) by
-// a slab of planes (z); CTA q of a group owns a contiguous range of tiles.  Stencil
-// phases march a tile plane by plane through a shared-memory ring of planes: the operand
-// of the stencil (u, p or s) is computed once per plane, with one halo row on each side
-// in y, and the 6 neighbours of a point come from the ring (x +- 1 wraps inside the row,
-// z +- 1 from the adjacent slots).  Global traffic per point and phase is one load per
-// input vector (plus the 2/TY halo rows and 2/slab halo planes) and one store per output.
+// Ownership: the n^3 points of a subinterval are cut into NY columns of TY rows (y); a
+// column has n tile-planes (z).  The NY * n tile-planes, column by column, are split into
+// G contiguous ranges of equal length, one per CTA of the group, so any G balances the
+// work: a CTA owns the tail of one column and the head of the next, each a tile (y0, a
+// range of planes).  Stencil phases march a tile plane by plane through a shared-memory
+// ring of planes: the operand of the stencil (u, p or s) is computed once per plane, with
+// one halo row on each side in y, and the 6 neighbours of a point come from the ring
+// (x +- 1 wraps inside the row, z +- 1 from the adjacent slots).  Global traffic per point
+// and phase is one load per input vector (plus the 2/TY halo rows and the 2 halo planes of
+// each tile) and one store per output.
 
 // Per-thread partial sums in two levels: runs of 16 ticks accumulate in f, the runs in
 // s, both in KT.  The FP32 mode thus keeps its dot products off GB300's narrow FP64 pipe
@@ -155,13 +158,14 @@ __device__ __forceinline__ void group_sums(const double* part, int grid, int g0,
     __syncthreads();
 }
 
+// Tile t (= the y-block column t) of a CTA that owns tile-planes [p_lo, p_hi): rows
+// y0 .. y0 + TY - 1, planes zlo .. zhi - 1 (non-empty for p_lo / n <= t < ceil(p_hi / n)).
 struct TileGeom {
-    int n, TY, NY, NZ;
+    int n, TY, p_lo, p_hi;
     __device__ __forceinline__ void tile(int t, int& y0, int& zlo, int& zhi) const {
-        const int yb = t % NY, zs = t / NY;
-        y0 = yb * TY;
-        zlo = zs * n / NZ;
-        zhi = (zs + 1) * n / NZ;
+        y0 = t * TY;
+        zlo = max(p_lo - t * n, 0);
+        zhi = min(p_hi - t * n, n);
     }
 };
 
@@ -311,9 +315,10 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
     const int ty = active ? threadIdx.x / lanes : RP + a.TY + 2;
     const int x0 = lx * W;
     const int TY = a.TY, RW = a.TY + 2;
-    const TileGeom geo{n, a.TY, a.NY, a.NZ};
-    const int T = a.NY * a.NZ;
-    const int t_lo = T * q / G, t_hi = T * (q + 1) / G;
+    const int TPN = a.NY * n;   // tile-planes of a subinterval (G <= TPN)
+    const int p_lo = (int)((long long)TPN * q / G), p_hi = (int)((long long)TPN * (q + 1) / G);
+    const TileGeom geo{n, a.TY, p_lo, p_hi};
+    const int t_lo = p_lo / n, t_hi = (p_hi + n - 1) / n;
     const int xl = (x0 == 0) ? n - 1 : x0 - 1;   // left neighbour of the first point
     const int xr = (x0 + W == n) ? 0 : x0 + W;   // right neighbour of the last point
 
@@ -1350,9 +1355,13 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
 
 // ------------------------------------------------------------------------------------
 // Launch geometry.  W = 4 points per thread when n % 4 == 0, else 1.  A row has n/W
-// lanes; RP rows per pass of the CTA is the largest divisor of n with RP * n/W <= 256;
-// a tile has TY = KS * RP rows (KS in {1, 2}), its FINE_SLOTS-plane ring (8 bytes a point)
-// within 64 KB.
+// lanes.  CTAs of at most 128 threads (RP rows a pass, one owned row a thread) when the
+// tile keeps at least 8 rows: the kernel is latency-bound at 128 registers a thread, and
+// small CTAs (4 an SM) let the groups of a launch fill nearly every CTA slot (64^3, 64
+// subintervals: 9 CTAs a subinterval, 576 of 608 slots, where 256-thread CTAs fill 256 of
+// 304; the fine sweep 63.1 -> 58.3 ms).  Otherwise RP is the largest divisor of n with
+// RP * n/W <= 256 and a tile has TY = KS * RP rows (KS in {1, 2}), its FINE_SLOTS-plane
+// ring (8 bytes a point) within 64 KB.
 struct FineGeom {
     int W, lanes, RP, TY, KS, KF, threads;
     size_t smem;
@@ -1362,12 +1371,19 @@ inline FineGeom fine_geom(int n, bool fp32) {
     FineGeom g{};
     g.W = (n % 4 == 0) ? 4 : 1;
     g.lanes = n / g.W;
+    int rp128 = 1;
+    for (int rp = 1; rp <= n; ++rp)
+        if (n % rp == 0 && rp * g.lanes <= 128) rp128 = rp;
     g.RP = 1;
     for (int rp = 1; rp <= n; ++rp)
         if (n % rp == 0 && rp * g.lanes <= 256) g.RP = rp;
     g.KS = 1;
-    if (n % (2 * g.RP) == 0 && 2 * g.RP <= 16 && (size_t)FINE_SLOTS * (2 * g.RP + 2) * n * 8 <= 64 * 1024)
+    if (rp128 >= 8) {
+        g.RP = rp128;
+    } else if (n % (2 * g.RP) == 0 && 2 * g.RP <= 16 &&
+               (size_t)FINE_SLOTS * (2 * g.RP + 2) * n * 8 <= 64 * 1024) {
         g.KS = 2;
+    }
     g.TY = g.KS * g.RP;
     g.KF = (g.TY + 2 + g.RP - 1) / g.RP;
     g.threads = (g.lanes * g.RP + 31) / 32 * 32;   // whole warps (full-mask shuffles)

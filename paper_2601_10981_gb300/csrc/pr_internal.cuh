@@ -204,7 +204,7 @@ struct FineArgs {
     unsigned* bar;      // [numGroups][2]
     int G;              // CTAs per group
     int numGroups;
-    int TY, NY, NZ;     // tiles of a subinterval: NY blocks of TY rows x NZ slabs of planes
+    int TY, NY;         // a subinterval: NY columns of TY rows, n tile-planes each
     int RP;             // rows per pass of a CTA (threads = n/W lanes x RP, rounded to warps)
     long long spin_limit;
     int* err;           // launch-wide error code

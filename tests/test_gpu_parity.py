@@ -160,13 +160,41 @@ def test_fine_propagator_ragged_groups(gpu):
     w = pi.Workload("rag", n, pi.Flow("abc"), 0.05, 1.0, 8, 1e-3, m_cap=8)
     op = O.make_operator(w)
     u = np.stack([pi.initial_state(n, seed=40 + b) for b in range(B)])
-    for G in (1, 3, 7):
+    ref = None
+    # one 12-row column of 12 tile-planes: 1-2 planes a CTA, one each, more CTAs than planes
+    for G in (1, 3, 7, 12, 20):
         s = solver(bd, w, group_ctas=G)
+        if ref is None:
+            ref = {b: O.fine_propagate(op, u[b], 0.0, 5, s.dt_eff, tol=1e-14)[0] for b in (0, B - 1)}
         out, _ = s.op_fine(dev(torch, u), 5)
         out = out.cpu().numpy()
         for b in (0, B - 1):
-            ue, _ = O.fine_propagate(op, u[b], 0.0, 5, s.dt_eff, tol=1e-14)
-            assert rel(out[b], ue) < TOL64
+            assert rel(out[b], ref[b]) < TOL64, (G, b)
+        s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fine_propagator_tiles_across_columns(gpu, prec):
+    # n = 32: two 16-row columns of 32 tile-planes each; G = 3, 5, 7 give CTAs whose
+    # planes run from the end of the first column into the second
+    bd, torch = gpu
+    n, B = 32, 3
+    w = pi.Workload("cols", n, pi.Flow("kolmogorov", k=2), 0.02, 1.0, 8, 1e-3, m_cap=8, f_seed=5)
+    op = O.make_operator(w)
+    u = np.stack([pi.initial_state(n, seed=60 + b) for b in range(B)])
+    tol = TOL64 if prec == 0 else TOL32
+    ref = None
+    for G in (3, 5, 7):
+        s = solver(bd, w, group_ctas=G, precision=prec)
+        s.set_initial(u[0], w.f())
+        if ref is None:
+            ref = [O.fine_propagate(op, u[b], 0.0, 6, s.dt_eff, 2, 3, tol=1e-14) for b in range(B)]
+        out, snap = s.op_fine(dev(torch, u), 6, 2, 3)
+        out, snap = out.cpu().numpy(), snap.cpu().numpy()
+        for b in range(B):
+            assert rel(out[b], ref[b][0]) < tol, (G, b, rel(out[b], ref[b][0]))
+            assert rel(snap[b, 2], ref[b][1][:, 2]) < tol, (G, b)
+        s.close()
 
 
 # ---------------------------------------------------------------------- POD
