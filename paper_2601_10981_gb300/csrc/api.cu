@@ -1210,7 +1210,6 @@ static CoarseSweepArgs coarse_args(pr_ctx* c) {
     a.Lc = c->Lc;
     a.aug_tol = c->o.aug_tol;
     a.augment = 1;
-    a.df = c->fp32 ? 1 : 0;
     a.d = c->cd;
     a.Ld = c->cLd;
     a.Ltd = c->cLtd;

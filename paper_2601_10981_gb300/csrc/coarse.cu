@@ -21,7 +21,6 @@
 // the partials of all CTAs in CTA order, so all CTAs hold bit-identical values and the
 // result does not depend on scheduling.  Each dot product over the basis is taken by one
 // warp per column with coalesced reads of the column.
-#include "df.cuh"
 #include "pr_internal.cuh"
 
 #include <algorithm>
@@ -150,7 +149,6 @@ struct CswShared {
     double c0, c1;
     double red[CSW_WARPS * 3];
     double g[CSW_MAXK];
-    float cfh[CSW_MAXK], cfl[CSW_MAXK];   // coefficients split for the double-float loops
     double A[CSW_MAXK * CSW_LDA];
     double prow[CSW_LDA];
     double mult[CSW_MAXK];
@@ -202,59 +200,6 @@ __device__ __forceinline__ void csw_dots(const double* R, long long Ng, int m, c
         }
         double a0 = (s0[0] + s0[1]) + (s0[2] + s0[3]);
         double a1 = (s1[0] + s1[1]) + (s1[2] + s1[3]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, off);
-            a1 += __shfl_down_sync(0xffffffffu, a1, off);
-        }
-        if (lane == 0) {
-            part[(size_t)(q0 + i) * G + blockIdx.x] = a0;
-            if (x1) part[(size_t)(q1 + i) * G + blockIdx.x] = a1;
-        }
-    }
-}
-
-// csw_dots in double-float arithmetic (the FP32 mode): the FP64 operands are split into
-// float pairs by bit moves, each product accumulated error-free (df_mac) in two chains a
-// lane, folded into FP64 every 16 products; ~1e-14 relative, and the FP64 pipe, which
-// GB300 issues at 1/64 of the FP32 rate, only adds the folds.
-__device__ __forceinline__ void csw_dots_df(const double* R, long long Ng, int m, const double* x0,
-                                            int q0, const double* x1, int q1, long long lo, long long hi,
-                                            double* part, int G) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < m; i += CSW_WARPS) {
-        const double* r = R + (size_t)i * Ng;
-        float h0[2] = {0.f, 0.f}, l0[2] = {0.f, 0.f}, h1[2] = {0.f, 0.f}, l1[2] = {0.f, 0.f};
-        double a0 = 0.0, a1 = 0.0;
-        auto mac = [&](long long p, int u) {
-            const float2 rv = d2df_bits(r[p]);
-            const float2 xv = d2df_bits(x0[p]);
-            df_mac(h0[u], l0[u], rv.x, rv.y, xv.x, xv.y);
-            if (x1) {
-                const float2 yv = d2df_bits(x1[p]);
-                df_mac(h1[u], l1[u], rv.x, rv.y, yv.x, yv.y);
-            }
-        };
-        auto fold = [&]() {
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                a0 += df_to_double(h0[u], l0[u]);
-                a1 += df_to_double(h1[u], l1[u]);
-                h0[u] = l0[u] = h1[u] = l1[u] = 0.f;
-            }
-        };
-        long long p = lo + lane;
-        int cnt = 0;
-        for (; p + 32 < hi; p += 64) {
-            mac(p, 0);
-            mac(p + 32, 1);
-            if (++cnt == 16) {
-                fold();
-                cnt = 0;
-            }
-        }
-        if (p < hi) mac(p, 0);
-        fold();
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             a0 += __shfl_down_sync(0xffffffffu, a0, off);
@@ -507,19 +452,6 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
     const long long n2 = (long long)n_ * n_;
     const int n2i = n_ * n_;
     const double inv2h = 0.5 / a.g.h, epsh2 = a.g.eps / (a.g.h * a.g.h);
-    auto dots = [&](const double* Rb, int m, const double* x0, int q0, const double* x1, int q1) {
-        if (a.df) csw_dots_df(Rb, Ng, m, x0, q0, x1, q1, lo, hi, part(), G);
-        else csw_dots(Rb, Ng, m, x0, q0, x1, q1, lo, hi, part(), G);
-    };
-    // split the FP64 coefficients c[0..m-1] for the double-float loops
-    auto split_coeffs = [&](const double* c, int m) {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const float2 s2 = d2df_bits(c[i]);
-            sh.cfh[i] = s2.x;
-            sh.cfl[i] = s2.y;
-        }
-        __syncthreads();
-    };
 
     for (int t = 0; t < a.count; ++t) {
         const long long n = a.n0 + t;
@@ -541,7 +473,7 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             double v[1] = {0.0};
             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) v[0] += U[p] * U[p];
             csw_block_sums(v, 1, sh, part() + (size_t)(2 * m) * G, G);
-            dots(R, m, U, 0, Up, m);
+            csw_dots(R, Ng, m, U, 0, Up, m, lo, hi, part(), G);
             if (!barrier()) return;
             csw_reduce(part(), 2 * m + 1, G, [&](int q, double s) {
                 if (q < m) sh.RU[q] = s;
@@ -573,29 +505,17 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
         //         rounding leaves in span R (at most ~eps ||U|| / ||d~|| of d~ / ||d~||).
         {
             double v[2] = {0.0, 0.0};
-            if (a.df) split_coeffs(sh.RU, m);
             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
                 const double u = U[p];
-                double d;
-                if (a.df) {
-                    // R (R^T U) in double-float, subtracted from U in FP64
-                    float ah = 0.f, al = 0.f;
-                    for (int i = 0; i < m; ++i) {
-                        const float2 rv = d2df_bits(R[(size_t)i * Ng + p]);
-                        df_mac(ah, al, rv.x, rv.y, sh.cfh[i], sh.cfl[i]);
-                    }
-                    d = u - df_to_double(ah, al);
-                } else {
-                    d = u;
-                    for (int i = 0; i < m; ++i) d -= sh.RU[i] * R[(size_t)i * Ng + p];
-                }
+                double d = u;
+                for (int i = 0; i < m; ++i) d -= sh.RU[i] * R[(size_t)i * Ng + p];
                 a.d[p] = d;
                 v[0] += d * d;
                 v[1] += d * (u - Up[p]);
             }
             csw_block_sums(v, 2, sh, part() + (size_t)m * G, G);
             __syncthreads();
-            dots(R, m, a.d, 0, nullptr, 0);
+            csw_dots(R, Ng, m, a.d, 0, nullptr, 0, lo, hi, part(), G);
             if (!barrier()) return;
             csw_reduce(part(), m + 2, G, [&](int q, double s) {
                 if (q < m) sh.RD[q] = s;
@@ -640,8 +560,8 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             }
             csw_block_sums(v, 3, sh, part() + (size_t)(3 * m) * G, G);
             __syncthreads();
-            dots(R, m, a.Ld, 0, a.Ltd, m);
-            dots(R, m, a.A1d, 2 * m, nullptr, 0);
+            csw_dots(R, Ng, m, a.Ld, 0, a.Ltd, m, lo, hi, part(), G);
+            csw_dots(R, Ng, m, a.A1d, 2 * m, nullptr, 0, lo, hi, part(), G);
             if (!barrier()) return;
             csw_reduce(part(), 3 * m + 3, G, [&](int q, double s) {
                 if (q < m) sh.RPD[q] = s;
@@ -697,7 +617,7 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
             }
             csw_block_sums(v, 1, sh, part() + (size_t)(2 * m) * G, G);
             __syncthreads();
-            dots(R, m, a.Ld, 0, a.Ltd, m);
+            csw_dots(R, Ng, m, a.Ld, 0, a.Ltd, m, lo, hi, part(), G);
             if (!barrier()) return;
             csw_reduce(part(), 2 * m + 1, G, [&](int q, double s) {
                 if (q < m) sh.RL[q] = s;
@@ -709,22 +629,10 @@ __global__ void __launch_bounds__(CSW_THREADS, 1) coarse_sweep_kernel(CoarseSwee
         // ---- E: reduced solve ; F: U^k_{n+1} = F_n + R g + d~ g_d
         if (a.tdep) csw_small_tdep(sh, a, m, Mr, Lr, t_n);
         else csw_small(sh, a, m, Mr, Lr);
-        if (a.df) {
-            split_coeffs(sh.g, m);
-            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                float ah = 0.f, al = 0.f;
-                for (int i = 0; i < m; ++i) {
-                    const float2 rv = d2df_bits(R[(size_t)i * Ng + p]);
-                    df_mac(ah, al, rv.x, rv.y, sh.cfh[i], sh.cfl[i]);
-                }
-                out[p] = F[p] + a.d[p] * sh.g[m] + df_to_double(ah, al);
-            }
-        } else {
-            for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                double s = F[p] + a.d[p] * sh.g[m];
-                for (int i = 0; i < m; ++i) s += R[(size_t)i * Ng + p] * sh.g[i];
-                out[p] = s;
-            }
+        for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+            double s = F[p] + a.d[p] * sh.g[m];
+            for (int i = 0; i < m; ++i) s += R[(size_t)i * Ng + p] * sh.g[i];
+            out[p] = s;
         }
         // out is read back at the same points by the same threads (next stage A) and by
         // other threads of this CTA only after the __syncthreads in csw_block_sums

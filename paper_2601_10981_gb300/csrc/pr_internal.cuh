@@ -353,8 +353,6 @@ struct CoarseSweepArgs {
     int Lc;
     double aug_tol;
     int augment;            // 0: plain coarse space R (no d~ stages, no augmentation)
-    int df;                 // FP32 mode: the projections on R and the combinations of R's
-                            // columns in double-float arithmetic on the FP32 pipe
     double* d;              // scratch [Ng] each
     double* Ld;
     double* Ltd;
