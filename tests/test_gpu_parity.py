@@ -259,6 +259,35 @@ def test_pod_mode_wide_snapshot_matrices(gpu):
             s.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_level2_pod_of_gpu_level1_bases(gpu, prec):
+    # Algorithm 1 on the window eq. (W^k_n) of the GPU's own level-1 bases (k = 1: the left
+    # neighbour, this subinterval and V0).  The FP32 mode takes the window's diagonal Gram
+    # blocks as the identity (the blocks are Cholesky-QR'd bases): the span must still be
+    # the oracle's to the Davis-Kahan bound of a ~1e-14 relative Gram error.
+    bd, torch = gpu
+    w = pi.tiny(n=12, n_sub=5, flow=pi.Flow("kolmogorov", k=2), f_seed=3, T=0.1)
+    prm = O.derive_params(w)
+    s = solver(bd, w, precision=prec)
+    s.set_initial(w.u0(), w.f())
+    s.iteration0()
+    s.fine_sweep(1)
+    s.pod_update(1)
+    V0 = s.basis(0).T
+    level1 = {nn: s.basis(1, nn).T for nn in range(w.n_sub)}
+    for n in range(1, w.n_sub):
+        blocks = O.level2_blocks(lambda kk, nn: level1.get(nn) if kk == 1 else None, 1, n, prm.m_l, prm.p, V0)
+        W2 = np.concatenate(blocks, axis=1)
+        Ro, mo, lam = O.pod_mode(W2, prm.gamma3, prm.m_cap, prm.tau)
+        Rg = s.basis(2, n).T
+        assert Rg.shape[1] == mo, (n, Rg.shape, mo)
+        tol = davis_kahan_tol(lam, mo, 1.1e-16 if prec == 0 else 1e-14)
+        assert span_dist(Rg, Ro) < tol, (n, span_dist(Rg, Ro), tol)
+        # orthonormal to the precision the identity-mass reading of the FP32 mode needs
+        assert np.abs(Rg.T @ Rg - np.eye(mo)).max() < 1e-12
+    s.close()
+
+
 # ---------------------------------------------------------------------- coarse update
 @pytest.mark.parametrize("m,prec", [(0, 0), (3, 0), (7, 0), (3, 1), (7, 1)])
 def test_coarse_update_matches_oracle(gpu, m, prec):
