@@ -149,21 +149,24 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_kernel(GramArgs a, long lon
 // snapshots runs at the FP64 rate (1/64 of FP32 on GB300); here each staged value is
 // split into a float pair (d2df_bits) and every product-sum is an error-free df_mac2 on
 // the FP32 pipe, two rows per packed instruction.  Row partials fold into a df
-// accumulator about every 64 rows, so the chunk sums keep ~1e-15 relative accuracy (the
+// accumulator every SUB rows (64 or 128), so the chunk sums keep ~1e-15 relative accuracy (the
 // POD needs the Gram to ~1e-13 of its norm).
-//   load      cp.async of the next block of GDF_SUB rows of every column (raw FP64)
+//   load      cp.async of the next block of SUB rows of every column (raw FP64)
 //             while the current block is reduced
 //   convert   raw -> column-major float planes hi, lo (quads of four rows XOR-swizzled by
 //             column so that the 16-byte reads of neighbouring tiles hit different banks)
 //   compute   one thread per 2 x 2 output tile and row group: the CTA has ntiles x P
 //             threads, group g takes the row quads g, g + P, ...; the groups' FP64 sums
 //             meet in shared memory at the end of the chunk.
-constexpr int GDF_SUB = 64;              // rows per staged block (16 quads)
-constexpr int GDF_LDP = GDF_SUB + 4;     // floats per staged column plane
+// SUB rows per staged block: 128 for CTAs of 256 threads or more, 64 below (measured on
+// the 64^3 workload: CholQR Grams 1.12 -> 0.88 and 1.48 -> 1.33 ms, Galerkin 2.53 -> 2.38,
+// level-2 2.37 -> 2.25 with 128 rows; the 160-thread level-1 Gram 6.83 with 64, 7.00 with
+// 128); a column plane holds SUB + 4 floats.
 constexpr int GDF_MAXTHR = 384;
 
+template <int SUB>
 __device__ __forceinline__ int gdf_pos(int col, int r) {
-    return col * GDF_LDP + ((((r >> 2) ^ ((col >> 3) & 1)) << 2) | (r & 3));
+    return col * (SUB + 4) + ((((r >> 2) ^ ((col >> 3) & 1)) << 2) | (r & 3));
 }
 __host__ __device__ __forceinline__ int gdf_cols(int K) { return (K + 1) & ~1; }
 __host__ __device__ __forceinline__ int gdf_tiles(int KA, int KB, bool sym) {
@@ -179,7 +182,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+template <int SUB>
 __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long long CH, int chunks) {
+    constexpr int GDF_SUB = SUB, GDF_LDP = SUB + 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int b = blockIdx.y, c = blockIdx.x;
@@ -269,7 +274,7 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
         for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
             const int col = e / GDF_SUB, r = e - col * GDF_SUB;
             const float2 v = d2df_bits(raw[e]);
-            const int o = gdf_pos(col, r);
+            const int o = gdf_pos<SUB>(col, r);
             dst[o] = v.x;
             dst[pl + o] = v.y;
         }
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
                 }
             }
         }
-        if (++nblk == P) {   // ~64 rows a thread since the last fold
+        if (++nblk == P) {   // SUB rows a thread since the last fold
 #pragma unroll
             for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -377,9 +382,9 @@ static int gram_df_threads(const GramArgs& a) {
     return (tiles * P + 31) / 32 * 32;
 }
 // Shared memory of gram_df_kernel: raw blocks and float planes, at least the group sums.
-static size_t gram_df_smem(const GramArgs& a, int threads) {
+static size_t gram_df_smem(const GramArgs& a, int threads, int sub) {
     const size_t cols = (size_t)gdf_cols(a.maxKA) + (a.sym ? 0 : gdf_cols(a.maxKB));
-    const size_t stage = cols * GDF_SUB * sizeof(double) + cols * 2 * GDF_LDP * sizeof(float);
+    const size_t stage = cols * sub * sizeof(double) + cols * 2 * (sub + 4) * sizeof(float);
     const size_t sums = (size_t)threads * 4 * sizeof(double);
     return std::max(stage, sums);
 }
@@ -411,14 +416,22 @@ cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t 
     if (a.B <= 0 || a.maxKA <= 0 || (!a.sym && a.maxKB <= 0)) return cudaSuccess;
     if (a.df && !a_f32 && !b_f32) {
         const int thr = gram_df_threads(a);
-        const size_t smem = thr > 0 ? gram_df_smem(a, thr) : 0;
+        int sub = thr >= 256 ? 128 : 64;
+        size_t smem = thr > 0 ? gram_df_smem(a, thr, sub) : 0;
+        if (smem > 160 * 1024 && sub == 128) {
+            sub = 64;
+            smem = gram_df_smem(a, thr, sub);
+        }
         if (thr > 0 && smem <= 160 * 1024) {
             const int chunks = gram_chunks(a.Ng);
             const long long CH = gram_chunk_len(a.Ng);
+            const void* fn = sub == 128 ? (const void*)gram_df_kernel<128> : (const void*)gram_df_kernel<64>;
             if (smem > 48 * 1024)
-                cudaFuncSetAttribute((const void*)gram_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            gram_df_kernel<<<dim3(chunks, a.B), thr, smem, st>>>(a, CH, chunks);
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (sub == 128)
+                gram_df_kernel<128><<<dim3(chunks, a.B), thr, smem, st>>>(a, CH, chunks);
+            else
+                gram_df_kernel<64><<<dim3(chunks, a.B), thr, smem, st>>>(a, CH, chunks);
             ++g_launch_count;
             return cudaGetLastError();
         }
