@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_kernel(GramArgs a, long lon
 //             meet in shared memory at the end of the chunk.
 // SUB rows per staged block: 128 for CTAs of 256 threads or more, 64 below (measured on
 // the 64^3 workload: CholQR Grams 1.12 -> 0.88 and 1.48 -> 1.33 ms, Galerkin 2.53 -> 2.38,
-// level-2 2.37 -> 2.25 with 128 rows; the 160-thread level-1 Gram 6.83 with 64, 7.00 with
-// 128); a column plane holds SUB + 4 floats.
+// level-2 2.37 -> 2.25 with 128 rows; a 160-thread level-1 Gram took 6.83 ms with 64 rows
+// and 7.00 with 128); a column plane holds SUB + 4 floats.
 constexpr int GDF_MAXTHR = 384;
 
 template <int SUB>
@@ -374,11 +374,13 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
 }
 
 // Threads of gram_df_kernel: every tile of the largest batch item once, times the row
-// groups that fit in 256 threads; 0 when the df kernel does not apply.
+// groups that fit in 256 threads, or two groups when one would leave a single group and
+// two still fit the launch bound (128 < tiles <= 192: the 33-column level-1 Gram, 6.83 ->
+// 6.60 ms on the 64^3 workload); 0 when the df kernel does not apply.
 static int gram_df_threads(const GramArgs& a) {
     const int tiles = gdf_tiles(a.maxKA, a.maxKB, a.sym);
     if (tiles <= 0 || tiles > GDF_MAXTHR) return 0;
-    const int P = std::max(1, 256 / tiles);
+    const int P = (tiles > 128 && 2 * tiles <= GDF_MAXTHR) ? 2 : std::max(1, 256 / tiles);
     return (tiles * P + 31) / 32 * 32;
 }
 // Shared memory of gram_df_kernel: raw blocks and float planes, at least the group sums.
