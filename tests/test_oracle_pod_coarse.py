@@ -151,3 +151,29 @@ def test_coarse_propagator_invariant_to_basis_rotation():
     a, _ = coarse_propagate(op, V, x, 0.0, 4, 0.02)
     b, _ = coarse_propagate(op, V @ Q, x, 0.0, 4, 0.02)
     assert np.linalg.norm(a - b) < 1e-13 * np.linalg.norm(a)
+
+
+def test_augmented_coarse_propagator_independent_of_gram_schmidt_passes():
+    # Reading R11: G in V = [R, d~ / ||d~||] depends only on span{R, U}, so one
+    # Gram-Schmidt pass (the CUDA sweep) and two (the oracle's augment) give the same G to
+    # rounding, the mass matrix V^T V absorbing what one pass leaves in span R.  Also for
+    # a basis that is orthonormal only to ~1e-9 and for U close to span R.
+    g = O.Grid(8)
+    op = Operator(g, Flow("abc"), 0.03, forcing(8, seed=2))
+    R, _ = np.linalg.qr(rng(14).standard_normal((512, 5)))
+    for noise, near in ((0.0, 1.0), (1e-9, 1.0), (0.0, 1e-6)):
+        Rn = R + noise * rng(15).standard_normal(R.shape)
+        U = Rn @ rng(16).standard_normal(5) + near * rng(17).standard_normal(512)
+        V2, augd = augment(Rn, U)
+        assert augd
+        d1 = U - Rn @ (Rn.T @ U)
+        V1 = np.concatenate([Rn, (d1 / np.linalg.norm(d1))[:, None]], axis=1)
+        a, _ = coarse_propagate(op, V2, U, 0.1, 6, 0.02)
+        b, _ = coarse_propagate(op, V1, U, 0.1, 6, 0.02)
+        assert np.linalg.norm(a - b) < 1e-11 * np.linalg.norm(a), (noise, near)
+        # a different direction (d~ of another vector) does change G
+        w = rng(18).standard_normal(512)
+        dw = w - Rn @ (Rn.T @ w)
+        e, _ = coarse_propagate(op, np.concatenate([Rn, (dw / np.linalg.norm(dw))[:, None]], axis=1), U, 0.1,
+                                6, 0.02)
+        assert np.linalg.norm(e - a) > 1e-6 * np.linalg.norm(a)
