@@ -1,16 +1,24 @@
 """Benchmark of the adaptive-parareal hot path on GB300.
 
-Workload: Kolmogorov flow b = (sin 4y, 0, 0), eps = 0.01, 64^3 periodic grid, T = 10,
-N = 64 subintervals of 157 fine implicit-Euler steps (dt = 9.952e-4), 32 snapshots per
-window, POD rank <= 16, seeded smooth forcing |k| <= 4 (synthetic inputs, see pr_inputs).
+Default workload (--config c2): Kolmogorov flow b = (sin 4y, 0, 0), eps = 0.01, 64^3
+periodic grid, T = 10, N = 64 subintervals of 157 fine implicit-Euler steps
+(dt = 9.952e-4), 32 snapshots per window, POD rank <= 16, seeded smooth forcing |k| <= 4
+(synthetic inputs, see pr_inputs).  --config c3 / c4 select the 128^3 ABC and the 256^3
+perturbed-Kolmogorov workloads.
 
-A step is one parareal iteration over all 64 subintervals: the fine sweep (one persistent
+A step is one parareal iteration over all subintervals: the fine sweep (one persistent
 launch), level-1 and level-2 POD with Galerkin matrices, the sequential augmented coarse
 sweep and the convergence check.  value = fine grid-point-steps propagated per second of
-whole-iteration time (GDOF-steps/s).
+whole-iteration time (GDOF-steps/s), in the precision of --precision (default: the FP32
+Krylov mode).  Beside it, on rank 0 (--extras 1): the same iteration in FP64
+(fp64_iteration), the wall time of pr_solve to rel. L2 <= 1e-6 against the sequential
+fine solution in both modes (solve_fp32, solve_fp64; the plain FP64 GPU parareal is the
+comparison the mixed-precision mode is measured against), the sequential fine solution
+on the GPU in both precisions (the cost_seq form), and the FP64 CPU oracle on real
+subinterval blocks, single-threaded and on all host cores (cpu_baseline).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
-    python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--config c2]
+    python bench.py --impl reference      # the FP64 CPU oracle on bounded samples
 """
 from __future__ import annotations
 
@@ -32,26 +40,38 @@ UNIT = "GDOF-steps/s"
 FINE_SRC = os.path.join(ROOT, "paper_2601_10981_gb300", "csrc", "fine_kernel.cuh")
 
 
-def workload(subintervals: int = 0):
-    """The 64^3 Kolmogorov workload; `subintervals` > 0 keeps DeltaT (and so the 157 fine
-    steps per subinterval) and shortens the horizon, for small profiling captures."""
+CONFIGS = {
+    "c2": ("kolmogorov4_64_eps0.01_N64",
+           "Kolmogorov sin(4y), eps=0.01, 64^3, T=10, N=64 subintervals x 157 fine steps, "
+           "32 snapshots/window, POD rank<=16, seeded forcing |k|<=4"),
+    "c3": ("abc128_eps0.005_N256",
+           "ABC (1,1,1), eps=0.005, 128^3 (2,097,152 points, the paper's DOF count), T=50, "
+           "N=256 subintervals x 391 fine steps, 64 snapshots/window, POD rank<=32"),
+    "c4": ("kolmogorov8_256_pert_eps0.002_N128",
+           "Kolmogorov sin(8y) + seeded divergence-free perturbation 0.05, eps=0.002, 256^3, T=20, "
+           "N=128 subintervals x 625 fine steps, 16 snapshots/window, POD rank<=8"),
+}
+
+
+def workload(config: str = "c2", subintervals: int = 0):
+    """The named workload; `subintervals` > 0 keeps DeltaT (and so the fine steps per
+    subinterval) and shortens the horizon, for small profiling captures."""
     import dataclasses
     import pr_inputs as pi
-    w = pi.KOL_64
+    w = pi.WORKLOADS[CONFIGS[config][0]]
     if subintervals > 0 and subintervals != w.n_sub:
         w = dataclasses.replace(w, name=f"{w.name}_first{subintervals}", n_sub=subintervals,
                                 T=w.T * subintervals / w.n_sub)
     return w
 
 
-def config_dict(w, precision):
+def config_dict(w, precision, config: str = "c2"):
     return {
-        "workload": f"{w.name}: Kolmogorov sin(4y), eps=0.01, 64^3, T=10, N=64 subintervals x 157 "
-                    f"fine steps, 32 snapshots/window, POD rank<=16, seeded forcing |k|<=4",
+        "workload": f"{w.name}: {CONFIGS[config][1]}",
         "precision": "fp32-delta fine, fp64 state/reduced" if precision == "fp32" else "fp64",
-        "step": "one parareal iteration k=1 over all 64 subintervals: fine sweep + level-1/2 POD "
-                "+ Galerkin + sequential coarse sweep + convergence check",
-        "l2": "no flush; working set ~9 GB (snapshots, bases, states) >> 129 MB L2",
+        "step": f"one parareal iteration k=1 over all {w.n_sub} subintervals: fine sweep + level-1/2 "
+                "POD + Galerkin + sequential coarse sweep + convergence check",
+        "l2": "no flush; working set (snapshots, bases, states) of several GB >> 129 MB L2",
     }
 
 
@@ -154,82 +174,174 @@ def dist_setup():
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-CPU_SAMPLE_CODE = r"""
-import json, sys, time
-sys.path.insert(0, sys.argv[1])
-import numpy as np
-import oracle as O
-import pr_inputs as pi
-w = pi.KOL_64
-prm = O.derive_params(w)
-op = O.make_operator(w)
-u = w.u0()
-fine_steps = int(sys.argv[2])
-t = time.perf_counter()
-_, W = O.fine_propagate(op, u, prm.T0, fine_steps, prm.dt, 1, fine_steps + 1, tol=prm.lin_tol)
-t_step = (time.perf_counter() - t) / fine_steps
-Wfull = np.concatenate([W] * ((prm.n_s + W.shape[1] - 1) // W.shape[1]), axis=1)[:, :prm.n_s]
-Wfull = Wfull + 1e-3 * np.random.default_rng(0).standard_normal(Wfull.shape)
-t = time.perf_counter()
-R1, m1, _ = O.pod_mode(Wfull, prm.gamma2, prm.m_cap, prm.tau)
-t_pod1 = time.perf_counter() - t
-t = time.perf_counter()
-R2, m2, _ = O.pod_mode(np.concatenate([R1, R1[:, ::-1], R1 * 0.5 + 1e-3], axis=1), prm.gamma3, prm.m_cap, prm.tau)
-t_pod2 = time.perf_counter() - t
-t = time.perf_counter()
-V, _ = O.augment(R2, u)
-a, _ = O.coarse_propagate(op, V, u, prm.T0, prm.Lc, prm.dT)
-b, _ = O.coarse_propagate(op, V, u, prm.T0, prm.Lc, prm.dT)
-t_coarse = time.perf_counter() - t
-t_iter = prm.N * (prm.S * t_step + t_pod1 + t_pod2 + t_coarse)
-dofs = prm.N * prm.S * w.Ng
-print(json.dumps(dict(t_step=t_step, t_pod1=t_pod1, t_pod2=t_pod2, t_coarse=t_coarse,
-                      t_iter=t_iter, value=dofs / t_iter / 1e9, fine_steps=fine_steps)))
-"""
+# The oracle legs run the FP64 numpy oracle on real blocks of the workload: iteration 0 once
+# (untimed), then, per sample, the fine propagator with snapshots and the level-1 POD of a
+# block of consecutive subintervals (one process per subinterval, all host cores), the
+# level-2 POD of each subinterval's real neighbours and the sequential augmented coarse
+# updates of the block, i.e. one parareal iteration restricted to the block.
+
+def _oracle_threads_env():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
 
 
-def cpu_oracle_sample(fine_steps: int = 4):
-    """Time the FP64 oracle, single-threaded, on a bounded sample of the workload and scale
-    it to one parareal iteration over all 64 subintervals."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    t0 = time.time()
-    r = subprocess.run([sys.executable, "-c", CPU_SAMPLE_CODE, ROOT, str(fine_steps)],
-                       capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    d["wall"] = time.time() - t0
-    return d
+def _oracle_fine_pod(args):
+    """Worker: the fine propagator with snapshots over the first `steps` fine steps of
+    subinterval n_idx, then POD_Mode of that window (level 1)."""
+    wname, n_idx, u_start, steps = args
+    import oracle as O
+    w = _workload_by_name(wname)
+    prm = O.derive_params(w)
+    op = O.make_operator(w)
+    t = time.perf_counter()
+    F, W = O.fine_propagate(op, u_start, prm.T0 + n_idx * prm.DeltaT, steps, prm.dt, prm.dM,
+                            steps // prm.dM + 1, tol=prm.lin_tol)
+    t_f = time.perf_counter() - t
+    t = time.perf_counter()
+    R1, m1, _ = O.pod_mode(W, prm.gamma2, prm.m_cap, prm.tau)
+    return n_idx, F, R1, m1, t_f, time.perf_counter() - t
 
 
-def cpu_baseline_obj(d):
-    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"64^3 FP64 numpy oracle, 1 thread: {d['fine_steps']} fine implicit-Euler "
-                       f"steps (BiCGStab) + one level-1 POD (32 snapshots) + one level-2 POD + one "
-                       f"augmented coarse update, scaled to one iteration over 64 subintervals x "
-                       f"157 steps (measured {d['wall']:.1f} s)")}
+def _workload_by_name(name):
+    import pr_inputs as pi
+    return pi.WORKLOADS[name]
+
+
+class OracleBlocks:
+    """Iteration 1 of the oracle restricted to blocks of B consecutive subintervals, each
+    propagated over the first 1/frac of its window (a bounded sample)."""
+
+    def __init__(self, w, frac: int = 4):
+        import oracle as O
+        self.O, self.w = O, w
+        self.prm = O.derive_params(w)
+        self.op = O.make_operator(w)
+        self.steps = max(2 * self.prm.dM, self.prm.S // frac)
+        t = time.perf_counter()
+        self.U0, self.V0, _ = O.iteration0(w, self.prm, self.op)
+        self.t_setup = time.perf_counter() - t
+
+    def step(self, b0: int, B: int, pool=None):
+        import numpy as np
+        O, prm = self.O, self.prm
+        N = prm.N
+        idx = [(b0 + i) % N for i in range(B)]
+        t0 = time.perf_counter()
+        tasks = [(self.w.name, n, self.U0[n], self.steps) for n in idx]
+        res = pool.map(_oracle_fine_pod, tasks) if pool is not None else list(map(_oracle_fine_pod, tasks))
+        t_par = time.perf_counter() - t0
+        F = {r[0]: r[1] for r in res}
+        R1 = {r[0]: r[2] for r in res}
+        # level-2 POD of eq. (W^k_n) at k = 1 from the block's real neighbours (the missing
+        # previous-iteration block is V0, reading R8), then the sequential coarse updates
+        t = time.perf_counter()
+        shape = self.U0[0].shape
+        U = F[idx[0]]
+        for j in range(1, B):
+            n, left = idx[j], idx[j - 1]
+            R2, _, _ = O.pod_mode(np.concatenate([R1[left], R1[n], self.V0], axis=1), prm.gamma3,
+                                  prm.m_cap, prm.tau)
+            V, _ = O.augment(R2, U, prm.aug_tol)
+            t_n = prm.T0 + n * prm.DeltaT
+            g_new, _ = O.coarse_propagate(self.op, V, U, t_n, prm.Lc, prm.dT)
+            g_old, _ = O.coarse_propagate(self.op, V, self.U0[n], t_n, prm.Lc, prm.dT)
+            U = (g_new + F[n].reshape(-1) - g_old).reshape(shape)
+        t_seq = time.perf_counter() - t
+        wall = time.perf_counter() - t0
+        dofs = B * self.steps * self.w.Ng
+        return {"wall_s": wall, "value": dofs / wall / 1e9, "subintervals": B,
+                "fine_steps_each": self.steps, "t_parallel_s": t_par, "t_sequential_s": t_seq,
+                "t_fine_mean_s": sum(r[4] for r in res) / B, "t_pod1_mean_s": sum(r[5] for r in res) / B}
+
+
+def oracle_pool(workers: int):
+    """Process pool for the oracle (spawn: safe after CUDA initialisation)."""
+    import multiprocessing as mp
+    _oracle_threads_env()
+    return mp.get_context("spawn").Pool(workers)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_measure(w):
+    """The oracle on real blocks of the workload: single-threaded (two consecutive
+    subintervals, one process) and on all host cores (one subinterval per core)."""
+    _oracle_threads_env()
+    cores = host_cores()
+    t = time.time()
+    ob = OracleBlocks(w)
+    one = ob.step(0, 2, None)
+    with oracle_pool(cores) as pool:
+        allc = ob.step(2, min(cores, ob.prm.N), pool)
+    return {"value": allc["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{w.name}: FP64 numpy oracle, iteration 1 restricted to {allc['subintervals']} "
+                       f"consecutive subintervals, each over the first {ob.steps} of its "
+                       f"{ob.prm.S} fine steps (fine propagator with snapshots + level-1 POD one "
+                       f"process per subinterval on {cores} cores, then level-2 POD of the real "
+                       f"neighbours and the sequential augmented coarse updates); value = "
+                       f"grid-point-steps of the sample / its wall time; iteration 0 computed "
+                       f"first, untimed ({ob.t_setup:.1f} s); whole leg {time.time() - t:.1f} s"),
+            "all_cores": allc,
+            "single_thread": dict(one, cores=1,
+                                  sample="the same on 2 consecutive subintervals in one process")}
+
+
+def oracle_c1_solve():
+    """The oracle end to end on the 16^3 ABC workload: sequential fine reference, then
+    Algorithm 2 to rel. L2 <= 1e-6 against it (single thread)."""
+    _oracle_threads_env()
+    import oracle as O
+    import pr_inputs as pi
+    w = pi.ABC_16
+    prm = O.derive_params(w)
+    t = time.perf_counter()
+    ref = O.sequential_fine(w, prm)
+    t_ref = time.perf_counter() - t
+    t = time.perf_counter()
+    h = O.parareal(w, prm, k_max=w.n_sub, tol=1e-6, reference=ref, record=False)
+    t_sol = time.perf_counter() - t
+    return {"workload": w.name, "tol": 1e-6, "iterations": h["k"],
+            "max_err": max(h["err"][-1]), "wall_s": t_sol, "sequential_fine_s": t_ref,
+            "cores": 1}
 
 
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    w = workload()
+    _oracle_threads_env()
+    w = workload(args.config)
+    cores = host_cores()
+    c1 = oracle_c1_solve()
+    ob = OracleBlocks(w)
+    B = min(cores, ob.prm.N)
     times = []
-    for i in range(args.warmup + args.steps):
-        d = cpu_oracle_sample(2)
-        if i >= args.warmup:
-            times.append(d)
+    with oracle_pool(cores) as pool:
+        for i in range(args.warmup + args.steps):
+            d = ob.step((i * B) % ob.prm.N, B, pool)
+            if i >= args.warmup:
+                times.append(d)
     val = statistics.median(x["value"] for x in times)
-    ms = statistics.median(x["t_iter"] for x in times) * 1e3
-    cb = cpu_baseline_obj(times[0])
-    cb["value"] = val
+    ms = statistics.median(x["wall_s"] for x in times) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w, "fp64"),
-            "cpu_baseline": cb,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": (f"each step: iteration 1 of the FP64 numpy oracle restricted to "
+                                        f"{B} consecutive subintervals of {w.name}, each over the first "
+                                        f"{ob.steps} of its {ob.prm.S} fine steps (fine propagator with "
+                                        f"snapshots + level-1 POD one process per subinterval, level-2 "
+                                        f"POD of the real neighbours, sequential coarse updates); value "
+                                        f"= grid-point-steps of the sample / its wall time; blocks "
+                                        f"rotate over the {ob.prm.N} subintervals; iteration 0 untimed "
+                                        f"({ob.t_setup:.1f} s)")},
+            "oracle_c1_solve": c1,
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -311,6 +423,73 @@ def run_serving(bd, n_req: int, rate: float, t_scale: float, tol: float = 1e-6):
     }
 
 
+def _timed_iterations(s, st, steps, warmup, torch, barrier=None, fine_events=True):
+    """Repeat iteration 1 from the same iterate `steps` times after `warmup` untimed
+    repetitions; CUDA events on the context stream around the whole loop and around each
+    fine sweep.  Returns (total ms, mean fine-launch ms, launches)."""
+    from paper_2601_10981_gb300 import binding as bd
+
+    def one_step(ev_f0=None, ev_f1=None):
+        s.rewind()
+        if ev_f0 is not None:
+            ev_f0.record(st)
+        s.fine_sweep(1)
+        if ev_f1 is not None:
+            ev_f1.record(st)
+        s.pod_update(1)
+        s.coarse_sweep(1)
+        return s.check(1)
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = bd.launch_count()
+    if barrier is not None:
+        barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in range(steps):
+        one_step(*fe[i]) if fine_events else one_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
+    launches = bd.launch_count() - l0
+    fine_ms = statistics.mean(a.elapsed_time(b) for a, b in fe) if fine_events else None
+    return e0.elapsed_time(e1), fine_ms, launches
+
+
+def _solve_leg(bd, w, prec, torch, tol=1e-6, k_max=0):
+    """Wall time of pr_solve to rel. L2 <= tol against the GPU's FP64 sequential fine
+    solution (eq. (error)), with the sequential fine solution itself timed (the cost_seq
+    form of Sec. 3.3) in FP64 and in the context's precision."""
+    s = bd.Parareal.from_workload(w, precision=prec)
+    s.set_initial(w.u0(), w.f())
+    out = {}
+    if prec == bd.PR_FP32:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.compute_reference(False)
+        torch.cuda.synchronize()
+        out["sequential_fine_fp32_s"] = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.compute_reference(True)
+    torch.cuda.synchronize()
+    out["sequential_fine_fp64_s"] = time.perf_counter() - t0
+    rep = s.solve(tol, k_max=k_max)
+    out.update({"tol": tol, "converged": bool(rep["converged"]), "iterations": rep["k"],
+                "wall_s": rep["t_total"], "max_err": rep["max_err"], "t_fine": rep["t_fine"],
+                "t_pod": rep["t_pod"], "t_coarse": rep["t_coarse"], "t_iter0": rep["t_iter0"],
+                "lin_iters_mean": rep["lin_iters_mean"], "m1_max": rep["m1_max"],
+                "m2_max": rep["m2_max"]})
+    s.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -321,14 +500,14 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2601_10981_gb300 import binding as bd
-    w = workload(args.subintervals)
+    w = workload(args.config, args.subintervals)
     prec = bd.PR_FP32 if args.precision == "fp32" else bd.PR_FP64
     s = bd.Parareal.from_workload(w, precision=prec)
     st = s.stream
     s.set_initial(w.u0(), w.f())
     s.iteration0()
     if args.mode == "fine":
-        # profiling mode: fine sweeps of iteration 1 only, no JSON line
+        # profiling mode: iteration 1 repeated, no timing and no JSON line
         for _ in range(args.warmup + args.steps):
             s.fine_sweep(1)
             s.pod_update(1)
@@ -345,40 +524,14 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def one_step(ev_f0=None, ev_f1=None):
-        s.rewind()
-        if ev_f0 is not None:
-            ev_f0.record(st)
-        s.fine_sweep(1)
-        if ev_f1 is not None:
-            ev_f1.record(st)
-        s.pod_update(1)
-        s.coarse_sweep(1)
-        return s.check(1)
-
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
+    s.rewind()
+    s.iterate(1)
     tot, mx = s.lin_stats()
     lin_mean = float(tot.sum()) / (w.n_sub * s.S)
     sampler = ClockSampler(local)
     sampler.start()
-    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = bd.launch_count()
-    barrier()
-    torch.cuda.synchronize()
-    e0.record(st)
-    for i in range(args.steps):
-        one_step(*fe[i])
-    e1.record(st)
-    torch.cuda.synchronize()
-    barrier()
-    launches = bd.launch_count() - l0
+    t_ms, fine_ms, launches = _timed_iterations(s, st, args.steps, args.warmup, torch, barrier)
     clocks = sampler.stop()
-    t_ms = e0.elapsed_time(e1)
-    fine_ms = statistics.mean(a.elapsed_time(b) for a, b in fe)
     t_max = reduce_max(t_ms, dist, "cuda")
     ms_per_step = t_max / args.steps
     value = ws * dofs_per_step / (ms_per_step * 1e-3) / 1e9
@@ -403,53 +556,60 @@ def run_ours(args):
     e2e_val = ws * dofs_per_step / (e2e_ms * 1e-3) / 1e9
 
     wb = 4 if args.precision == "fp32" else 8
-    bpd = fine_bytes_per_dof_step(wb, lin_mean, s.dM, True)
+    bpd = fine_bytes_per_dof_step(wb, lin_mean, s.dM, w.f_seed is not None)
     achieved = bpd * dofs_per_step / (fine_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = recorded_traffic(args.precision)
+    traffic = recorded_traffic(args.precision) if args.config == "c2" and not args.subintervals else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": config_dict(w, args.precision),
+        "config": config_dict(w, args.precision, args.config),
         "e2e": {"value": e2e_val, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(Uout.nbytes)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "traffic_source": ("DRAM bytes of one full-size fine launch from a committed "
+                                        "ncu capture (profiles/fine_sweep_kol64_traffic.txt) of "
+                                        "the same fine-kernel source; not measured in this run")
+                                       if traffic is not None else None,
                      "kernel": "fine_kernel (persistent BiCGStab fine sweep)",
-                     "peak_source": peak_kind,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                                    if peak_kind == "measured" else peak_kind,
                      "bytes_per_dof_step": bpd, "lin_iters_per_step": lin_mean,
                      "fine_ms_per_launch": fine_ms},
         "clocks": clocks,
     }
+    s.close()
+    del s
+    if rank == 0 and args.extras:
+        # the same iteration in the paper's arithmetic (FP64 everywhere)
+        if args.precision == "fp32":
+            s64 = bd.Parareal.from_workload(w, precision=bd.PR_FP64)
+            s64.set_initial(w.u0(), w.f())
+            s64.iteration0()
+            s64.iterate(1)
+            k64 = max(1, min(3, args.steps))
+            t64, f64, _ = _timed_iterations(s64, s64.stream, k64, 1, torch)
+            line["fp64_iteration"] = {"ms_per_step": t64 / k64,
+                                      "value": dofs_per_step / (t64 / k64 * 1e-3) / 1e9,
+                                      "unit": UNIT, "fine_ms_per_launch": f64, "steps": k64}
+            s64.close()
+            del s64
+        if args.solve:
+            line["solve_fp32"] = _solve_leg(bd, w, bd.PR_FP32, torch, 1e-6, args.solve_kmax)
+            line["solve_fp64"] = _solve_leg(bd, w, bd.PR_FP64, torch, 1e-6, args.solve_kmax)
+            line["solve"] = dict(line["solve_fp32"] if args.precision == "fp32" else line["solve_fp64"])
+    if rank == 0 and args.serve_requests > 0:
+        line["serving"] = run_serving(bd, args.serve_requests, args.serve_rate, args.serve_tscale)
     if rank == 0 and not args.no_cpu:
         try:
-            line["cpu_baseline"] = cpu_baseline_obj(cpu_oracle_sample(4))
+            line["cpu_baseline"] = cpu_baseline_measure(w)
         except Exception as e:  # report, do not hide the GPU number
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"failed: {e}"[:300]}
-    if rank == 0 and args.solve:
-        # wall time to rel. L2 <= 1e-6 against the sequential fine solution (eq. (error)),
-        # the sequential fine solution itself timed as the plain GPU fine-only form
-        s2 = bd.Parareal.from_workload(w, precision=prec)
-        s2.set_initial(w.u0(), w.f())
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s2.compute_reference(True)
-        torch.cuda.synchronize()
-        t_seq = time.perf_counter() - t0
-        rep = s2.solve(1e-6, k_max=args.solve_kmax)
-        line["solve"] = {"tol": 1e-6, "converged": bool(rep["converged"]), "iterations": rep["k"],
-                         "wall_s": rep["t_total"], "max_err": rep["max_err"],
-                         "t_fine": rep["t_fine"], "t_pod": rep["t_pod"],
-                         "t_coarse": rep["t_coarse"], "t_iter0": rep["t_iter0"],
-                         "sequential_fine_fp64_s": t_seq}
-        s2.close()
-    if rank == 0 and args.serve_requests > 0:
-        s.close()
-        line["serving"] = run_serving(bd, args.serve_requests, args.serve_rate, args.serve_tscale)
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": host_cores(),
+                                    "kind": "oracle", "sample": f"failed: {e}"[:300]}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -465,7 +625,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--solve", type=int, default=1, help="also time a full solve to 1e-6")
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS),
+                    help="c2: 64^3 Kolmogorov (default); c3: 128^3 ABC; c4: 256^3 perturbed Kolmogorov")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="also time the FP64 iteration and the solves (rank 0)")
+    ap.add_argument("--solve", type=int, default=1, help="also time full solves to 1e-6")
     ap.add_argument("--solve-kmax", type=int, default=0, help="0: N (finite termination)")
     ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the mixed serving stream to serve (0: skip)")

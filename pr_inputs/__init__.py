@@ -207,7 +207,11 @@ KOL_64 = Workload("kolmogorov4_64_eps0.01_N64", 64, Flow("kolmogorov", k=4), 0.0
 ABC_128 = Workload("abc128_eps0.005_N256", 128, Flow("abc"), 0.005, 50.0, 256, 5e-4,
                    n_snap=64, m_cap=32, k_max=0, u0_seed=1)
 
-WORKLOADS = {w.name: w for w in (ABC_16, KOL_64, ABC_128)}
+KOL_256 = Workload("kolmogorov8_256_pert_eps0.002_N128", 256,
+                   Flow("kolmogorov", k=8, pert_seed=4, pert_amp=0.05), 0.002, 20.0, 128, 2.5e-4,
+                   n_snap=16, m_cap=8, k_max=0, u0_seed=1)
+
+WORKLOADS = {w.name: w for w in (ABC_16, KOL_64, ABC_128, KOL_256)}
 
 
 def tiny(n: int = 8, n_sub: int = 4, flow: Flow = Flow("abc"), eps: float = 0.05,
