@@ -53,6 +53,11 @@ CONFIGS = {
 }
 
 
+# context options per workload: the 128^3 and 256^3 workloads stream each iteration in
+# waves of subintervals (the form whose workspace fits one GPU)
+CONFIG_OPTS = {"c2": {}, "c3": {"wave": 32}, "c4": {"wave": 8}}
+
+
 def workload(config: str = "c2", subintervals: int = 0):
     """The named workload; `subintervals` > 0 keeps DeltaT (and so the fine steps per
     subinterval) and shortens the horizon, for small profiling captures."""
@@ -423,10 +428,13 @@ def run_serving(bd, n_req: int, rate: float, t_scale: float, tol: float = 1e-6):
     }
 
 
-def _timed_iterations(s, st, steps, warmup, torch, barrier=None, fine_events=True):
+def _timed_iterations(s, st, steps, warmup, torch, barrier=None, wave=False):
     """Repeat iteration 1 from the same iterate `steps` times after `warmup` untimed
     repetitions; CUDA events on the context stream around the whole loop and around each
-    fine sweep.  Returns (total ms, mean fine-launch ms, launches)."""
+    fine sweep.  Returns (total ms, mean fine-kernel ms per iteration, launches).  In wave
+    mode the fine-sweep phase holds the whole streamed iteration, so the fine-kernel time
+    is the library's own event pairs around each wave's fine launch (pr_get_fine_ms), read
+    after each step (one host synchronisation per iteration of several seconds)."""
     from paper_2601_10981_gb300 import binding as bd
 
     def one_step(ev_f0=None, ev_f1=None):
@@ -446,19 +454,25 @@ def _timed_iterations(s, st, steps, warmup, torch, barrier=None, fine_events=Tru
     fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wave_fine = []
     l0 = bd.launch_count()
     if barrier is not None:
         barrier()
     torch.cuda.synchronize()
     e0.record(st)
     for i in range(steps):
-        one_step(*fe[i]) if fine_events else one_step()
+        one_step(*fe[i])
+        if wave:
+            wave_fine.append(s.fine_ms()[0])
     e1.record(st)
     torch.cuda.synchronize()
     if barrier is not None:
         barrier()
     launches = bd.launch_count() - l0
-    fine_ms = statistics.mean(a.elapsed_time(b) for a, b in fe) if fine_events else None
+    if wave:
+        fine_ms = statistics.mean(wave_fine)
+    else:
+        fine_ms = statistics.mean(a.elapsed_time(b) for a, b in fe)
     return e0.elapsed_time(e1), fine_ms, launches
 
 
@@ -490,6 +504,43 @@ def _solve_leg(bd, w, prec, torch, tol=1e-6, k_max=0):
     return out
 
 
+def _large_leg(bd, config, torch, steps=2):
+    """One parareal iteration of a large workload (wave mode), repeated `steps` times after
+    one warm-up: time per iteration, the fine kernel's time and its fraction of the HBM
+    roof (algorithmic bytes)."""
+    try:
+        w = workload(config)
+        s = bd.Parareal.from_workload(w, precision=bd.PR_FP32, **CONFIG_OPTS[config])
+        s.set_initial(w.u0(), w.f())
+        t0 = time.perf_counter()
+        s.iteration0()
+        torch.cuda.synchronize()
+        t_it0 = time.perf_counter() - t0
+        s.iterate(1)
+        tot, _ = s.lin_stats()
+        lin_mean = float(tot.sum()) / (w.n_sub * s.S)
+        t_ms, fine_ms, launches = _timed_iterations(s, s.stream, steps, 1, torch, wave=True)
+        dofs = w.n_sub * s.S * w.Ng
+        bpd = fine_bytes_per_dof_step(4, lin_mean, s.dM, w.f_seed is not None)
+        peak, _ = measured_peaks()
+        ws_gib = s.workspace_bytes() / 2**30
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        ms = t_ms / steps
+        return {"workload": f"{w.name}: {CONFIGS[config][1]}", "precision": "fp32",
+                "form": f"wave mode: each iteration streamed in waves of {CONFIG_OPTS[config]['wave']} subintervals",
+                "ms_per_iteration": ms, "value": dofs / (ms * 1e-3) / 1e9, "unit": UNIT,
+                "fine_kernel_ms_per_iteration": fine_ms,
+                "fine_roofline_frac": bpd * dofs / (fine_ms * 1e-3) / 1e9 / peak if peak else None,
+                "iteration0_s": t_it0, "steps": steps, "lin_iters_per_step": lin_mean,
+                "workspace_gib": ws_gib, "launches_per_iteration": launches / steps,
+                "fine_bytes_per_dof_step": bpd, "peak_gbs": peak}
+    except Exception as e:   # report, do not hide the headline
+        torch.cuda.empty_cache()
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -502,20 +553,29 @@ def run_ours(args):
     from paper_2601_10981_gb300 import binding as bd
     w = workload(args.config, args.subintervals)
     prec = bd.PR_FP32 if args.precision == "fp32" else bd.PR_FP64
-    s = bd.Parareal.from_workload(w, precision=prec)
+    copts = dict(CONFIG_OPTS[args.config])
+    s = bd.Parareal.from_workload(w, precision=prec, **copts)
     st = s.stream
     s.set_initial(w.u0(), w.f())
+    l_setup = bd.launch_count()
     s.iteration0()
     if args.mode == "fine":
-        # profiling mode: iteration 1 repeated, no timing and no JSON line
+        # profiling mode: iteration 1 repeated warmup + steps times, no timing; the launch
+        # counts let an ncu capture skip to one chosen iteration (-s, -c)
+        l_it0 = bd.launch_count()
+        per = []
         for _ in range(args.warmup + args.steps):
+            l0 = bd.launch_count()
             s.fine_sweep(1)
             s.pod_update(1)
             s.coarse_sweep(1)
             s.check(1)
             s.rewind()
+            per.append(bd.launch_count() - l0)
         torch.cuda.synchronize()
-        print(json.dumps({"mode": "fine", "workload": w.name, "launches": bd.launch_count()}))
+        print(json.dumps({"mode": "fine", "workload": w.name, "launches": bd.launch_count(),
+                          "launches_before_iterations": l_it0, "launches_setup": l_setup,
+                          "launches_per_iteration": per}))
         return 0
     s.iterate(1)                      # first iteration: the state every timed step repeats
     dofs_per_step = w.n_sub * s.S * w.Ng
@@ -530,7 +590,8 @@ def run_ours(args):
     lin_mean = float(tot.sum()) / (w.n_sub * s.S)
     sampler = ClockSampler(local)
     sampler.start()
-    t_ms, fine_ms, launches = _timed_iterations(s, st, args.steps, args.warmup, torch, barrier)
+    t_ms, fine_ms, launches = _timed_iterations(s, st, args.steps, args.warmup, torch, barrier,
+                                                wave=bool(copts.get("wave")))
     clocks = sampler.stop()
     t_max = reduce_max(t_ms, dist, "cuda")
     ms_per_step = t_max / args.steps
@@ -575,7 +636,9 @@ def run_ours(args):
                                         "ncu capture (profiles/fine_sweep_kol64_traffic.txt) of "
                                         "the same fine-kernel source; not measured in this run")
                                        if traffic is not None else None,
-                     "kernel": "fine_kernel (persistent BiCGStab fine sweep)",
+                     "kernel": "fine_kernel (persistent BiCGStab fine sweep)" + (
+                         f", {copts['wave']} subintervals a launch (wave mode), time summed over the waves"
+                         if copts else ""),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                                     if peak_kind == "measured" else peak_kind,
                      "bytes_per_dof_step": bpd, "lin_iters_per_step": lin_mean,
@@ -584,7 +647,12 @@ def run_ours(args):
     }
     s.close()
     del s
-    if rank == 0 and args.extras:
+    if copts:
+        line["config"]["form"] = (f"wave mode: each iteration streamed in waves of {copts['wave']} "
+                                  f"subintervals (fine sweep, level-1/2 POD, Galerkin, coarse sweep)")
+    if rank == 0 and args.extras and args.config == "c2":
+        if args.large:
+            line["c3_iteration"] = _large_leg(bd, "c3", torch)
         # the same iteration in the paper's arithmetic (FP64 everywhere)
         if args.precision == "fp32":
             s64 = bd.Parareal.from_workload(w, precision=bd.PR_FP64)
@@ -629,6 +697,8 @@ def main():
                     help="c2: 64^3 Kolmogorov (default); c3: 128^3 ABC; c4: 256^3 perturbed Kolmogorov")
     ap.add_argument("--extras", type=int, default=1,
                     help="also time the FP64 iteration and the solves (rank 0)")
+    ap.add_argument("--large", type=int, default=1,
+                    help="with --config c2 and extras: also time one iteration of the 128^3 workload")
     ap.add_argument("--solve", type=int, default=1, help="also time full solves to 1e-6")
     ap.add_argument("--solve-kmax", type=int, default=0, help="0: N (finite termination)")
     ap.add_argument("--serve-requests", type=int, default=16,

@@ -105,6 +105,22 @@ typedef struct pr_opts {
                                (default 1<<22, about a second)                            */
     int method;             /* enum pr_method; default PR_METHOD_ADAPTIVE                 */
     int fine;               /* enum pr_fine; default PR_FINE_IMPLICIT_EULER               */
+    int wave;               /* adaptive method only.  0 (default): pr_fine_sweep covers all
+                               active subintervals in one launch, the snapshot store holds
+                               all their windows and the level-2 bases of all of them.
+                               w > 0 (w < n_sub): pr_fine_sweep streams iteration k in waves
+                               of w subintervals (n = k-1, k, ... in order): per wave the
+                               fine sweep, the level-1 POD, the level-2 POD and Galerkin
+                               matrices of its subintervals and their share of the
+                               sequential coarse sweep; pr_pod_update and pr_coarse_sweep
+                               then only advance the phase.  The workspace holds one wave's
+                               snapshots, level-2 bases and scratch and one generation of
+                               level-1 bases (replaced wave by wave), which is what lets the
+                               128^3 x 256 and 256^3 x 128 problems fit one GPU.  Every step
+                               sees the inputs it has with w = 0, in the same order, so the
+                               iterates are bit-identical for a fixed group_ctas.
+                               pr_rewind can only undo iteration 1; pr_get_snapshots and
+                               pr_get_basis(level 2) reach the last wave's subintervals only. */
 } pr_opts;
 
 /* Fine integrator.  PR_FINE_IMPLICIT_EULER: the paper's, eq. (semi-dis-eq), BiCGStab per
@@ -261,6 +277,12 @@ pr_status pr_get_diagnostics(pr_ctx* ctx, double* inc, double* err, int* m0, int
  * subinterval n (N each, host; entries of inactive subintervals are 0).  Synchronises. */
 pr_status pr_get_lin_stats(pr_ctx* ctx, int* total, int* max_per_step);
 
+/* Device time of the fine-kernel launches of the last pr_fine_sweep (one launch, or one a
+ * wave in wave mode, measured with CUDA events around each launch on the context stream):
+ * *ms their summed milliseconds, *launches (may be NULL) their count.  PR_ERR_STATE before
+ * the first fine sweep.  Synchronises on the last launch. */
+pr_status pr_get_fine_ms(pr_ctx* ctx, double* ms, int* launches);
+
 /* Wait for the stream; return the first error any kernel recorded. */
 pr_status pr_sync(pr_ctx* ctx);
 const char* pr_last_error(const pr_ctx* ctx);
@@ -283,7 +305,7 @@ pr_status pr_op_apply_L(pr_ctx* ctx, const double* d_in, double* d_out, int coun
 pr_status pr_op_fine(pr_ctx* ctx, const double* d_in, double* d_out, void* d_snap, int B,
                      double t0, int steps, int dM, int n_snap);
 
-/* POD_Mode (Algorithm 1) with CholQR2 re-orthonormalisation on B snapshot matrices:
+/* POD_Mode (Algorithm 1) with one Cholesky-QR re-orthonormalisation pass on B snapshot matrices:
  * d_W: B x n_cols x n^3 doubles (w_f32 = 0; the level-1 path, numerical zero 1e-13) or
  * floats (w_f32 = 1; Gram accumulated over 32-point blocks in FP32, numerical zero 1e-6);
  * d_R: B x m_max x n^3 doubles, m_max = min(cap, n_cols) or
@@ -304,11 +326,15 @@ pr_status pr_op_coarse_update(pr_ctx* ctx, const void* d_R, int m, const double*
  * workspace: its scratch (velocity tables, pointer lists) is one static device array of
  * 13 568 bytes that every GPU loading this library holds until the process exits.
  * Limits: n <= 256 and count <= 64 grid functions per call (PR_ERR_INVALID_ARG beyond).
- * d_in, d_out: count x n^3 device doubles.  Runs on the context stream and synchronises.
- * The first call on a device looks up the array's device address; make that call before
- * any stream capture.  All calls share the array and leave the last call's contents;
- * each call rewrites what it reads, but calls that overlap on the GPU (different streams,
- * no ordering) race on it.  The paper has no counterpart: this is library plumbing. */
+ * d_in, d_out: count x n^3 device doubles.  Runs on the context stream and synchronises
+ * it before returning.  A stored velocity perturbation (pr_flow.pert) lives in the
+ * workspace: with one, bind the workspace and call pr_set_initial first
+ * (PR_ERR_UNSUPPORTED otherwise).  The first call on a device looks up the array's device
+ * address and keeps it for the life of the process; make that call before any stream
+ * capture, and do not use the library across a cudaDeviceReset (the kept address would be
+ * stale).  All calls share the array and leave the last call's contents; each call
+ * rewrites what it reads, but calls that overlap on the GPU (different streams, no
+ * ordering) race on it.  The paper has no counterpart: this is library plumbing. */
 pr_status pr_op_apply_L_noalloc(pr_ctx* ctx, const double* d_in, double* d_out, int count,
                                 int transpose);
 

@@ -42,7 +42,7 @@ class pr_opts(C.Structure):
                 ("rank_tau", C.c_double), ("precision", C.c_int), ("lin_tol", C.c_double),
                 ("lin_maxit", C.c_int), ("aug_tol", C.c_double), ("group_ctas", C.c_int),
                 ("ctas_per_sm", C.c_int), ("spin_limit", C.c_longlong), ("method", C.c_int),
-                ("fine", C.c_int)]
+                ("fine", C.c_int), ("wave", C.c_int)]
 
 
 class pr_report(C.Structure):
@@ -117,6 +117,7 @@ _SIGS = {
     "pr_server_submit": (C.c_int, [_P, C.POINTER(pr_request), _I]),
     "pr_server_step": (C.c_int, [_P, _I, _I]),
     "pr_server_query": (C.c_int, [_P, C.c_int, _I, _I, _D]),
+    "pr_get_fine_ms": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "pr_server_result": (C.c_int, [_P, C.c_int, _D]),
     "pr_server_request_error": (C.c_char_p, [_P, C.c_int]),
     "pr_server_last_error": (C.c_char_p, [_P]),
@@ -228,12 +229,16 @@ class Parareal:
         self.fp32 = bool(options is not None and options.precision == PR_FP32)
 
     @classmethod
-    def from_workload(cls, w, precision: int = PR_FP64, **opt_kw):
+    def from_workload(cls, w, precision: int = PR_FP64, workspace: bool = True, **opt_kw):
         fl = w.flow
         flow = flow_of(fl, w.n)
         o = opts(n_snap=w.n_snap, m_cap=w.m_cap, m_l=w.m_l, p=w.p, precision=precision, **opt_kw)
-        obj = cls(w.n, flow, w.eps, w.T, w.n_sub, w.dt, w.pod_tol, o)
+        obj = cls(w.n, flow, w.eps, w.T, w.n_sub, w.dt, w.pod_tol, o, workspace=workspace)
         return obj
+
+    def workspace_bytes(self) -> int:
+        """pr_workspace_bytes: device bytes the context needs."""
+        return int(self._lib.pr_workspace_bytes(self.ctx))
 
     # ------------------------------------------------------------------ errors
     def _check(self, st: int):
@@ -328,6 +333,12 @@ class Parareal:
         self._check(self._lib.pr_get_diagnostics(self.ctx, _dptr(inc), _dptr(err), C.byref(m0),
                                                   m1.ctypes.data_as(_I), m2.ctypes.data_as(_I)))
         return dict(inc=inc, err=err, m0=m0.value, m1=m1, m2=m2)
+
+    def fine_ms(self):
+        """(ms, launches): device time of the fine-kernel launches of the last fine sweep."""
+        ms, nl = C.c_double(), C.c_int()
+        self._check(self._lib.pr_get_fine_ms(self.ctx, C.byref(ms), C.byref(nl)))
+        return ms.value, nl.value
 
     def lin_stats(self):
         tot, mx = np.zeros(self.N, dtype=np.int32), np.zeros(self.N, dtype=np.int32)

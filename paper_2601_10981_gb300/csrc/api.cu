@@ -56,7 +56,10 @@ struct pr_ctx {
     int S = 0, S0 = 0, Lc = 0, dM = 0, ns = 0, ns0 = 0, nsmax = 0;
     double gamma1 = 0, gamma3 = 0, tau = 0, tau1 = 1e-13, lin_tol = 0;
     bool fp32 = false;
-    int esz = 8;
+    int esz = 8;         // POD bases are FP64 in both modes (the augmentation needs them exact)
+    int wave = 0;        // > 0: the iteration streams in waves of this many subintervals
+    int wave_lo = 0, wave_hi = 0;   // subintervals whose snapshots the store holds
+    int r2_lo = 0, r2_hi = 0;       // wave mode: subintervals whose level-2 bases are held
     int mcap0 = 0, mcap1 = 0, w2 = 0, mcap2 = 0, mscr = 0, maxK = 0, ldcols = 0;
     int groups_max = 1;
     int max_ctas = 1;
@@ -79,6 +82,8 @@ struct pr_ctx {
     char* snap = nullptr;
     char* R1[2] = {nullptr, nullptr};
     int* m1[2] = {nullptr, nullptr};
+    char* R1t = nullptr;           // wave mode: level-1 bases of the current wave
+    int* m1t = nullptr;
     int r1cur = 0;  // R1[r1cur]: level-1 bases of the latest pod update
     char* V0 = nullptr;
     int* m0 = nullptr;
@@ -158,6 +163,8 @@ struct pr_ctx {
     std::string err;
     cudaEvent_t ev[8] = {};
     bool ev_ready = false;
+    std::vector<cudaEvent_t> fev;   // pairs around the fine launches of the last fine sweep
+    int fev_used = 0;
 };
 
 namespace {
@@ -190,18 +197,26 @@ size_t plan(pr_ctx* c, char* base) {
     c->Ubuf[0] = b.take<double>((size_t)(N + 1) * Ng);
     c->Ubuf[1] = b.take<double>((size_t)(N + 1) * Ng);
     c->Fend = b.take<double>((size_t)N * Ng);
-    c->snap = b.take<char>((size_t)N * c->nsmax * Ng * sizeof(double));
-    for (int i = 0; i < 2; ++i) {
+    // wave mode: the snapshot store, the level-2 bases, POD scratch and fine workspace
+    // hold one wave; the level-1 bases keep one generation (updated in place after each
+    // wave's level 2) plus the current wave's
+    const int NB = c->wave > 0 ? std::min(c->wave, N) : N;
+    c->snap = b.take<char>((size_t)std::max(NB, 1) * c->nsmax * Ng * sizeof(double));
+    for (int i = 0; i < (c->wave > 0 ? 1 : 2); ++i) {
         c->R1[i] = b.take<char>((size_t)N * c->mcap1 * Ng * c->esz);
         c->m1[i] = b.take<int>(N);
     }
+    if (c->wave > 0) {
+        c->R1t = b.take<char>((size_t)NB * c->mcap1 * Ng * c->esz);
+        c->m1t = b.take<int>(NB);
+    }
     c->V0 = b.take<char>((size_t)c->mcap0 * Ng * c->esz);
     c->m0 = b.take<int>(1);
-    c->R2 = b.take<char>((size_t)N * c->mcap2 * Ng * c->esz);
+    c->R2 = b.take<char>((size_t)NB * c->mcap2 * Ng * c->esz);
     c->m2 = b.take<int>(N + 1);
     c->mop = b.take<int>(N + 1);
-    c->LR = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
-    c->scr[0] = b.take<char>((size_t)N * c->mscr * Ng * c->esz);
+    c->LR = b.take<char>((size_t)NB * c->mscr * Ng * c->esz);
+    c->scr[0] = b.take<char>((size_t)NB * c->mscr * Ng * c->esz);
     c->Mr = b.take<double>((size_t)(N + 1) * c->mcap2 * c->mcap2);
     // Galerkin blocks of L: R^T L R (steady flows) or the pieces R^T D R, R^T A0 R, R^T A1 R
     c->Lr = b.take<double>((size_t)(N + 1) * 3 * c->mcap2 * c->mcap2);
@@ -237,7 +252,7 @@ size_t plan(pr_ctx* c, char* base) {
     c->lam = b.take<double>((size_t)N * c->maxK);
     c->Cm = b.take<double>((size_t)N * c->maxK * c->maxK);
     c->X = b.take<double>((size_t)N * c->mscr * c->mscr);
-    c->gpart_n = gram_part_doubles(Ng, N + 1, c->maxK, c->maxK);
+    c->gpart_n = gram_part_doubles(Ng, NB + 1, c->maxK, c->maxK);
     c->gpart = b.take<double>(c->gpart_n);
     c->counters = b.take<unsigned>((size_t)N + 64);
     c->colsA = b.take<const void*>((size_t)(N + 1) * c->ldcols);
@@ -290,7 +305,7 @@ pr_status init_ws(pr_ctx* c) {
     PR_CUDA(cudaMemsetAsync(c->fits, 0, sizeof(int) * ((size_t)c->N + 1), st));
     PR_CUDA(cudaMemsetAsync(c->fitsmax, 0, sizeof(int) * ((size_t)c->N + 1), st));
     PR_CUDA(cudaMemsetAsync(c->m1[0], 0, sizeof(int) * c->N, st));
-    PR_CUDA(cudaMemsetAsync(c->m1[1], 0, sizeof(int) * c->N, st));
+    if (c->m1[1]) PR_CUDA(cudaMemsetAsync(c->m1[1], 0, sizeof(int) * c->N, st));
     PR_CUDA(cudaMemsetAsync(c->m2, 0, sizeof(int) * ((size_t)c->N + 1), st));
     PR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(double) * c->Ng, st));
     PR_CUDA(cudaMemsetAsync(c->f32, 0, sizeof(float) * c->Ng, st));
@@ -374,7 +389,7 @@ pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const i
     return upload_blocks(c, bs, cs, 1, B, cols, K, esize);
 }
 
-// POD_Mode + CholQR2 on B batch items whose snapshot columns are already in
+// POD_Mode + one Cholesky-QR pass on B batch items whose snapshot columns are already in
 // (c->colsA, c->KA).  Result: dest + b*dest_bstride (columns of Ng), dims m_dest[b].
 // ortho_blocks: the snapshot columns are blocks of orthonormal bases (c->colblk says
 // which); the FP32 mode then takes their diagonal Gram blocks as the identity.
@@ -657,6 +672,179 @@ pr_status check_finite_host(const double* x, long long n) {
     return PR_OK;
 }
 
+// The blocks of eq. (W^k_n) for subinterval n: left neighbour (m_l = 1), this
+// subinterval, previous iteration (p = 1; V0 at k = 1, reading R8), as (base, count).
+struct L2Blocks {
+    const void* base[3];
+    const int* cnt[3];
+};
+
+// Level-2 POD (eq. (W^k_n)) and the Galerkin matrices of the result for subintervals
+// n_lo .. n_hi-1 into R2 (item n at R2 + (n - n_lo) mcap2 columns), m2 + n, Mr/Lr at n;
+// blocks(n) gives the level-1 blocks of n.
+template <typename BlocksOf>
+pr_status level2_range(pr_ctx* c, int n_lo, int n_hi, char* R2, BlocksOf blocks) {
+    const int B2 = n_hi - n_lo;
+    if (B2 <= 0) return PR_OK;
+    const long long Ng = c->Ng;
+    std::vector<const void*> bs;
+    std::vector<const int*> cs;
+    for (int n = n_lo; n < n_hi; ++n) {
+        const L2Blocks q = blocks(n);
+        for (int j = 0; j < 3; ++j) {
+            bs.push_back(q.base[j]);
+            cs.push_back(q.cnt[j]);
+        }
+    }
+    pr_status s = upload_blocks(c, bs, cs, 3, B2, c->colsA, c->KA, c->esz, c->colblk);
+    if (s != PR_OK) return s;
+    s = pod_pipeline(c, B2, c->w2, c->gamma3, c->tau, false, c->o.m_cap, c->mcap2, R2, (size_t)c->mcap2 * Ng,
+                     c->m2 + n_lo, true);
+    if (s != PR_OK) return s;
+    return galerkin(c, R2, (size_t)c->mcap2 * Ng, c->m2 + n_lo, B2, c->mcap2,
+                    c->Mr + (size_t)n_lo * c->mcap2 * c->mcap2, c->Lr + (size_t)n_lo * 3 * c->mcap2 * c->mcap2, true);
+}
+
+// run_fine bracketed by a pair of the context's fine-launch events (pr_get_fine_ms).
+pr_status run_fine_timed(pr_ctx* c, const double* u_in, double* u_out, char* snap, int B, int n_snap, int stat_off,
+                         double t0) {
+    if ((int)c->fev.size() < c->fev_used + 2) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            PR_CUDA(cudaEventCreate(&e));
+            c->fev.push_back(e);
+        }
+    }
+    PR_CUDA(cudaEventRecord(c->fev[c->fev_used], c->st));
+    pr_status s = run_fine(c, u_in, u_out, snap, B, c->S, n_snap, stat_off, false, t0, c->DeltaT);
+    if (s != PR_OK) return s;
+    PR_CUDA(cudaEventRecord(c->fev[c->fev_used + 1], c->st));
+    c->fev_used += 2;
+    return PR_OK;
+}
+
+// Level-1 POD of B snapshot windows (stride ns grid functions) into dest (stride mcap1).
+pr_status level1(pr_ctx* c, const char* snap, int B, char* dest, int* m_dest) {
+    const long long Ng = c->Ng;
+    pr_status s = cols_contig(c, snap, (size_t)c->ns * Ng * sizeof(double), c->cnst + 0, 0, B, c->colsA, c->KA,
+                              sizeof(double));
+    if (s != PR_OK) return s;
+    return pod_pipeline(c, B, c->ns, c->gamma1, c->tau1, false, c->o.m_cap, c->mcap1, dest, (size_t)c->mcap1 * Ng,
+                        m_dest);
+}
+
+CoarseSweepArgs coarse_args(pr_ctx* c) {
+    CoarseSweepArgs a{};
+    a.g = grid_of(c);
+    a.tdep = c->tdep ? 1 : 0;
+    a.kind = c->flow.kind;
+    a.w = c->flow.w;
+    a.t0 = c->T0;
+    a.DeltaT = c->DeltaT;
+    a.A1d = c->cA1;
+    a.ldM = c->mcap2;
+    a.maxm = c->mcap2;
+    a.dT = c->dT;
+    a.Lc = c->Lc;
+    a.aug_tol = c->o.aug_tol;
+    a.augment = 1;
+    a.d = c->cd;
+    a.Ld = c->cLd;
+    a.Ltd = c->cLtd;
+    a.part = c->cpart;
+    a.bar = c->counters + c->N + 16;
+    a.spin_limit = c->o.spin_limit;
+    a.err = c->derr;
+    return a;
+}
+
+// The sequential augmented coarse sweep of eq. (formula4) over n = n_lo .. n_hi-1 of
+// iteration k: U^k_{n+1} = G(U^k_n) + F_n - G(P U^{k-1}_n) into Ubuf[1 - cur], with the
+// level-2 bases of item n at R2 + (n - n_lo) mcap2 columns.
+pr_status coarse_range(pr_ctx* c, int n_lo, int n_hi, const char* R2) {
+    if (n_hi <= n_lo) return PR_OK;
+    const long long Ng = c->Ng;
+    CoarseSweepArgs a = coarse_args(c);
+    a.n0 = n_lo;
+    a.count = n_hi - n_lo;
+    a.U = c->Ubuf[1 - c->cur];
+    a.sU = Ng;
+    a.Up = c->Ubuf[c->cur];
+    a.sUp = Ng;
+    a.F = c->Fend;
+    a.sF = Ng;
+    a.out = c->Ubuf[1 - c->cur] + Ng;
+    a.sOut = Ng;
+    a.sR = (long long)c->mcap2 * Ng;
+    a.R = reinterpret_cast<const double*>(R2) - (size_t)n_lo * a.sR;   // item n at a.R + n sR
+    a.m = c->m2;
+    a.sm = 1;
+    a.Mr = c->Mr;
+    a.Lr = c->Lr;
+    a.sM = (long long)c->mcap2 * c->mcap2;
+    a.sML = (long long)3 * c->mcap2 * c->mcap2;
+    PR_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), c->st));
+    PR_CUDA(launch_coarse_sweep(a, c->st));
+    return PR_OK;
+}
+
+// Wave mode: iteration k streamed over waves of subintervals n = k-1, k, ... in order.
+// For each wave: the fine sweep with its snapshots; the level-1 POD into the wave's
+// bases; the level-2 POD and Galerkin matrices of the wave's subintervals n >= k (left
+// neighbour: the wave's, or the one the previous wave committed; previous-iteration
+// block: the committed basis of iteration k-1, or V0 at k = 1); the coarse sweep over the
+// same subintervals, which continues from U^k_n that the previous wave's sweep wrote;
+// then the wave's level-1 bases replace the committed ones.  Every step sees exactly the
+// inputs it has in the single-launch form, in the same order.
+pr_status wave_sweep(pr_ctx* c, int k) {
+    const long long Ng = c->Ng;
+    const int N = c->N, W = c->wave;
+    const size_t bstride = (size_t)c->mcap1 * Ng * c->esz;
+    const double* Uold = c->Ubuf[c->cur];
+    double* Unew = c->Ubuf[1 - c->cur];
+    c->fev_used = 0;
+    // U^k_n = U^{k-1}_n for n < k (reading R10)
+    PR_CUDA(cudaMemcpyAsync(Unew, Uold, sizeof(double) * (size_t)k * Ng, cudaMemcpyDeviceToDevice, c->st));
+    for (int a = k - 1; a < N; a += W) {
+        const int nb = std::min(W, N - a);
+        pr_status s = run_fine_timed(c, Uold + (size_t)a * Ng, c->Fend + (size_t)a * Ng, c->snap, nb, c->ns, a,
+                                     c->T0 + a * c->DeltaT);
+        if (s != PR_OK) return s;
+        c->wave_lo = a;
+        c->wave_hi = a + nb;
+        if (a == k - 1)   // U^k_k = F_{k-1} (reading R10)
+            PR_CUDA(cudaMemcpyAsync(Unew + (size_t)k * Ng, c->Fend + (size_t)(k - 1) * Ng, sizeof(double) * Ng,
+                                    cudaMemcpyDeviceToDevice, c->st));
+        s = level1(c, c->snap, nb, c->R1t, c->m1t);
+        if (s != PR_OK) return s;
+        const int n_lo = std::max(a, k), n_hi = a + nb;
+        s = level2_range(c, n_lo, n_hi, c->R2, [&](int n) {
+            L2Blocks q{};
+            if (c->o.m_l >= 1) {
+                const bool in_wave = n - 1 >= a;
+                q.base[0] = in_wave ? c->R1t + (size_t)(n - 1 - a) * bstride : c->R1[0] + (size_t)(n - 1) * bstride;
+                q.cnt[0] = in_wave ? c->m1t + (n - 1 - a) : c->m1[0] + (n - 1);
+            }
+            q.base[1] = c->R1t + (size_t)(n - a) * bstride;
+            q.cnt[1] = c->m1t + (n - a);
+            if (c->o.p >= 1) {
+                q.base[2] = k == 1 ? (const void*)c->V0 : (const void*)(c->R1[0] + (size_t)n * bstride);
+                q.cnt[2] = k == 1 ? c->m0 : c->m1[0] + n;
+            }
+            return q;
+        });
+        if (s != PR_OK) return s;
+        s = coarse_range(c, n_lo, n_hi, c->R2);
+        if (s != PR_OK) return s;
+        PR_CUDA(cudaMemcpyAsync(c->R1[0] + (size_t)a * bstride, c->R1t, (size_t)nb * bstride, cudaMemcpyDeviceToDevice,
+                                c->st));
+        PR_CUDA(cudaMemcpyAsync(c->m1[0] + a, c->m1t, sizeof(int) * nb, cudaMemcpyDeviceToDevice, c->st));
+        c->r2_lo = n_lo;
+        c->r2_hi = n_hi;
+    }
+    return PR_OK;
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -673,6 +861,7 @@ void pr_opts_init(pr_opts* o) {
     o->spin_limit = 1LL << 22;
     o->method = PR_METHOD_ADAPTIVE;
     o->fine = PR_FINE_IMPLICIT_EULER;
+    o->wave = 0;
 }
 
 const char* pr_status_string(pr_status s) {
@@ -716,6 +905,8 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (o.lin_maxit <= 0) o.lin_maxit = 200;
     if (o.spin_limit < 0) o.spin_limit = 1LL << 22;
     if (o.aug_tol <= 0) o.aug_tol = 1e-12;
+    if (o.wave < 0) return PR_ERR_INVALID_ARG;
+    if (o.wave > 0 && o.method != PR_METHOD_ADAPTIVE) return PR_ERR_UNSUPPORTED;   // waves stream Algorithm 2
     pr_ctx* c = new pr_ctx();
     c->n = grid->n;
     c->L = grid->L > 0 ? grid->L : 2.0 * M_PI;
@@ -744,6 +935,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     c->o = o;
     c->fp32 = o.precision == PR_FP32;
     c->esz = 8;  // POD bases are FP64 in both modes (the augmentation needs them exact)
+    c->wave = (o.wave > 0 && o.wave < n_sub) ? o.wave : 0;
     c->DeltaT = T / n_sub;
     c->S = steps_for(c->DeltaT, dt_fine);
     c->dt = c->DeltaT / c->S;
@@ -793,7 +985,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     }
     c->max_ctas = fine_max_ctas(c->n, c->fp32, o.ctas_per_sm);
     c->max_ctas = std::max(c->max_ctas, fine_max_ctas(c->n, false, o.ctas_per_sm));
-    c->groups_max = std::max(1, std::min(c->N, c->max_ctas));
+    c->groups_max = std::max(1, std::min(c->wave > 0 ? c->wave : c->N, c->max_ctas));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         delete c;
@@ -812,6 +1004,7 @@ void pr_destroy(pr_ctx* c) {
     if (c->ref) cudaFree(c->ref);
     if (c->ev_ready)
         for (auto& e : c->ev) cudaEventDestroy(e);
+    for (auto& e : c->fev) cudaEventDestroy(e);
     delete c;
 }
 
@@ -904,6 +1097,7 @@ pr_status pr_iteration0(pr_ctx* c) {
     s = pod_pipeline(c, 1, c->ns0, c->gamma1, c->tau1, false, c->o.m_cap, c->mcap0, c->V0,
                      (size_t)c->mcap0 * Ng, c->m0);
     if (s != PR_OK) return s;
+
     // Galerkin matrices of V0 and projections of u_hat0, f
     s = galerkin(c, c->V0, (size_t)c->mcap0 * Ng, c->m0, 1, c->mcap0, c->M0, c->L0);
     if (s != PR_OK) return s;
@@ -986,9 +1180,16 @@ pr_status pr_fine_sweep(pr_ctx* c, int k) {
     const int B = c->N - k + 1;
     const double* Uprev = c->Ubuf[c->cur];
     const bool plain = c->o.method != PR_METHOD_ADAPTIVE;   // no snapshots needed
-    pr_status s = run_fine(c, Uprev + (size_t)(k - 1) * Ng, c->Fend + (size_t)(k - 1) * Ng,
-                           plain ? nullptr : c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->S,
-                           c->ns, k - 1, false, c->T0 + (k - 1) * c->DeltaT, c->DeltaT);
+    if (c->wave > 0) {
+        pr_status s = wave_sweep(c, k);
+        if (s != PR_OK) return s;
+        c->phase = 1;
+        return PR_OK;
+    }
+    c->fev_used = 0;
+    pr_status s = run_fine_timed(c, Uprev + (size_t)(k - 1) * Ng, c->Fend + (size_t)(k - 1) * Ng,
+                                 plain ? nullptr : c->snap + (size_t)(k - 1) * c->ns * Ng * c->esz, B, c->ns,
+                                 k - 1, c->T0 + (k - 1) * c->DeltaT);
     if (s != PR_OK) return s;
     c->phase = 1;
     return PR_OK;
@@ -1005,6 +1206,7 @@ pr_status pr_fine_sweep_batch(pr_ctx* const* ctxs, const int* ks, int count) {
         if (k < 1 || k > c->N) return fail(c, PR_ERR_INVALID_ARG, "k out of range");
         if (c->k_done != k - 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "pr_fine_sweep_batch out of order");
         if (!c->ws_ready) return fail(c, PR_ERR_STATE, "workspace not initialised (pr_set_initial first)");
+        if (c->wave > 0) return fail(c, PR_ERR_UNSUPPORTED, "pr_fine_sweep_batch: contexts in wave mode sweep alone");
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return fail(c, PR_ERR_INVALID_ARG, "a context appears twice");
         if (owner && (c->n != owner->n || c->L != owner->L || c->fp32 != owner->fp32 ||
@@ -1128,7 +1330,8 @@ pr_status pr_tune_fine(pr_ctx* c, int steps, int* best_group_ctas, double* best_
 pr_status pr_pod_update(pr_ctx* c, int k) {
     if (!c) return PR_ERR_INVALID_ARG;
     if (c->k_done != k - 1 || c->phase != 1) return fail(c, PR_ERR_STATE, "pr_pod_update out of order");
-    if (c->o.method != PR_METHOD_ADAPTIVE) {   // plain parareal: no POD bases
+    if (c->o.method != PR_METHOD_ADAPTIVE || c->wave > 0) {
+        // plain parareal: no POD bases; wave mode: done wave by wave in pr_fine_sweep
         c->phase = 2;
         return PR_OK;
     }
@@ -1137,87 +1340,29 @@ pr_status pr_pod_update(pr_ctx* c, int k) {
     pr_status s;
     // level 1: n = k-1 .. N-1 into R1[nw] (the other buffer)
     const int nw = 1 - c->r1cur;
-    const int B1 = N - k + 1;
-    {
-        s = cols_contig(c, c->snap + (size_t)(k - 1) * c->ns * Ng * sizeof(double),
-                        (size_t)c->ns * Ng * sizeof(double), c->cnst + 0, 0, B1, c->colsA, c->KA,
-                        sizeof(double));
-        if (s != PR_OK) return s;
-        s = pod_pipeline(c, B1, c->ns, c->gamma1, c->tau1, false, c->o.m_cap, c->mcap1,
-                         c->R1[nw] + (size_t)(k - 1) * c->mcap1 * Ng * c->esz, (size_t)c->mcap1 * Ng,
-                         c->m1[nw] + (k - 1));
-        if (s != PR_OK) return s;
-    }
-    // level 2: n = k .. N-1
-    const int B2 = N - k;
-    if (B2 > 0) {
-        std::vector<const void*> bs;
-        std::vector<const int*> cs;
-        const int nb = 3;
-        const size_t colstride = (size_t)c->mcap1 * Ng * c->esz;
-        for (int n = k; n < N; ++n) {
-            // left neighbour(s), this subinterval, previous iteration (V0 at k = 1)
-            if (c->o.m_l >= 1) {
-                bs.push_back(c->R1[nw] + (size_t)(n - 1) * colstride);
-                cs.push_back(c->m1[nw] + (n - 1));
-            } else {
-                bs.push_back(nullptr);
-                cs.push_back(nullptr);
-            }
-            bs.push_back(c->R1[nw] + (size_t)n * colstride);
-            cs.push_back(c->m1[nw] + n);
-            if (c->o.p >= 1) {
-                if (k == 1) {
-                    bs.push_back(c->V0);
-                    cs.push_back(c->m0);
-                } else {
-                    bs.push_back(c->R1[1 - nw] + (size_t)n * colstride);
-                    cs.push_back(c->m1[1 - nw] + n);
-                }
-            } else {
-                bs.push_back(nullptr);
-                cs.push_back(nullptr);
-            }
+    const size_t bstride = (size_t)c->mcap1 * Ng * c->esz;
+    s = level1(c, c->snap + (size_t)(k - 1) * c->ns * Ng * sizeof(double), N - k + 1,
+               c->R1[nw] + (size_t)(k - 1) * bstride, c->m1[nw] + (k - 1));
+    if (s != PR_OK) return s;
+    // level 2: n = k .. N-1 (left neighbour(s), this subinterval, previous iteration)
+    s = level2_range(c, k, N, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, [&](int n) {
+        L2Blocks q{};
+        if (c->o.m_l >= 1) {
+            q.base[0] = c->R1[nw] + (size_t)(n - 1) * bstride;
+            q.cnt[0] = c->m1[nw] + (n - 1);
         }
-        s = upload_blocks(c, bs, cs, nb, B2, c->colsA, c->KA, c->esz, c->colblk);
-        if (s != PR_OK) return s;
-        s = pod_pipeline(c, B2, c->w2, c->gamma3, c->tau, false, c->o.m_cap, c->mcap2,
-                         c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k,
-                         true);
-        if (s != PR_OK) return s;
-        s = galerkin(c, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz, (size_t)c->mcap2 * Ng, c->m2 + k, B2,
-                     c->mcap2, c->Mr + (size_t)k * c->mcap2 * c->mcap2, c->Lr + (size_t)k * 3 * c->mcap2 * c->mcap2,
-                     true);
-        if (s != PR_OK) return s;
-    }
+        q.base[1] = c->R1[nw] + (size_t)n * bstride;
+        q.cnt[1] = c->m1[nw] + n;
+        if (c->o.p >= 1) {
+            q.base[2] = k == 1 ? (const void*)c->V0 : (const void*)(c->R1[1 - nw] + (size_t)n * bstride);
+            q.cnt[2] = k == 1 ? c->m0 : c->m1[1 - nw] + n;
+        }
+        return q;
+    });
+    if (s != PR_OK) return s;
     c->r1cur = nw;
     c->phase = 2;
     return PR_OK;
-}
-
-static CoarseSweepArgs coarse_args(pr_ctx* c) {
-    CoarseSweepArgs a{};
-    a.g = grid_of(c);
-    a.tdep = c->tdep ? 1 : 0;
-    a.kind = c->flow.kind;
-    a.w = c->flow.w;
-    a.t0 = c->T0;
-    a.DeltaT = c->DeltaT;
-    a.A1d = c->cA1;
-    a.ldM = c->mcap2;
-    a.maxm = c->mcap2;
-    a.dT = c->dT;
-    a.Lc = c->Lc;
-    a.aug_tol = c->o.aug_tol;
-    a.augment = 1;
-    a.d = c->cd;
-    a.Ld = c->cLd;
-    a.Ltd = c->cLtd;
-    a.part = c->cpart;
-    a.bar = c->counters + c->N + 16;
-    a.spin_limit = c->o.spin_limit;
-    a.err = c->derr;
-    return a;
 }
 
 pr_status pr_coarse_sweep(pr_ctx* c, int k) {
@@ -1226,6 +1371,13 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
     const long long Ng = c->Ng;
     const double* Uold = c->Ubuf[c->cur];
     double* Unew = c->Ubuf[1 - c->cur];
+    if (c->wave > 0) {   // the sweep ran wave by wave inside pr_fine_sweep
+        c->cur = 1 - c->cur;
+        c->k_done = k;
+        c->phase = 0;
+        c->checked = false;
+        return PR_OK;
+    }
     PR_CUDA(cudaMemcpyAsync(Unew, Uold, sizeof(double) * (size_t)k * Ng, cudaMemcpyDeviceToDevice, c->st));
     PR_CUDA(cudaMemcpyAsync(Unew + (size_t)k * Ng, c->Fend + (size_t)(k - 1) * Ng, sizeof(double) * Ng,
                             cudaMemcpyDeviceToDevice, c->st));
@@ -1245,6 +1397,16 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
         c->checked = false;
         return PR_OK;
     }
+    if (c->o.method == PR_METHOD_ADAPTIVE) {
+        pr_status s = coarse_range(c, k, c->N, c->R2 + (size_t)k * c->mcap2 * Ng * c->esz);
+        if (s != PR_OK) return s;
+        c->cur = 1 - c->cur;
+        c->k_done = k;
+        c->phase = 0;
+        c->checked = false;
+        return PR_OK;
+    }
+    // Parareal-I: G in the fixed space V0, no augmentation
     CoarseSweepArgs a = coarse_args(c);
     a.n0 = k;
     a.count = c->N - k;
@@ -1256,27 +1418,17 @@ pr_status pr_coarse_sweep(pr_ctx* c, int k) {
     a.sF = Ng;
     a.out = Unew + Ng;
     a.sOut = Ng;
-    a.R = reinterpret_cast<const double*>(c->R2);
-    a.sR = (long long)c->mcap2 * Ng;
-    a.m = c->m2;
-    a.sm = 1;
-    a.Mr = c->Mr;
-    a.Lr = c->Lr;
-    a.sM = (long long)c->mcap2 * c->mcap2;
-    a.sML = (long long)3 * c->mcap2 * c->mcap2;
-    if (c->o.method == PR_METHOD_PARAREAL_I) {   // G in the fixed space V0
-        a.R = reinterpret_cast<const double*>(c->V0);
-        a.sR = 0;
-        a.m = c->m0;
-        a.sm = 0;
-        a.Mr = c->M0;
-        a.Lr = c->L0;
-        a.sM = 0;
-        a.sML = 0;
-        a.ldM = c->mcap0;
-        a.maxm = c->mcap0;
-        a.augment = 0;
-    }
+    a.R = reinterpret_cast<const double*>(c->V0);
+    a.sR = 0;
+    a.m = c->m0;
+    a.sm = 0;
+    a.Mr = c->M0;
+    a.Lr = c->L0;
+    a.sM = 0;
+    a.sML = 0;
+    a.ldM = c->mcap0;
+    a.maxm = c->mcap0;
+    a.augment = 0;
     PR_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), c->st));
     PR_CUDA(launch_coarse_sweep(a, c->st));
     c->cur = 1 - c->cur;
@@ -1494,6 +1646,21 @@ pr_status pr_get_diagnostics(pr_ctx* c, double* inc, double* err, int* m0, int* 
     return PR_OK;
 }
 
+pr_status pr_get_fine_ms(pr_ctx* c, double* ms, int* launches) {
+    if (!c || !ms) return PR_ERR_INVALID_ARG;
+    if (c->fev_used == 0) return fail(c, PR_ERR_STATE, "no fine sweep timed yet");
+    PR_CUDA(cudaEventSynchronize(c->fev[c->fev_used - 1]));
+    double t = 0.0;
+    for (int i = 0; i < c->fev_used; i += 2) {
+        float a = 0.f;
+        PR_CUDA(cudaEventElapsedTime(&a, c->fev[i], c->fev[i + 1]));
+        t += a;
+    }
+    *ms = t;
+    if (launches) *launches = c->fev_used / 2;
+    return PR_OK;
+}
+
 pr_status pr_get_lin_stats(pr_ctx* c, int* total, int* mx) {
     if (!c) return PR_ERR_INVALID_ARG;
     PR_CUDA(cudaStreamSynchronize(c->st));
@@ -1505,9 +1672,13 @@ pr_status pr_get_lin_stats(pr_ctx* c, int* total, int* mx) {
 pr_status pr_rewind(pr_ctx* c) {
     if (!c) return PR_ERR_INVALID_ARG;
     if (c->k_done < 1 || c->phase != 0) return fail(c, PR_ERR_STATE, "no completed iteration to undo");
+    // wave mode keeps one generation of level-1 bases: iteration k >= 2 replaced those of
+    // k-1 in place; iteration 1 used V0 instead, so it can be repeated
+    if (c->wave > 0 && c->k_done > 1)
+        return fail(c, PR_ERR_STATE, "wave mode can only undo iteration 1 (the level-1 bases of k-1 are replaced)");
     PR_CUDA(cudaStreamSynchronize(c->st));
     c->cur = 1 - c->cur;
-    if (c->o.method == PR_METHOD_ADAPTIVE) c->r1cur = 1 - c->r1cur;
+    if (c->o.method == PR_METHOD_ADAPTIVE && c->wave == 0) c->r1cur = 1 - c->r1cur;
     c->k_done -= 1;
     c->phase = 0;
     return PR_OK;
@@ -1526,7 +1697,13 @@ pr_status pr_get_snapshots(pr_ctx* c, int n, void* out) {
     if (!c || !out || n < 0 || n >= c->N) return PR_ERR_INVALID_ARG;
     if (!c->ws_ready) return fail(c, PR_ERR_STATE, "no workspace");
     const size_t per = (size_t)c->ns * c->Ng * sizeof(double);
-    PR_CUDA(cudaMemcpyAsync(out, c->snap + (size_t)n * per, per, cudaMemcpyDeviceToHost, c->st));
+    size_t slot = (size_t)n;
+    if (c->wave > 0) {   // the store holds the last wave only
+        if (n < c->wave_lo || n >= c->wave_hi)
+            return fail(c, PR_ERR_STATE, "wave mode: the snapshots of this subinterval are not resident");
+        slot = (size_t)(n - c->wave_lo);
+    }
+    PR_CUDA(cudaMemcpyAsync(out, c->snap + slot * per, per, cudaMemcpyDeviceToHost, c->st));
     PR_CUDA(cudaStreamSynchronize(c->st));
     return PR_OK;
 }
@@ -1540,7 +1717,12 @@ pr_status pr_get_basis(pr_ctx* c, int level, int n, void* out, int* m_out) {
     const int* mp;
     if (level == 0) { base = c->V0; mp = c->m0; }
     else if (level == 1) { base = c->R1[c->r1cur] + (size_t)n * c->mcap1 * col; mp = c->m1[c->r1cur] + n; }
-    else { base = c->R2 + (size_t)n * c->mcap2 * col; mp = c->m2 + n; }
+    else if (c->wave > 0) {   // the last wave's level-2 bases only
+        if (n < c->r2_lo || n >= c->r2_hi)
+            return fail(c, PR_ERR_STATE, "wave mode: the level-2 basis of this subinterval is not resident");
+        base = c->R2 + (size_t)(n - c->r2_lo) * c->mcap2 * col;
+        mp = c->m2 + n;
+    } else { base = c->R2 + (size_t)n * c->mcap2 * col; mp = c->m2 + n; }
     int m = 0;
     PR_CUDA(cudaMemcpyAsync(&m, mp, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     PR_CUDA(cudaStreamSynchronize(c->st));
@@ -1593,6 +1775,7 @@ pr_status pr_op_pod(pr_ctx* c, const void* d_W, int w_f32, int n_cols, int B, do
                     void* d_R, int* m_out) {
     if (!c || !d_W || !d_R || !m_out || B < 1 || B > c->N || n_cols < 1) return PR_ERR_INVALID_ARG;
     if (n_cols > c->maxK || !(gamma > 0 && gamma <= 1)) return PR_ERR_INVALID_ARG;
+    if (c->wave > 0 && B > c->wave) return fail(c, PR_ERR_INVALID_ARG, "wave mode: B above the wave size");
     const int mmax = cap > 0 ? std::min(cap, n_cols) : n_cols;
     if (mmax > c->mscr) return fail(c, PR_ERR_INVALID_ARG, "POD dimension above the context's cap");
     pr_status s = ensure_ws(c);

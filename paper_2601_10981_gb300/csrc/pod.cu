@@ -2,7 +2,7 @@
 //   Gram W^T M W (M = I)           -> gram_kernel     (batched, split over points)
 //   eigenpairs, rank r, dimension m -> eig_pod_kernel  (cyclic Jacobi, FP64, one CTA/matrix)
 //   R = W Y_m Lambda_m^{-1/2}       -> tsmm_kernel     (tall-skinny multiply)
-//   CholQR2 re-orthonormalisation   -> gram + chol_inv_kernel + tsmm, twice
+//   Cholesky-QR re-orthonormalisation -> gram + chol_inv_kernel + tsmm, one pass
 // The Gram and projection stream every snapshot once per use; the small dense steps stay
 // in FP64 because their stability needs it (Gram-based POD squares the conditioning).
 #include "df.cuh"
