@@ -121,6 +121,10 @@ typedef struct pr_opts {
                                iterates are bit-identical for a fixed group_ctas.
                                pr_rewind can only undo iteration 1; pr_get_snapshots and
                                pr_get_basis(level 2) reach the last wave's subintervals only. */
+    int no_tensor_gram;     /* FP32 mode: 0 (default) computes the symmetric POD Grams of at
+                               most 64 columns (level 1, Cholesky QR) on the tensor cores
+                               with error-free BF16 digits (FP64-accurate, see pr_op_gram);
+                               1 keeps them in double-float arithmetic on the FP32 pipe.   */
 } pr_opts;
 
 /* Fine integrator.  PR_FINE_IMPLICIT_EULER: the paper's, eq. (semi-dis-eq), BiCGStab per
@@ -314,6 +318,17 @@ pr_status pr_op_fine(pr_ctx* ctx, const double* d_in, double* d_out, void* d_sna
 pr_status pr_op_pod(pr_ctx* ctx, const void* d_W, int w_f32, int n_cols, int B, double gamma,
                     int cap, void* d_R, int* m_out);
 
+/* Gram matrices G_b = W_b^T W_b of B snapshot matrices, step 1 of POD_Mode (Algorithm 1)
+ * (M = I).  d_W: B x n_cols x n^3 device doubles (column-major blocks as for pr_op_pod);
+ * d_G: B x n_cols x n_cols device doubles (row-major, symmetric).  tensor = 1: on the
+ * tensor cores (tcgen05.mma with BF16 operands and FP32 accumulation): each column is
+ * aligned to its largest magnitude and cut into eight balanced base-128 integer digits,
+ * which BF16 holds exactly; digit products are summed exactly in FP32 over 1024 points
+ * and then added in FP64 with their power-of-two weights, so the result is FP64-accurate
+ * (n_cols <= 64).  tensor = 0: FP64 arithmetic.  B <= n_sub + 1, n_cols <= the context's
+ * largest POD window.  Synchronises. */
+pr_status pr_op_gram(pr_ctx* ctx, const double* d_W, int n_cols, int B, double* d_G, int tensor);
+
 /* One coarse update of eq. (formula4) on subinterval [t, t+DeltaT] with the augmented
  * space [R, d(U)]:  d_out = G(U) + F - G(P U_prev).  d_R: m x n^3 doubles (orthonormal
  * columns), d_U, d_Uprev, d_F, d_out: n^3 doubles. */
@@ -346,18 +361,21 @@ pr_status pr_op_apply_L_noalloc(pr_ctx* ctx, const double* d_in, double* d_out, 
  * A submitted request waits in arrival order until its workspace (pr_workspace_bytes)
  * fits the memory budget next to the resident requests and the resident cap allows it;
  * it is then admitted (device workspace and stream of its own, initial state copied,
- * iteration 0 run) and stays resident until it finishes.  Each pr_server_step advances
- * every resident request by one parareal iteration: fine sweeps of requests with the
- * same n, box and precision share persistent launches (pr_fine_sweep_batch, up to 16
- * requests each); then every request's POD update and coarse sweep are issued on its
- * own stream before any is waited for, so that they overlap on the device; then the
- * convergence checks.  A request finishes when its max increment
- * max_n ||U^k_n - U^{k-1}_n|| / ||U^k_n|| <= tol or k = k_max; U^k_N (the state at the
- * end of the horizon) is copied to host memory and the workspace released, and waiting
- * requests are admitted in the same step.  The fine CTA-group size is tuned once per
- * (n, box, precision) by pr_tune_fine on the first request admitted with
- * opts.group_ctas = 0 and used for every later request of that shape; a request with
- * group_ctas > 0 keeps its own, and then gives the same result alone and in a mix.
+ * iteration 0 issued) and stays resident until it finishes.  Requests advance on their
+ * own iteration clocks, not in lock-step: each has at most one iteration in flight on its
+ * stream.  Each pr_server_step admits waiting requests; finds the requests whose work in
+ * flight has completed (polling for up to about a millisecond if none has), checks their
+ * convergence and retires the finished ones (max increment
+ * max_n ||U^k_n - U^{k-1}_n|| / ||U^k_n|| <= tol or k = k_max: U^k_N is copied to host
+ * memory, the workspace released and waiting requests admitted at once); and issues the
+ * next iteration of every ready request: fine sweeps of ready requests with the same n,
+ * box and precision share persistent launches (pr_fine_sweep_batch, up to 16 requests
+ * each), then each request's POD update and coarse sweep on its own stream, so that the
+ * requests' work overlaps on the device.  A small request thus finishes while a large
+ * one is mid-solve.  The fine CTA-group size is tuned once per (n, box, precision) by
+ * pr_tune_fine on the first request admitted with opts.group_ctas = 0 and used for every
+ * later request of that shape; a request with group_ctas > 0 keeps its own, and then
+ * gives the same result alone and in a mix.
  * Single-threaded: one thread calls the pr_server_* functions of a server.
  * ------------------------------------------------------------------------------------ */
 typedef struct pr_server pr_server;
@@ -389,9 +407,10 @@ pr_status pr_server_create(const pr_server_opts* opts, pr_server** out);
 void pr_server_destroy(pr_server* srv);
 /* Queue a request; *id numbers requests 0, 1, 2, ... in submission order. */
 pr_status pr_server_submit(pr_server* srv, const pr_request* req, int* id);
-/* Admit, advance every resident request by one iteration, retire finished ones, admit
- * again.  n_active / n_pending (may be NULL): resident and waiting requests after the
- * step.  Synchronises (the checks read increments). */
+/* Admit; check the requests whose iteration in flight completed (polling up to about a
+ * millisecond for one), retire finished ones and admit again; issue the next iteration of
+ * every ready request.  n_active / n_pending (may be NULL): resident and waiting requests
+ * after the step.  Call it repeatedly; it does not wait for all resident requests. */
 pr_status pr_server_step(pr_server* srv, int* n_active, int* n_pending);
 /* state: PR_REQ_*, k: iterations done, max_inc: increment of the last check. */
 pr_status pr_server_query(pr_server* srv, int id, int* state, int* k, double* max_inc);

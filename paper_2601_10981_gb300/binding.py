@@ -42,7 +42,7 @@ class pr_opts(C.Structure):
                 ("rank_tau", C.c_double), ("precision", C.c_int), ("lin_tol", C.c_double),
                 ("lin_maxit", C.c_int), ("aug_tol", C.c_double), ("group_ctas", C.c_int),
                 ("ctas_per_sm", C.c_int), ("spin_limit", C.c_longlong), ("method", C.c_int),
-                ("fine", C.c_int), ("wave", C.c_int)]
+                ("fine", C.c_int), ("wave", C.c_int), ("no_tensor_gram", C.c_int)]
 
 
 class pr_report(C.Structure):
@@ -118,6 +118,7 @@ _SIGS = {
     "pr_server_step": (C.c_int, [_P, _I, _I]),
     "pr_server_query": (C.c_int, [_P, C.c_int, _I, _I, _D]),
     "pr_get_fine_ms": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "pr_op_gram": (C.c_int, [_P, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "pr_server_result": (C.c_int, [_P, C.c_int, _D]),
     "pr_server_request_error": (C.c_char_p, [_P, C.c_int]),
     "pr_server_last_error": (C.c_char_p, [_P]),
@@ -408,6 +409,15 @@ class Parareal:
         self._check(self._lib.pr_op_pod(self.ctx, _tptr(W), w32, ncol, B, gamma, cap, _tptr(R),
                                         m.ctypes.data_as(_I)))
         return R, m
+
+    def op_gram(self, W, tensor: bool = True):
+        """G_b = W_b^T W_b of a (B, n_cols, n^3) float64 CUDA tensor; returns (B, n_cols, n_cols)."""
+        torch = self.torch
+        B, K = W.shape[0], W.shape[1]
+        G = torch.empty((B, K, K), dtype=torch.float64, device=W.device)
+        self._check(self._lib.pr_op_gram(self.ctx, C.c_void_p(W.data_ptr()), K, B, C.c_void_p(G.data_ptr()),
+                                         1 if tensor else 0))
+        return G
 
     def op_coarse_update(self, R, m: int, U, Uprev, F):
         out = self.torch.empty_like(U)

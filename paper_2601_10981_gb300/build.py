@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libpr_gb300.so"
-SOURCES = ["fine_f32.cu", "fine_f64.cu", "fine_pert.cu", "fine.cu", "pod.cu", "coarse.cu", "api.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["fine_f32.cu", "fine_f64.cu", "fine_pert.cu", "fine.cu", "pod.cu", "coarse.cu", "api.cu", "noalloc.cu", "server.cu", "gram_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr"]

@@ -127,6 +127,7 @@ struct pr_ctx {
     double* X = nullptr;
     double* gpart = nullptr;
     size_t gpart_n = 0;
+    unsigned long long* colmax = nullptr;   // [N + 1][64] column maxima of the tensor-core Gram
     unsigned* counters = nullptr;  // [N + 64]
     const void** colsA = nullptr;
     const void** colsB = nullptr;
@@ -254,6 +255,7 @@ size_t plan(pr_ctx* c, char* base) {
     c->X = b.take<double>((size_t)N * c->mscr * c->mscr);
     c->gpart_n = gram_part_doubles(Ng, NB + 1, c->maxK, c->maxK);
     c->gpart = b.take<double>(c->gpart_n);
+    c->colmax = b.take<unsigned long long>((size_t)(N + 1) * gram_tc_max_cols());
     c->counters = b.take<unsigned>((size_t)N + 64);
     c->colsA = b.take<const void*>((size_t)(N + 1) * c->ldcols);
     c->colsB = b.take<const void*>((size_t)(N + 1) * c->ldcols);
@@ -393,6 +395,16 @@ pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const i
 // (c->colsA, c->KA).  Result: dest + b*dest_bstride (columns of Ng), dims m_dest[b].
 // ortho_blocks: the snapshot columns are blocks of orthonormal bases (c->colblk says
 // which); the FP32 mode then takes their diagonal Gram blocks as the identity.
+// Symmetric Grams of the FP32 mode with at most 64 FP64 columns run on the tensor cores
+// (error-free BF16 digit products, FP64-accurate; gram_tc.cu) unless the options ask for
+// the double-float kernel; every other Gram runs in double-float or FP64.
+cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32) {
+    if (c->fp32 && !c->o.no_tensor_gram && !in_f32 && ga.sym && ga.colblk == nullptr &&
+        ga.maxKA <= gram_tc_max_cols() && ga.B <= (c->wave > 0 ? c->wave : c->N) + 1)
+        return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st);
+    return launch_gram(ga, in_f32, in_f32, c->st);
+}
+
 pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, bool in_f32, int cap,
                        int mmax, char* dest, size_t dest_bstride_elems, int* m_dest,
                        bool ortho_blocks = false) {
@@ -418,7 +430,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     ga.df = c->fp32;   // FP32 mode: double-float Grams and projections on the FP32 pipe
     // the bases leave Cholesky QR orthonormal to ~1e-15, far below the FP32 mode's accuracy
     ga.colblk = (c->fp32 && ortho_blocks && !in_f32) ? c->colblk : nullptr;
-    PR_CUDA(launch_gram(ga, in_f32, in_f32, st));
+    PR_CUDA(gram_auto(c, ga, in_f32));
     // eigenpairs + dimension + C = Y_m Lambda_m^{-1/2}
     EigArgs ea{};
     ea.G = c->gout;
@@ -467,7 +479,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     gb.maxKB = mmax;
     gb.ldG = mmax;
     gb.ldG_b = (long long)mmax * mmax;
-    PR_CUDA(launch_gram(gb, f32, f32, st));
+    PR_CUDA(gram_auto(c, gb, f32));
     PR_CUDA(launch_chol_inv(c->gout, mmax, (long long)mmax * mmax, m_dest, mmax, B, c->X, mmax,
                             (long long)mmax * mmax, c->derr, st));
     TsmmArgs tb = ta;
@@ -862,6 +874,7 @@ void pr_opts_init(pr_opts* o) {
     o->method = PR_METHOD_ADAPTIVE;
     o->fine = PR_FINE_IMPLICIT_EULER;
     o->wave = 0;
+    o->no_tensor_gram = 0;
 }
 
 const char* pr_status_string(pr_status s) {
@@ -1789,6 +1802,40 @@ pr_status pr_op_pod(pr_ctx* c, const void* d_W, int w_f32, int n_cols, int B, do
                      (size_t)mmax * c->Ng, c->mop);
     if (s != PR_OK) return s;
     PR_CUDA(cudaMemcpyAsync(m_out, c->mop, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st));
+    return pr_sync(c);
+}
+
+pr_status pr_op_gram(pr_ctx* c, const double* d_W, int n_cols, int B, double* d_G, int tensor) {
+    if (!c || !d_W || !d_G || B < 1 || n_cols < 1) return PR_ERR_INVALID_ARG;
+    const int bmax = (c->wave > 0 ? c->wave : c->N) + 1;   // partial sums: gram_part_doubles(Ng, bmax, ...)
+    if (B > bmax || n_cols > c->maxK) return fail(c, PR_ERR_INVALID_ARG, "pr_op_gram: B or n_cols above the context's sizes");
+    if (tensor && n_cols > gram_tc_max_cols())
+        return fail(c, PR_ERR_INVALID_ARG, "pr_op_gram: the tensor-core Gram takes at most 64 columns");
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    int nc = n_cols;
+    PR_CUDA(cudaMemcpyAsync(c->cnst + 2, &nc, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    s = cols_contig(c, (const char*)d_W, (size_t)n_cols * c->Ng * sizeof(double), c->cnst + 2, 0, B, c->colsA, c->KA,
+                    sizeof(double));
+    if (s != PR_OK) return s;
+    GramArgs ga{};
+    ga.colsA = c->colsA;
+    ga.colsB = c->colsA;
+    ga.KA = c->KA;
+    ga.KB = c->KA;
+    ga.ldcols = c->ldcols;
+    ga.Ng = c->Ng;
+    ga.B = B;
+    ga.maxKA = n_cols;
+    ga.maxKB = n_cols;
+    ga.sym = true;
+    ga.part = c->gpart;
+    ga.counter = c->counters;
+    ga.G = d_G;
+    ga.ldG = n_cols;
+    ga.ldG_b = (long long)n_cols * n_cols;
+    if (tensor) PR_CUDA(launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st));
+    else PR_CUDA(launch_gram(ga, false, false, c->st));
     return pr_sync(c);
 }
 

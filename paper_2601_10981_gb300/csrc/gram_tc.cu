@@ -1,0 +1,401 @@
+// Gram matrix G = W^T W of FP64 columns on GB300's fifth-generation tensor cores
+// (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory), with FP64 accuracy.
+//
+// Step 1 of POD_Mode (Algorithm 1) forms the Gram matrix of the snapshots; its trailing
+// eigenvalues (down to 1e-13 of the largest) decide the POD dimension, so the Gram must
+// be as accurate as an FP64 one (~1e-15 relative).  A BF16 or TF32 product is not.  Here
+// every FP64 value is cut, error-free, into integer digits that BF16 holds exactly, and
+// the tensor core multiplies digits:
+//
+//   column i is aligned to its largest magnitude, 2^(e_i - 2) > max_p |W[p, i]|, and each
+//   value is written as  W[p, i] = 2^e_i * sum_{s=1..8} d_s(p, i) 2^(-7 s)  (+ < 2^(e_i-56))
+//   with balanced digits d_s in [-64, 63] (the value truncated to 2^-53 of the column's
+//   largest magnitude; the headroom bit keeps the top digit from carrying out);
+//   G[i, j] = 2^(e_i + e_j) * sum_{s,t} 2^(-7 (s + t)) sum_p d_s(p, i) d_t(p, j).
+//
+// A digit product is an integer of at most 2^12 in magnitude, so a sum of 4096 of them
+// is an integer below 2^24 and exact in the FP32 accumulator.  Products of equal weight
+// (equal s + t) share an accumulator: with the two slices s, s+1 (s odd) stacked as the
+// 128 rows of the MMA's A operand and slice t as its B operand, the accumulator of tile c
+// collects, in its top 64 lanes, the products with s + t = c and, in its bottom 64 lanes,
+// those with s + t = c + 1, from at most four (s, t) pairs each.  Every 1024 points
+// (4 x 1024 x 2^12 = 2^24) the eight tiles (c = 2..9, all pairs with s + t <= 9; the
+// dropped ones weigh below 2^-58 of a leading product) are read back with tcgen05.ld and
+// added into FP64 accumulators with their weights, which are powers of two.  The only
+// roundings are those FP64 additions and the 56-bit truncation of each value, so the
+// result has the accuracy of an FP64 Gram.
+//
+// Work split: a persistent grid, one CTA per SM (the eight tiles fill the SM's 512 TMEM
+// columns); a CTA takes work units (batch item, chunk of points) in turn and, per stage
+// of 64 points, its 128 threads load the FP64 values, cut them into digits and store them
+// in shared memory in the canonical K-major layout of the MMA operands (8 x 16-byte core
+// matrices, no swizzle), then one thread issues the 80 MMAs of the stage and commits
+// them to an mbarrier.  Every wait on the mbarrier is bounded: on time-out the kernel
+// records PR_ERR_TIMEOUT, waits (bounded) for its MMAs in flight, frees its tensor memory
+// and returns.  Column maxima come from a pre-pass (colmax_kernel).
+#include "pr_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <stdint.h>
+
+namespace pr {
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_N = 64;             // columns handled (K <= 64)
+constexpr int TC_PTS = 64;           // points per shared-memory stage
+constexpr int TC_SLICES = 8;         // digits per value
+constexpr int TC_TILES = 8;          // accumulator tiles c = 2..9
+constexpr int TC_STAGES_PER_DRAIN = 16;   // 16 x 64 = 1024 points per accumulation
+constexpr int TC_TMEM_COLS = TC_TILES * TC_N;   // 512: all of an SM's tensor memory
+// operand layout: core matrix (8 rows x 8 BF16 = 128 B) of slice s, row group g (rows
+// 8g..8g+7, i.e. columns of W), K group kg (points 8kg..8kg+7) at
+// ((s * 8 + g) * 8 + kg) * 128 bytes; LBO (next core matrix along K) = 128 B, SBO (next
+// 8-row group) = 1024 B
+constexpr int TC_LBO = 128;
+constexpr int TC_SBO = 1024;
+constexpr int TC_STAGE_BYTES = TC_SLICES * 8 * TC_SBO;   // 64 KiB
+static_assert(TC_STAGE_BYTES >= TC_N * TC_N * (int)sizeof(double), "the stage buffer holds the half sums");
+constexpr long long TC_SPIN_LIMIT = 1LL << 24;   // polls of an mbarrier (~1 s with the sleeps)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// UMMA shared-memory matrix descriptor (K-major, no swizzle): start address, leading
+// (K) and stride (M/N) byte offsets, each >> 4; descriptor version 1 at bit 46.
+__device__ __forceinline__ uint64_t umma_desc(unsigned saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) |
+           ((uint64_t)(TC_SBO >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and
+// 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
+                              ((unsigned)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier (non-blocking test, short sleeps: about
+// a second at most); false on time-out.
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+    for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+        unsigned ok = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it >= 64) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+// Fixed-point value of x in units of 2^(e - 56) (|x| < 2^(e - 2), so |result| < 2^54),
+// truncated toward zero, from the bits of x (integer operations only).
+__device__ __forceinline__ long long fixed56(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) return 0;   // zero or subnormal (below 2^-1022)
+    const long long mant = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
+    const int sh = ex - 1019 - e;   // x * 2^(56 - e) = mant * 2^sh, sh <= 1
+    long long y;
+    if (sh >= 0) y = mant << sh;
+    else y = (sh <= -63) ? 0 : (mant >> (-sh));
+    return bits < 0 ? -y : y;
+}
+
+// Balanced base-128 digits of y (|y| < 2^54): y = sum_{s=1..8} d_s 128^(8-s),
+// d_s in [-64, 63]; d[s-1] = d_s.  (The seven lower steps leave |y| < 2^54 / 128^7 + 1/2
+// < 33, so the top digit takes what is left without a carry.)
+__device__ __forceinline__ void digits8(long long y, int (&d)[TC_SLICES]) {
+#pragma unroll
+    for (int s = TC_SLICES - 1; s >= 0; --s) {
+        const int lo = (((int)(y & 127)) + 64) & 127;
+        d[s] = lo - 64;
+        y = (y - d[s]) >> 7;
+    }
+}
+
+__device__ __forceinline__ unsigned pack_bf16x2(int a, int b) {
+    const __nv_bfloat16 x = __float2bfloat16_rn((float)a), y = __float2bfloat16_rn((float)b);
+    return (unsigned)__bfloat16_as_ushort(x) | ((unsigned)__bfloat16_as_ushort(y) << 16);
+}
+
+}  // namespace
+
+// colmax[b * ld + i] = bit pattern of max_p |W_b[p, i]| (non-negative doubles order like
+// their bit patterns), by atomicMax from each CTA's chunk; the buffer starts at zero.
+__global__ void __launch_bounds__(256) colmax_kernel(GramArgs a, long long CH, unsigned long long* colmax,
+                                                     int ld) {
+    const int b = blockIdx.y;
+    const int K = a.KA[b];
+    const long long p_lo = (long long)blockIdx.x * CH, p_hi = min(a.Ng, p_lo + CH);
+    const void* const* cols = a.colsA + (size_t)b * a.ldcols;
+    __shared__ unsigned long long red[8];
+    for (int i = 0; i < K; ++i) {
+        const double* c = reinterpret_cast<const double*>(cols[i]);
+        unsigned long long m = 0ull;
+        for (long long p = p_lo + threadIdx.x; p < p_hi; p += blockDim.x) {
+            const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(c[p]));
+            m = v > m ? v : m;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+            m = o > m ? o : m;
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0ull;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = red[w] > t ? red[w] : t;
+            if (t) atomicMax(colmax + (size_t)b * ld + i, t);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long long CH, int chunks,
+                                                                const unsigned long long* colmax, int ld,
+                                                                int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ unsigned s_tmem;
+    __shared__ int s_e[TC_N];
+    __shared__ int s_last;
+    unsigned char* stage = smem_raw;   // TC_STAGE_BYTES, 1024-aligned
+    double* sacc = reinterpret_cast<double*>(smem_raw);   // reused for the bottom-half sums
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const unsigned mbar = smem_u32(&s_mbar);
+    const unsigned stage_s = smem_u32(stage);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    unsigned parity = 0;
+    bool failed = false;
+    // this thread's accumulator row: lane r of every tile; top half (r < 64) holds the
+    // products with s + t = c, the bottom half those with s + t = c + 1
+    const int row = tid;
+    const bool top = row < 64;
+    const int irow = top ? row : row - 64;
+    double acc[TC_N];
+
+    const int units = a.B * chunks;
+    for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+        const int b = u / chunks, chunk = u - b * chunks;
+        const int K = a.KA[b];
+        const long long p_lo = (long long)chunk * CH, p_hi = min(a.Ng, p_lo + CH);
+        const void* const* cols = a.colsA + (size_t)b * a.ldcols;
+        if (tid < TC_N) {
+            const unsigned long long m = (tid < K) ? colmax[(size_t)b * ld + tid] : 0ull;
+            // 2^(e - 2) > max |W[:, i]|:  e = unbiased exponent of the maximum + 3
+            s_e[tid] = m ? (int)((m >> 52) & 0x7FF) - 1023 + 3 : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < TC_N; ++j) acc[j] = 0.0;
+        __syncthreads();
+        int nst = 0;   // stages since the last drain
+        for (long long p0 = p_lo; p0 < p_hi; p0 += TC_PTS) {
+            // ---- digits of 64 points x 64 columns into the stage (4 items a thread:
+            //      one column and 8 consecutive points each)
+#pragma unroll 1
+            for (int it = tid; it < TC_N * 8; it += TC_THREADS) {
+                const int col = it >> 3, kg = it & 7;
+                unsigned w[TC_SLICES][4];   // slice s: the 8 points' digits as BF16 pairs
+                const long long pb = p0 + kg * 8;
+                const bool live = col < K;
+                const double* c = live ? reinterpret_cast<const double*>(cols[col]) : nullptr;
+                const int e = s_e[col];
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    int d0[TC_SLICES], d1[TC_SLICES];
+                    const double x0 = (live && pb + k < p_hi) ? c[pb + k] : 0.0;
+                    const double x1 = (live && pb + k + 1 < p_hi) ? c[pb + k + 1] : 0.0;
+                    digits8(fixed56(x0, e), d0);
+                    digits8(fixed56(x1, e), d1);
+#pragma unroll
+                    for (int sl = 0; sl < TC_SLICES; ++sl) w[sl][k >> 1] = pack_bf16x2(d0[sl], d1[sl]);
+                }
+                const int g = col >> 3, rho = col & 7;
+#pragma unroll
+                for (int sl = 0; sl < TC_SLICES; ++sl)
+                    *reinterpret_cast<uint4*>(stage + ((sl * 8 + g) * 8 + kg) * 128 + rho * 16) =
+                        make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            // ---- 4 K-steps of 16 points x 20 (s, t) pairs
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                for (int k = 0; k < TC_PTS / 16; ++k) {
+                    bool fresh[TC_TILES];
+#pragma unroll
+                    for (int c = 0; c < TC_TILES; ++c) fresh[c] = (nst == 0 && k == 0);
+#pragma unroll 1
+                    for (int sa = 0; sa < TC_SLICES; sa += 2) {   // A: slices sa, sa + 1 (0-based)
+                        for (int t = 0; sa + t < TC_TILES; ++t) {  // B: slice t; tile c = sa + t
+                            const int c = sa + t;
+                            const uint64_t ad = umma_desc(stage_s + (sa * 8) * TC_SBO + (2 * k) * TC_LBO);
+                            const uint64_t bdsc = umma_desc(stage_s + (t * 8) * TC_SBO + (2 * k) * TC_LBO);
+                            mma_bf16(tmem + (unsigned)(c * TC_N), ad, bdsc, fresh[c] ? 0u : 1u);
+                            fresh[c] = false;
+                        }
+                    }
+                }
+                mma_commit(mbar);
+            }
+            // every thread waits; one vote decides, so no thread leaves the loop alone
+            failed = __syncthreads_or(mbar_wait(mbar, parity) ? 0 : 1) != 0;
+            if (failed) break;
+            parity ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            ++nst;
+            if (nst == TC_STAGES_PER_DRAIN || p0 + TC_PTS >= p_hi) {
+                // ---- drain: this thread's lane of every tile, weights 2^(-7 q)
+                const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+#pragma unroll 1
+                for (int c = 0; c < TC_TILES; ++c) {
+                    const int q = c + 2 + (top ? 0 : 1);
+                    const double wq = ldexp(1.0, -7 * q);
+#pragma unroll
+                    for (int j0 = 0; j0 < TC_N; j0 += 16) {
+                        float v[16];
+                        tmem_ld16(lane_base + (unsigned)(c * TC_N + j0), v);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) acc[j0 + e] = fma((double)v[e], wq, acc[j0 + e]);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                nst = 0;
+            }
+        }
+        if (failed) break;
+        // ---- the unit's partial Gram: top + bottom halves, scaled by 2^(e_i + e_j)
+        __syncthreads();   // the stage buffer is free (every MMA of the unit completed)
+        if (!top) {
+#pragma unroll
+            for (int j = 0; j < TC_N; ++j) sacc[irow * TC_N + j] = acc[j];
+        }
+        __syncthreads();
+        const size_t outsz = (size_t)a.maxKA * a.maxKB;
+        double* mypart = a.part + ((size_t)b * chunks + chunk) * outsz;
+        if (top && irow < K) {
+            const int ei = s_e[irow];
+#pragma unroll
+            for (int j = 0; j < TC_N; ++j)
+                if (j >= irow && j < K)
+                    mypart[(size_t)irow * a.maxKB + j] = ldexp(acc[j] + sacc[irow * TC_N + j], ei + s_e[j]);
+        }
+        // the last unit of item b sums the chunk partials in chunk order
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned ticket = atom_add_acq_rel_u32(a.counter + b, 1u);
+            s_last = (ticket == (unsigned)chunks - 1u);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const double* bpart = a.part + (size_t)b * chunks * outsz;
+            double* Gb = a.G + (size_t)b * a.ldG_b;
+            for (int o = tid; o < K * K; o += TC_THREADS) {
+                const int i = o / K, j = o - i * K;
+                if (j < i) continue;
+                double s = 0.0;
+                for (int cc = 0; cc < chunks; ++cc) s += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
+                Gb[(size_t)i * a.ldG + j] = s;
+                Gb[(size_t)j * a.ldG + i] = s;
+            }
+            if (tid == 0) st_relaxed_u32(a.counter + b, 0u);
+        }
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0) record_error(err, DERR_TIMEOUT);
+        // the MMAs of the stage may still be running: wait once more (bounded) before the
+        // tensor memory is released
+        mbar_wait(mbar, parity);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+int gram_tc_max_cols() { return TC_N; }
+
+cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld, int* err, cudaStream_t st) {
+    if (!a.sym || a.maxKA > TC_N || a.maxKA <= 0 || !colmax || !err || ld < a.maxKA) return cudaErrorInvalidValue;
+    if (a.B <= 0) return cudaSuccess;
+    // the chunks of the other Gram kernels, so that the partial buffer (gram_part_doubles)
+    // fits; any chunk length works for this kernel
+    const int chunks = gram_chunks(a.Ng);
+    const long long CH = (a.Ng + chunks - 1) / chunks;
+    cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)a.B * ld, st);
+    if (e != cudaSuccess) return e;
+    colmax_kernel<<<dim3(chunks, a.B), 256, 0, st>>>(a, CH, colmax, ld);
+    ++g_launch_count;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one CTA an SM: the tiles take all 512 tensor-memory columns; the shared-memory request
+    // (stage buffer plus slack, above half an SM) keeps a second CTA off the SM
+    const size_t smem = 120 * 1024;
+    e = cudaFuncSetAttribute((const void*)gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(sms, a.B * chunks));
+    gram_tc_kernel<<<grid, TC_THREADS, smem, st>>>(a, CH, chunks, colmax, ld, err);
+    ++g_launch_count;
+    return cudaGetLastError();
+}
+
+}  // namespace pr

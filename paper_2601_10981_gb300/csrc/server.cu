@@ -3,29 +3,36 @@
 //
 // A request waits in a FIFO until its context's workspace fits the memory budget and the
 // cap on resident requests; it is then admitted (workspace allocated, initial state
-// copied, iteration 0 run on its own stream) and stays resident until it finishes.  Each
-// pr_server_step advances every resident request by one parareal iteration:
-//   1. fine sweeps: requests with the same n, box and precision share one persistent
-//      launch (pr_fine_sweep_batch, up to FINE_MAX_JOBS requests per launch);
-//   2. POD update and coarse sweep of every request, issued on the request's own stream
-//      before any of them is waited for, so that they overlap on the device;
-//   3. convergence checks; a request whose max increment is <= tol, or whose k reached
-//      k_max, copies U^k_N to host memory and releases its workspace, which lets the
-//      next waiting requests in at the following step.
-// The CTA-group size of the fine launch is tuned once per (n, precision) by
-// pr_tune_fine on the first request admitted with group_ctas = 0, and reused for every
-// later request of that shape, so that batched and single launches tile a subinterval
-// the same way.
+// copied, iteration 0 issued on its own stream) and stays resident until it finishes.
+// Requests advance on their own iteration clocks, not in lock-step: each resident request
+// has at most one iteration in flight on its stream, followed by an event.  A
+// pr_server_step
+//   1. admits waiting requests while memory and the resident cap allow;
+//   2. finds the requests whose in-flight work has completed (event queries; if none has,
+//      it polls for up to about a millisecond), runs their convergence checks, retires the
+//      finished ones: U^k_N is copied to host memory and the workspace released, so the
+//      next waiting requests are admitted in the same step;
+//   3. issues the next iteration of every ready request: fine sweeps of ready requests
+//      with the same n, box and precision share one persistent launch
+//      (pr_fine_sweep_batch, up to FINE_MAX_JOBS requests per launch), then each request's
+//      POD update and coarse sweep on its own stream, then its event.
+// A small request therefore finishes while a large one is mid-solve, and its iterations
+// never wait for another request's.  The CTA-group size of the fine launch is tuned once
+// per (n, precision) by pr_tune_fine on the first request admitted with group_ctas = 0,
+// and reused for every later request of that shape, so that batched and single launches
+// tile a subinterval the same way (results are then identical alone and in the mix).
 #include "../../include/parareal.h"
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <deque>
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -42,7 +49,10 @@ struct Req {
     void* ws = nullptr;
     size_t bytes = 0;
     cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;      // recorded after the work in flight
+    bool in_flight = false;        // iteration k + 1 (or iteration 0) issued, not checked
     int k = 0;
+    int issued_k = 0;              // iteration in flight (k + 1) or last issued
     int k_max = 0;
     double inc = INFINITY;
     std::vector<double> result;
@@ -88,6 +98,11 @@ void release(pr_server* s, Req& q) {
         cudaStreamDestroy(q.st);
         q.st = nullptr;
     }
+    if (q.ev) {
+        cudaEventDestroy(q.ev);
+        q.ev = nullptr;
+    }
+    q.in_flight = false;
     if (q.ws) {
         cudaFree(q.ws);
         q.ws = nullptr;
@@ -152,6 +167,11 @@ void admit(pr_server* s) {
             q.st = nullptr;
             st = PR_ERR_CUDA;
         }
+        if (st == PR_OK && cudaEventCreateWithFlags(&q.ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            q.ev = nullptr;
+            st = PR_ERR_CUDA;
+        }
         if (st == PR_OK) st = pr_set_stream(q.ctx, q.st);
         if (st == PR_OK) st = pr_set_initial(q.ctx, q.u0.data(), q.f.empty() ? nullptr : q.f.data());
         if (st == PR_OK) st = pr_iteration0(q.ctx);
@@ -168,10 +188,57 @@ void admit(pr_server* s) {
         q.u0.shrink_to_fit();
         q.f.clear();
         q.f.shrink_to_fit();
+        if (cudaEventRecord(q.ev, q.st) != cudaSuccess) {
+            cudaGetLastError();
+            mark_failed(s, q, PR_ERR_CUDA, "admission");
+            continue;
+        }
         q.state = PR_REQ_ACTIVE;
         q.k = 0;
+        q.in_flight = true;   // iteration 0
         s->active.push_back(q.id);
     }
+}
+
+// Has the request's in-flight work completed?  (An event error fails the request.)
+bool work_done(pr_server* s, Req& q) {
+    const cudaError_t e = cudaEventQuery(q.ev);
+    if (e == cudaErrorNotReady) return false;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mark_failed(s, q, PR_ERR_CUDA, "event query");
+    }
+    return true;
+}
+
+// A request whose in-flight work completed: check the iteration it ran (none after
+// iteration 0) and retire it if it is finished.  Returns true if it stays active.
+bool settle(pr_server* s, Req& q) {
+    q.in_flight = false;
+    if (q.state != PR_REQ_ACTIVE) return false;
+    if (q.issued_k > q.k) {
+        double inc = 0.0, e = 0.0;
+        pr_status st = pr_check(q.ctx, q.issued_k, &inc, &e);
+        if (st != PR_OK) {
+            mark_failed(s, q, st, "convergence check");
+            return false;
+        }
+        q.k = q.issued_k;
+        q.inc = inc;
+        if (inc <= q.r.tol || q.k >= q.k_max) {
+            const long long Ng = (long long)q.r.grid.n * q.r.grid.n * q.r.grid.n;
+            q.result.resize((size_t)Ng);
+            st = pr_get_interface(q.ctx, q.r.n_sub, q.result.data());
+            if (st != PR_OK) {
+                mark_failed(s, q, st, "result read-back");
+                return false;
+            }
+            q.state = PR_REQ_DONE;
+            release(s, q);
+            return false;
+        }
+    }
+    return true;
 }
 
 }  // namespace
@@ -236,15 +303,43 @@ pr_status pr_server_submit(pr_server* s, const pr_request* r, int* id) {
 pr_status pr_server_step(pr_server* s, int* n_active, int* n_pending) {
     if (!s) return PR_ERR_INVALID_ARG;
     admit(s);
-    // 1. fine sweeps, batched by shape
-    std::vector<Req*> act;
-    for (int id : s->active) act.push_back(s->reqs[id].get());
+    // 1. requests whose in-flight work completed; wait (polling) until at least one has,
+    //    for at most about a millisecond, so that the caller can submit new arrivals
+    std::vector<Req*> ready;
+    const auto t_start = std::chrono::steady_clock::now();
+    for (int pass = 0;; ++pass) {
+        bool any_active = false;
+        for (int id : s->active) {
+            Req* q = s->reqs[id].get();
+            if (q->state != PR_REQ_ACTIVE) continue;
+            any_active = true;
+            if (q->in_flight && work_done(s, *q) && settle(s, *q)) ready.push_back(q);
+            else if (!q->in_flight && q->state == PR_REQ_ACTIVE) ready.push_back(q);
+        }
+        if (!ready.empty() || !any_active) break;
+        bool left = false;
+        for (int id : s->active) left = left || s->reqs[id]->state == PR_REQ_ACTIVE;
+        if (!left) break;   // every resident request finished in this pass
+        if (std::chrono::steady_clock::now() - t_start > std::chrono::microseconds(1000)) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    // finished requests left: their memory lets waiting requests in now
+    {
+        std::vector<int> still;
+        for (int id : s->active)
+            if (s->reqs[id]->state == PR_REQ_ACTIVE) still.push_back(id);
+        s->active.swap(still);
+    }
+    admit(s);
+    // 2. the next iteration of every ready request: fine sweeps batched by shape
     std::map<ShapeKey, std::vector<Req*>> by_shape;
-    for (Req* q : act) by_shape[shape_of(q->r)].push_back(q);
+    for (Req* q : ready)
+        if (q->state == PR_REQ_ACTIVE) by_shape[shape_of(q->r)].push_back(q);
     for (auto& kv : by_shape) {
         auto& v = kv.second;
-        for (size_t i0 = 0; i0 < v.size(); i0 += s->o.batch_fine ? kMaxJobsPerLaunch : 1) {
-            const size_t i1 = std::min(v.size(), i0 + (s->o.batch_fine ? kMaxJobsPerLaunch : 1));
+        const size_t per = s->o.batch_fine ? kMaxJobsPerLaunch : 1;
+        for (size_t i0 = 0; i0 < v.size(); i0 += per) {
+            const size_t i1 = std::min(v.size(), i0 + per);
             std::vector<pr_ctx*> cs;
             std::vector<int> ks;
             for (size_t i = i0; i < i1; ++i) {
@@ -256,41 +351,28 @@ pr_status pr_server_step(pr_server* s, int* n_active, int* n_pending) {
                 for (size_t i = i0; i < i1; ++i) mark_failed(s, *v[i], st, "fine sweep");
         }
     }
-    // 2. POD update and coarse sweep on each request's stream, all issued before any wait
-    for (Req* q : act) {
+    // 3. POD update, coarse sweep and the completion event on each request's stream
+    for (Req* q : ready) {
         if (q->state != PR_REQ_ACTIVE) continue;
         pr_status st = pr_pod_update(q->ctx, q->k + 1);
         if (st == PR_OK) st = pr_coarse_sweep(q->ctx, q->k + 1);
-        if (st != PR_OK) mark_failed(s, *q, st, "POD update / coarse sweep");
-    }
-    // 3. checks, finished requests leave
-    for (Req* q : act) {
-        if (q->state != PR_REQ_ACTIVE) continue;
-        double inc = 0.0, e = 0.0;
-        pr_status st = pr_check(q->ctx, q->k + 1, &inc, &e);
+        if (st == PR_OK && cudaEventRecord(q->ev, q->st) != cudaSuccess) {
+            cudaGetLastError();
+            st = PR_ERR_CUDA;
+        }
         if (st != PR_OK) {
-            mark_failed(s, *q, st, "convergence check");
+            mark_failed(s, *q, st, "POD update / coarse sweep");
             continue;
         }
-        q->k += 1;
-        q->inc = inc;
-        if (inc <= q->r.tol || q->k >= q->k_max) {
-            const long long Ng = (long long)q->r.grid.n * q->r.grid.n * q->r.grid.n;
-            q->result.resize((size_t)Ng);
-            st = pr_get_interface(q->ctx, q->r.n_sub, q->result.data());
-            if (st != PR_OK) {
-                mark_failed(s, *q, st, "result read-back");
-                continue;
-            }
-            q->state = PR_REQ_DONE;
-            release(s, *q);
-        }
+        q->issued_k = q->k + 1;
+        q->in_flight = true;
     }
-    std::vector<int> still;
-    for (int id : s->active)
-        if (s->reqs[id]->state == PR_REQ_ACTIVE) still.push_back(id);
-    s->active.swap(still);
-    admit(s);   // freed memory lets waiting requests start their iteration 0 now
+    {
+        std::vector<int> still;
+        for (int id : s->active)
+            if (s->reqs[id]->state == PR_REQ_ACTIVE) still.push_back(id);
+        s->active.swap(still);
+    }
     if (n_active) *n_active = (int)s->active.size();
     if (n_pending) *n_pending = (int)s->pending.size();
     return PR_OK;

@@ -88,16 +88,17 @@ def test_tune_fine_keeps_the_iterate_and_fixes_the_group_size(gpu):
 
 
 def run_server(bd, reqs, prec, tol, **srv_kw):
+    import time
     srv = bd.Server(**srv_kw)
     ids = [srv.submit(w, w.u0(), w.f(), tol=tol, precision=prec, group_ctas=4) for w in reqs]
-    most_active, steps = 0, 0
+    most_active = 0
+    t0 = time.time()
     while True:
         act, pend = srv.step()
         most_active = max(most_active, act)
-        steps += 1
         if act == 0 and pend == 0:
             break
-        assert steps < 200
+        assert time.time() - t0 < 120
     out = {}
     for w, i in zip(reqs, ids):
         st, k, inc = srv.query(i)
@@ -162,10 +163,48 @@ def test_server_admission_and_failures(gpu):
     srv = bd.Server()
     ib = srv.submit(bad, bad.u0(), None, tol=1e-6)
     ic = srv.submit(c, c.u0(), c.f(), tol=1e-6)
-    for _ in range(50):
+    import time
+    t0 = time.time()
+    while time.time() - t0 < 60:
         act, pend = srv.step()
         if act == 0 and pend == 0:
             break
     assert srv.query(ib)[0] == bd.PR_REQ_FAILED
     assert srv.query(ic)[0] == bd.PR_REQ_DONE
+    srv.close()
+
+
+def test_small_request_finishes_while_a_large_one_is_mid_solve(gpu):
+    """Requests run on their own iteration clocks: a small problem submitted beside a
+    large one does many iterations while the large one does few, finishes first, and the
+    large one's result is still the one it gives alone."""
+    import time
+    bd, torch = gpu
+    big = pi.Workload("big", 48, pi.Flow("abc"), 0.01, 2.0, 32, 1e-3, n_snap=16, m_cap=8)
+    small = pi.tiny(n=8, n_sub=4, name="small")
+    srv = bd.Server()
+    ib = srv.submit(big, big.u0(), None, tol=1e-13, precision=0, group_ctas=4)
+    is_ = srv.submit(small, small.u0(), None, tol=1e-9, precision=0, group_ctas=4)
+    t0 = time.time()
+    while srv.query(is_)[0] not in (bd.PR_REQ_DONE, bd.PR_REQ_FAILED):
+        srv.step()
+        assert time.time() - t0 < 60
+    st_s, k_s, _ = srv.query(is_)
+    st_b, k_b, _ = srv.query(ib)
+    assert st_s == bd.PR_REQ_DONE, srv.request_error(is_)
+    assert st_b == bd.PR_REQ_ACTIVE and k_b < k_s, (k_b, k_s)   # mid-solve, behind
+    while srv.query(ib)[0] == bd.PR_REQ_ACTIVE:
+        srv.step()
+        assert time.time() - t0 < 120
+    assert srv.query(ib)[0] == bd.PR_REQ_DONE, srv.request_error(ib)
+    res_b, res_s = srv.result(ib), srv.result(is_)
+    srv.close()
+    alone, _ = run_server(bd, [small], 0, 1e-9)
+    assert np.array_equal(alone["small"][0], res_s)
+    srv = bd.Server()
+    i = srv.submit(big, big.u0(), None, tol=1e-13, precision=0, group_ctas=4)
+    while srv.query(i)[0] == bd.PR_REQ_ACTIVE or srv.query(i)[0] == bd.PR_REQ_PENDING:
+        srv.step()
+        assert time.time() - t0 < 240
+    assert np.array_equal(srv.result(i), res_b)
     srv.close()
