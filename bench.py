@@ -554,6 +554,7 @@ def run_ours(args):
     w = workload(args.config, args.subintervals)
     prec = bd.PR_FP32 if args.precision == "fp32" else bd.PR_FP64
     copts = dict(CONFIG_OPTS[args.config])
+    copts["gram_mode"] = {"auto": bd.PR_GRAM_AUTO, "df": bd.PR_GRAM_DF, "tensor": bd.PR_GRAM_TENSOR}[args.gram_mode]
     s = bd.Parareal.from_workload(w, precision=prec, **copts)
     st = s.stream
     s.set_initial(w.u0(), w.f())
@@ -638,7 +639,7 @@ def run_ours(args):
                                        if traffic is not None else None,
                      "kernel": "fine_kernel (persistent BiCGStab fine sweep)" + (
                          f", {copts['wave']} subintervals a launch (wave mode), time summed over the waves"
-                         if copts else ""),
+                         if copts.get("wave") else ""),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                                     if peak_kind == "measured" else peak_kind,
                      "bytes_per_dof_step": bpd, "lin_iters_per_step": lin_mean,
@@ -647,7 +648,7 @@ def run_ours(args):
     }
     s.close()
     del s
-    if copts:
+    if copts.get("wave"):
         line["config"]["form"] = (f"wave mode: each iteration streamed in waves of {copts['wave']} "
                                   f"subintervals (fine sweep, level-1/2 POD, Galerkin, coarse sweep)")
     if rank == 0 and args.extras and args.config == "c2":
@@ -697,6 +698,8 @@ def main():
                     help="c2: 64^3 Kolmogorov (default); c3: 128^3 ABC; c4: 256^3 perturbed Kolmogorov")
     ap.add_argument("--extras", type=int, default=1,
                     help="also time the FP64 iteration and the solves (rank 0)")
+    ap.add_argument("--gram-mode", default="auto", choices=["auto", "df", "tensor"],
+                    help="FP32 mode's symmetric POD Grams: auto, double-float, or tensor cores (pr_opts.gram_mode)")
     ap.add_argument("--large", type=int, default=1,
                     help="with --config c2 and extras: also time one iteration of the 128^3 workload")
     ap.add_argument("--solve", type=int, default=1, help="also time full solves to 1e-6")

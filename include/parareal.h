@@ -121,10 +121,8 @@ typedef struct pr_opts {
                                iterates are bit-identical for a fixed group_ctas.
                                pr_rewind can only undo iteration 1; pr_get_snapshots and
                                pr_get_basis(level 2) reach the last wave's subintervals only. */
-    int no_tensor_gram;     /* FP32 mode: 0 (default) computes the symmetric POD Grams of at
-                               most 64 columns (level 1, Cholesky QR) on the tensor cores
-                               with error-free BF16 digits (FP64-accurate, see pr_op_gram);
-                               1 keeps them in double-float arithmetic on the FP32 pipe.   */
+    int gram_mode;          /* enum pr_gram_mode: which kernel forms the FP32 mode's symmetric
+                               POD Grams (level 1, Cholesky QR); default PR_GRAM_AUTO        */
 } pr_opts;
 
 /* Fine integrator.  PR_FINE_IMPLICIT_EULER: the paper's, eq. (semi-dis-eq), BiCGStab per
@@ -143,6 +141,14 @@ enum pr_fine { PR_FINE_IMPLICIT_EULER = 0, PR_FINE_RK4 = 1 };
  * G(x) = P G_c(R x), restriction by injection, trilinear prolongation; iteration 0 keeps
  * the Case-I window [0, T0] and then U^0_{n+1} = G(U^0_n). */
 enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1, PR_METHOD_PARAREAL_II = 2 };
+
+/* Symmetric Gram kernels of the FP32 mode.  PR_GRAM_DF: double-float arithmetic on the
+ * FP32 pipe (up to 54 columns; FP64 beyond).  PR_GRAM_TENSOR: the tensor cores, with the
+ * values cut into error-free BF16 digits (FP64-accurate, see pr_op_gram; up to 64 columns,
+ * double-float beyond).  PR_GRAM_AUTO: the tensor cores for 55..64 columns, where the
+ * double-float kernel does not reach, double-float otherwise.  The FP64 mode always forms
+ * its Grams in FP64. */
+enum pr_gram_mode { PR_GRAM_AUTO = 0, PR_GRAM_DF = 1, PR_GRAM_TENSOR = 2 };
 
 /* Per-solve report (pr_solve).  Times are seconds measured with CUDA events. */
 typedef struct pr_report {

@@ -23,6 +23,7 @@ PR_FLOW_ABC, PR_FLOW_KOLMOGOROV, PR_FLOW_CONST = 0, 1, 2
 PR_FLOW_PAPER_KOLMOGOROV, PR_FLOW_PAPER_ABC = 3, 4
 PR_FP64, PR_FP32 = 0, 1
 PR_METHOD_ADAPTIVE, PR_METHOD_PARAREAL_I, PR_METHOD_PARAREAL_II = 0, 1, 2
+PR_GRAM_AUTO, PR_GRAM_DF, PR_GRAM_TENSOR = 0, 1, 2
 PR_FINE_IMPLICIT_EULER, PR_FINE_RK4 = 0, 1
 
 
@@ -42,7 +43,7 @@ class pr_opts(C.Structure):
                 ("rank_tau", C.c_double), ("precision", C.c_int), ("lin_tol", C.c_double),
                 ("lin_maxit", C.c_int), ("aug_tol", C.c_double), ("group_ctas", C.c_int),
                 ("ctas_per_sm", C.c_int), ("spin_limit", C.c_longlong), ("method", C.c_int),
-                ("fine", C.c_int), ("wave", C.c_int), ("no_tensor_gram", C.c_int)]
+                ("fine", C.c_int), ("wave", C.c_int), ("gram_mode", C.c_int)]
 
 
 class pr_report(C.Structure):

@@ -395,12 +395,16 @@ pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const i
 // (c->colsA, c->KA).  Result: dest + b*dest_bstride (columns of Ng), dims m_dest[b].
 // ortho_blocks: the snapshot columns are blocks of orthonormal bases (c->colblk says
 // which); the FP32 mode then takes their diagonal Gram blocks as the identity.
-// Symmetric Grams of the FP32 mode with at most 64 FP64 columns run on the tensor cores
-// (error-free BF16 digit products, FP64-accurate; gram_tc.cu) unless the options ask for
-// the double-float kernel; every other Gram runs in double-float or FP64.
+// Symmetric Grams of the FP32 mode: on the tensor cores (error-free BF16 digit products,
+// FP64-accurate; gram_tc.cu) for 55..64 columns, which the double-float kernel does not
+// take (gram_mode PR_GRAM_AUTO), for every width up to 64 (PR_GRAM_TENSOR), or never
+// (PR_GRAM_DF); every other Gram runs in double-float or FP64.
 cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32) {
-    if (c->fp32 && !c->o.no_tensor_gram && !in_f32 && ga.sym && ga.colblk == nullptr &&
-        ga.maxKA <= gram_tc_max_cols() && ga.B <= (c->wave > 0 ? c->wave : c->N) + 1)
+    const int mode = c->o.gram_mode;
+    const bool fits = c->fp32 && !in_f32 && ga.sym && ga.colblk == nullptr && ga.maxKA <= gram_tc_max_cols() &&
+                      ga.B <= (c->wave > 0 ? c->wave : c->N) + 1;
+    const bool wide = ga.maxKA > 54;   // beyond the double-float kernel's 384 output tiles
+    if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && wide)))
         return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st);
     return launch_gram(ga, in_f32, in_f32, c->st);
 }
@@ -874,7 +878,7 @@ void pr_opts_init(pr_opts* o) {
     o->method = PR_METHOD_ADAPTIVE;
     o->fine = PR_FINE_IMPLICIT_EULER;
     o->wave = 0;
-    o->no_tensor_gram = 0;
+    o->gram_mode = PR_GRAM_AUTO;
 }
 
 const char* pr_status_string(pr_status s) {
@@ -919,6 +923,7 @@ pr_status pr_create(const pr_grid* grid, const pr_flow* flow, double eps, double
     if (o.spin_limit < 0) o.spin_limit = 1LL << 22;
     if (o.aug_tol <= 0) o.aug_tol = 1e-12;
     if (o.wave < 0) return PR_ERR_INVALID_ARG;
+    if (o.gram_mode < PR_GRAM_AUTO || o.gram_mode > PR_GRAM_TENSOR) return PR_ERR_INVALID_ARG;
     if (o.wave > 0 && o.method != PR_METHOD_ADAPTIVE) return PR_ERR_UNSUPPORTED;   // waves stream Algorithm 2
     pr_ctx* c = new pr_ctx();
     c->n = grid->n;

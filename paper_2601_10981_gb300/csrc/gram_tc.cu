@@ -44,7 +44,7 @@ namespace pr {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;   // 8 warps: two cover each tensor-memory lane quarter
 constexpr int TC_N = 64;             // columns handled (K <= 64)
 constexpr int TC_PTS = 64;           // points per shared-memory stage
 constexpr int TC_SLICES = 8;         // digits per value
@@ -58,7 +58,7 @@ constexpr int TC_TMEM_COLS = TC_TILES * TC_N;   // 512: all of an SM's tensor me
 constexpr int TC_LBO = 128;
 constexpr int TC_SBO = 1024;
 constexpr int TC_STAGE_BYTES = TC_SLICES * 8 * TC_SBO;   // 64 KiB
-static_assert(TC_STAGE_BYTES >= TC_N * TC_N * (int)sizeof(double), "the stage buffer holds the half sums");
+static_assert(2 * TC_STAGE_BYTES >= TC_N * TC_N * (int)sizeof(double), "the stage buffers hold the half sums");
 constexpr long long TC_SPIN_LIMIT = 1LL << 24;   // polls of an mbarrier (~1 s with the sleeps)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -135,20 +135,30 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
 }
 
 // Balanced base-128 digits of y (|y| < 2^54): y = sum_{s=1..8} d_s 128^(8-s),
-// d_s in [-64, 63]; d[s-1] = d_s.  (The seven lower steps leave |y| < 2^54 / 128^7 + 1/2
-// < 33, so the top digit takes what is left without a carry.)
+// d_s in [-64, 63]; d[s-1] = d_s.  The low 28 bits give the four lower digits (and a
+// carry of 0 or 1), the high part the four upper ones, all in 32-bit integers.  (The
+// seven lower steps leave |y| < 2^54 / 128^7 + 1/2 < 33, so the top digit takes what is
+// left without a carry.)
 __device__ __forceinline__ void digits8(long long y, int (&d)[TC_SLICES]) {
+    int v = (int)(y & 0xFFFFFFFll);
+    int hi = (int)(y >> 28);
 #pragma unroll
-    for (int s = TC_SLICES - 1; s >= 0; --s) {
-        const int lo = (((int)(y & 127)) + 64) & 127;
-        d[s] = lo - 64;
-        y = (y - d[s]) >> 7;
+    for (int s = TC_SLICES - 1; s >= TC_SLICES / 2; --s) {
+        d[s] = ((v + 64) & 127) - 64;
+        v = (v - d[s]) >> 7;
+    }
+    hi += v;
+#pragma unroll
+    for (int s = TC_SLICES / 2 - 1; s >= 0; --s) {
+        d[s] = ((hi + 64) & 127) - 64;
+        hi = (hi - d[s]) >> 7;
     }
 }
 
+// two small integers (|a|, |b| <= 64, exact in BF16) as a packed BF16 pair, a in the low half
 __device__ __forceinline__ unsigned pack_bf16x2(int a, int b) {
-    const __nv_bfloat16 x = __float2bfloat16_rn((float)a), y = __float2bfloat16_rn((float)b);
-    return (unsigned)__bfloat16_as_ushort(x) | ((unsigned)__bfloat16_as_ushort(y) << 16);
+    const __nv_bfloat162 p = __floats2bfloat162_rn((float)a, (float)b);
+    return *reinterpret_cast<const unsigned*>(&p);
 }
 
 }  // namespace
@@ -189,18 +199,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
                                                                 const unsigned long long* colmax, int ld,
                                                                 int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ __align__(8) unsigned long long s_mbar[2];
     __shared__ unsigned s_tmem;
     __shared__ int s_e[TC_N];
     __shared__ int s_last;
-    unsigned char* stage = smem_raw;   // TC_STAGE_BYTES, 1024-aligned
+    unsigned char* stages = smem_raw;   // two stages of TC_STAGE_BYTES, 1024-aligned
     double* sacc = reinterpret_cast<double*>(smem_raw);   // reused for the bottom-half sums
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const unsigned mbar = smem_u32(&s_mbar);
-    const unsigned stage_s = smem_u32(stage);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned mbar0 = smem_u32(&s_mbar[0]);
+    const unsigned stage_s = smem_u32(stages);
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -213,14 +224,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
-    unsigned parity = 0;
+    unsigned parity[2] = {0u, 0u};
+    bool pending[2] = {false, false};   // a commit on this stage buffer not yet waited for
     bool failed = false;
-    // this thread's accumulator row: lane r of every tile; top half (r < 64) holds the
-    // products with s + t = c, the bottom half those with s + t = c + 1
-    const int row = tid;
+    // wait for the MMAs that read stage buffer q (all threads; one vote decides)
+    auto wait_buf = [&](int q) -> bool {
+        if (!pending[q]) return true;
+        const bool ok = mbar_wait(mbar0 + 8u * q, parity[q]);
+        parity[q] ^= 1u;
+        pending[q] = false;
+        return __syncthreads_or(ok ? 0 : 1) == 0;
+    };
+    // drain rows: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane = accumulator
+    // row r) and the 32 columns 32 (w / 4) .. + 31; rows r < 64 hold the products with
+    // s + t = c (top), rows r >= 64 those with s + t = c + 1 (bottom)
+    const int row = 32 * (warp & 3) + lane;
+    const int cbase = 32 * (warp >> 2);
     const bool top = row < 64;
     const int irow = top ? row : row - 64;
-    double acc[TC_N];
+    // tiles c0 = 0..3 and 4..7 fold into exact 46-bit integers H, Lo (weights 2^(7(3-c0)),
+    // 2^(7(7-c0))), worth H 2^(-7(5+d)) + Lo 2^(-7(9+d)) with d = 0 (top) or 1 (bottom)
+    const double wH = ldexp(1.0, -7 * (5 + (top ? 0 : 1)));
+    const double wL = ldexp(1.0, -7 * (9 + (top ? 0 : 1)));
+    double acc[32];
+    int prevK = TC_N;   // rows [K, prevK) of the stage buffers may hold another item's digits
 
     const int units = a.B * chunks;
     for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
@@ -233,26 +260,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
             // 2^(e - 2) > max |W[:, i]|:  e = unbiased exponent of the maximum + 3
             s_e[tid] = m ? (int)((m >> 52) & 0x7FF) - 1023 + 3 : 0;
         }
+        if (K < prevK) {   // zero the digit rows of columns K .. prevK - 1 in both buffers
+            const int nrow = prevK - K;
+            for (int e = tid; e < 2 * TC_SLICES * nrow * 8; e += TC_THREADS) {
+                const int bufq = e / (TC_SLICES * nrow * 8);
+                const int r = e - bufq * TC_SLICES * nrow * 8;
+                const int sl = r / (nrow * 8), rest = r - sl * nrow * 8;
+                const int col = K + rest / 8, kg = rest & 7;
+                *reinterpret_cast<uint4*>(stages + bufq * TC_STAGE_BYTES +
+                                          ((sl * 8 + (col >> 3)) * 8 + kg) * 128 + (col & 7) * 16) =
+                    make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        prevK = K;
 #pragma unroll
-        for (int j = 0; j < TC_N; ++j) acc[j] = 0.0;
+        for (int j = 0; j < 32; ++j) acc[j] = 0.0;
         __syncthreads();
-        int nst = 0;   // stages since the last drain
-        for (long long p0 = p_lo; p0 < p_hi; p0 += TC_PTS) {
-            // ---- digits of 64 points x 64 columns into the stage (4 items a thread:
-            //      one column and 8 consecutive points each)
+        int nst = 0, si = 0;   // stages since the last drain; stage counter of the unit
+        for (long long p0 = p_lo; p0 < p_hi; p0 += TC_PTS, ++si) {
+            const int q = si & 1;
+            unsigned char* stage = stages + q * TC_STAGE_BYTES;
+            if (!wait_buf(q)) {   // the MMAs that read this buffer two stages ago
+                failed = true;
+                break;
+            }
+            // ---- digits of 64 points x K columns (one column and 8 consecutive points an item)
 #pragma unroll 1
-            for (int it = tid; it < TC_N * 8; it += TC_THREADS) {
+            for (int it = tid; it < K * 8; it += TC_THREADS) {
                 const int col = it >> 3, kg = it & 7;
-                unsigned w[TC_SLICES][4];   // slice s: the 8 points' digits as BF16 pairs
-                const long long pb = p0 + kg * 8;
-                const bool live = col < K;
-                const double* c = live ? reinterpret_cast<const double*>(cols[col]) : nullptr;
+                const double* c = reinterpret_cast<const double*>(cols[col]);
                 const int e = s_e[col];
+                const long long pb = p0 + kg * 8;
+                unsigned w[TC_SLICES][4];
 #pragma unroll
                 for (int k = 0; k < 8; k += 2) {
                     int d0[TC_SLICES], d1[TC_SLICES];
-                    const double x0 = (live && pb + k < p_hi) ? c[pb + k] : 0.0;
-                    const double x1 = (live && pb + k + 1 < p_hi) ? c[pb + k + 1] : 0.0;
+                    const double x0 = (pb + k < p_hi) ? c[pb + k] : 0.0;
+                    const double x1 = (pb + k + 1 < p_hi) ? c[pb + k + 1] : 0.0;
                     digits8(fixed56(x0, e), d0);
                     digits8(fixed56(x1, e), d1);
 #pragma unroll
@@ -266,47 +310,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
-            // ---- 4 K-steps of 16 points x 20 (s, t) pairs
+            // ---- 4 K-steps of 16 points x 20 (s, t) pairs, committed to this buffer's mbarrier
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned sb = stage_s + q * TC_STAGE_BYTES;
 #pragma unroll 1
                 for (int k = 0; k < TC_PTS / 16; ++k) {
                     bool fresh[TC_TILES];
 #pragma unroll
-                    for (int c = 0; c < TC_TILES; ++c) fresh[c] = (nst == 0 && k == 0);
+                    for (int cc = 0; cc < TC_TILES; ++cc) fresh[cc] = (nst == 0 && k == 0);
 #pragma unroll 1
                     for (int sa = 0; sa < TC_SLICES; sa += 2) {   // A: slices sa, sa + 1 (0-based)
-                        for (int t = 0; sa + t < TC_TILES; ++t) {  // B: slice t; tile c = sa + t
-                            const int c = sa + t;
-                            const uint64_t ad = umma_desc(stage_s + (sa * 8) * TC_SBO + (2 * k) * TC_LBO);
-                            const uint64_t bdsc = umma_desc(stage_s + (t * 8) * TC_SBO + (2 * k) * TC_LBO);
-                            mma_bf16(tmem + (unsigned)(c * TC_N), ad, bdsc, fresh[c] ? 0u : 1u);
-                            fresh[c] = false;
+                        for (int t = 0; sa + t < TC_TILES; ++t) {  // B: slice t; tile c0 = sa + t
+                            const int c0 = sa + t;
+                            const uint64_t ad = umma_desc(sb + (sa * 8) * TC_SBO + (2 * k) * TC_LBO);
+                            const uint64_t bdsc = umma_desc(sb + (t * 8) * TC_SBO + (2 * k) * TC_LBO);
+                            mma_bf16(tmem + (unsigned)(c0 * TC_N), ad, bdsc, fresh[c0] ? 0u : 1u);
+                            fresh[c0] = false;
                         }
                     }
                 }
-                mma_commit(mbar);
+                mma_commit(mbar0 + 8u * q);
             }
-            // every thread waits; one vote decides, so no thread leaves the loop alone
-            failed = __syncthreads_or(mbar_wait(mbar, parity) ? 0 : 1) != 0;
-            if (failed) break;
-            parity ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            pending[q] = true;
             ++nst;
             if (nst == TC_STAGES_PER_DRAIN || p0 + TC_PTS >= p_hi) {
-                // ---- drain: this thread's lane of every tile, weights 2^(-7 q)
-                const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
-#pragma unroll 1
-                for (int c = 0; c < TC_TILES; ++c) {
-                    const int q = c + 2 + (top ? 0 : 1);
-                    const double wq = ldexp(1.0, -7 * q);
+                // ---- drain: every MMA so far has completed once both buffers are waited for
+                if (!wait_buf(q) || !wait_buf(q ^ 1)) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned lane_base = tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)cbase;
 #pragma unroll
-                    for (int j0 = 0; j0 < TC_N; j0 += 16) {
+                for (int j0 = 0; j0 < 32; j0 += 16) {
+                    long long H[16], Lo[16];
+#pragma unroll
+                    for (int e2 = 0; e2 < 16; ++e2) H[e2] = Lo[e2] = 0ll;
+#pragma unroll
+                    for (int c0 = 0; c0 < TC_TILES; ++c0) {
                         float v[16];
-                        tmem_ld16(lane_base + (unsigned)(c * TC_N + j0), v);
+                        tmem_ld16(lane_base + (unsigned)(c0 * TC_N + j0), v);
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) acc[j0 + e] = fma((double)v[e], wq, acc[j0 + e]);
+                        for (int e2 = 0; e2 < 16; ++e2) {
+                            const long long x = (long long)__float2int_rn(v[e2]);   // an exact integer
+                            if (c0 < 4) H[e2] += x << (7 * (3 - c0));
+                            else Lo[e2] += x << (7 * (7 - c0));
+                        }
                     }
+#pragma unroll
+                    for (int e2 = 0; e2 < 16; ++e2)
+                        acc[j0 + e2] = fma((double)H[e2], wH, fma((double)Lo[e2], wL, acc[j0 + e2]));
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncthreads();
@@ -315,10 +369,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
         }
         if (failed) break;
         // ---- the unit's partial Gram: top + bottom halves, scaled by 2^(e_i + e_j)
-        __syncthreads();   // the stage buffer is free (every MMA of the unit completed)
+        __syncthreads();   // every MMA of the unit completed (drained): the buffers are free
         if (!top) {
 #pragma unroll
-            for (int j = 0; j < TC_N; ++j) sacc[irow * TC_N + j] = acc[j];
+            for (int j = 0; j < 32; ++j) sacc[irow * TC_N + cbase + j] = acc[j];
         }
         __syncthreads();
         const size_t outsz = (size_t)a.maxKA * a.maxKB;
@@ -326,9 +380,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
         if (top && irow < K) {
             const int ei = s_e[irow];
 #pragma unroll
-            for (int j = 0; j < TC_N; ++j)
-                if (j >= irow && j < K)
-                    mypart[(size_t)irow * a.maxKB + j] = ldexp(acc[j] + sacc[irow * TC_N + j], ei + s_e[j]);
+            for (int j = 0; j < 32; ++j) {
+                const int jj = cbase + j;
+                if (jj >= irow && jj < K)
+                    mypart[(size_t)irow * a.maxKB + jj] = ldexp(acc[j] + sacc[irow * TC_N + jj], ei + s_e[jj]);
+            }
         }
         // the last unit of item b sums the chunk partials in chunk order
         __threadfence();
@@ -345,10 +401,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
             for (int o = tid; o < K * K; o += TC_THREADS) {
                 const int i = o / K, j = o - i * K;
                 if (j < i) continue;
-                double s = 0.0;
-                for (int cc = 0; cc < chunks; ++cc) s += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
-                Gb[(size_t)i * a.ldG + j] = s;
-                Gb[(size_t)j * a.ldG + i] = s;
+                double sum = 0.0;
+                for (int cc = 0; cc < chunks; ++cc) sum += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
+                Gb[(size_t)i * a.ldG + j] = sum;
+                Gb[(size_t)j * a.ldG + i] = sum;
             }
             if (tid == 0) st_relaxed_u32(a.counter + b, 0u);
         }
@@ -356,9 +412,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
     }
     if (failed) {
         if (tid == 0) record_error(err, DERR_TIMEOUT);
-        // the MMAs of the stage may still be running: wait once more (bounded) before the
+        // MMAs may still be running: wait once more (bounded) on both buffers before the
         // tensor memory is released
-        mbar_wait(mbar, parity);
+        for (int q = 0; q < 2; ++q)
+            if (pending[q]) mbar_wait(mbar0 + 8u * q, parity[q]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -377,7 +434,7 @@ cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld
     // the chunks of the other Gram kernels, so that the partial buffer (gram_part_doubles)
     // fits; any chunk length works for this kernel
     const int chunks = gram_chunks(a.Ng);
-    const long long CH = (a.Ng + chunks - 1) / chunks;
+    const long long CH = ((a.Ng + chunks - 1) / chunks + TC_PTS - 1) / TC_PTS * TC_PTS;
     cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)a.B * ld, st);
     if (e != cudaSuccess) return e;
     colmax_kernel<<<dim3(chunks, a.B), 256, 0, st>>>(a, CH, colmax, ld);
@@ -387,9 +444,9 @@ cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // one CTA an SM: the tiles take all 512 tensor-memory columns; the shared-memory request
-    // (stage buffer plus slack, above half an SM) keeps a second CTA off the SM
-    const size_t smem = 120 * 1024;
+    // one CTA an SM: the tiles take all 512 tensor-memory columns, and the two stage
+    // buffers (128 KiB of shared memory) keep a second CTA off the SM
+    const size_t smem = 2 * TC_STAGE_BYTES;
     e = cudaFuncSetAttribute((const void*)gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(sms, a.B * chunks));

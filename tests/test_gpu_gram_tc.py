@@ -75,3 +75,34 @@ def test_tensor_gram_matches_exact_sums(gpu, n, K, B):
     assert worst_tc < 1.0, worst_tc
     rel = np.abs(Gt - G64).max() / np.abs(G64).max()
     assert rel < 1e-14, rel
+
+
+@pytest.mark.parametrize("wl", ["tiny_forced", "abc16"])
+def test_fp32_mode_with_tensor_grams_against_oracle(gpu, wl):
+    """The FP32 mode with every symmetric POD Gram on the tensor cores (level 1 and the
+    Cholesky-QR Grams, PR_GRAM_TENSOR) against the FP64 oracle, within the FP32-mode bar
+    max(1e-5, 10 x the oracle's change under 1e-8 fine perturbations) at every (k, n)."""
+    import oracle as O
+    from test_gpu_parity import TOL32, oracle_envelope, rel
+    bd, torch = gpu
+    w = {"tiny_forced": pi.tiny(n=10, n_sub=5, T=0.1, dt=2e-3, f_seed=2, flow=pi.Flow("kolmogorov", k=2)),
+         "abc16": pi.ABC_16}[wl]
+    prm = O.derive_params(w)
+    K = min(w.n_sub, 3)
+    hist, env = oracle_envelope(w, prm, K, 1e-8, where="fine")
+    s = bd.Parareal.from_workload(w, precision=bd.PR_FP32, gram_mode=bd.PR_GRAM_TENSOR)
+    s.set_initial(w.u0(), w.f())
+    s.iteration0()
+    Us = [s.interfaces()]
+    for k in range(1, K + 1):
+        s.iterate(k)
+        Us.append(s.interfaces())
+    s.close()
+    worst = 0.0
+    for k in range(K + 1):
+        for n in range(w.n_sub + 1):
+            e = rel(Us[k][n], hist["U"][k][n])
+            tol = max(TOL32, 10 * env[k][n])
+            worst = max(worst, e / tol)
+            assert e < tol, (k, n, e, env[k][n])
+    print(f"{wl} FP32 mode, tensor-core Grams: worst error / tolerance {worst:.3f}")
