@@ -135,25 +135,10 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
 }
 
 // Balanced base-128 digits of y (|y| < 2^54): y = sum_{s=1..8} d_s 128^(8-s),
-// d_s in [-64, 63]; d[s-1] = d_s.  The low 28 bits give the four lower digits (and a
-// carry of 0 or 1), the high part the four upper ones, all in 32-bit integers.  (The
+// d_s in [-64, 63].  The low 28 bits of y give the four lower digits (and a carry of 0 or
+// 1 into the high part), the high part the four upper ones, all in 32-bit integers.  (The
 // seven lower steps leave |y| < 2^54 / 128^7 + 1/2 < 33, so the top digit takes what is
-// left without a carry.)
-__device__ __forceinline__ void digits8(long long y, int (&d)[TC_SLICES]) {
-    int v = (int)(y & 0xFFFFFFFll);
-    int hi = (int)(y >> 28);
-#pragma unroll
-    for (int s = TC_SLICES - 1; s >= TC_SLICES / 2; --s) {
-        d[s] = ((v + 64) & 127) - 64;
-        v = (v - d[s]) >> 7;
-    }
-    hi += v;
-#pragma unroll
-    for (int s = TC_SLICES / 2 - 1; s >= 0; --s) {
-        d[s] = ((hi + 64) & 127) - 64;
-        hi = (hi - d[s]) >> 7;
-    }
-}
+// left without a carry.)  The kernel runs these steps for 8 values in lockstep.
 
 // two small integers (|a|, |b| <= 64, exact in BF16) as a packed BF16 pair, a in the low half
 __device__ __forceinline__ unsigned pack_bf16x2(int a, int b) {
@@ -280,33 +265,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
         for (long long p0 = p_lo; p0 < p_hi; p0 += TC_PTS, ++si) {
             const int q = si & 1;
             unsigned char* stage = stages + q * TC_STAGE_BYTES;
+            // ---- this thread's items of the stage (one column and 8 consecutive points
+            //      each; item it -> row rho = it & 7 of row group it >> 6, K group
+            //      (it >> 3) & 7, so that 8 consecutive threads fill one 128-byte core-
+            //      matrix row): all their loads are issued before anything waits
+            double xr[2][8];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int it = tid + r * TC_THREADS;
+                const int col = ((it >> 6) << 3) | (it & 7), kg = (it >> 3) & 7;
+                const long long pb = p0 + kg * 8;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) xr[r][k] = 0.0;
+                if (col < K) {
+                    const double* c = reinterpret_cast<const double*>(cols[col]);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (pb + k < p_hi) xr[r][k] = c[pb + k];
+                }
+            }
             if (!wait_buf(q)) {   // the MMAs that read this buffer two stages ago
                 failed = true;
                 break;
             }
-            // ---- digits of 64 points x K columns (one column and 8 consecutive points an item)
-#pragma unroll 1
-            for (int it = tid; it < K * 8; it += TC_THREADS) {
-                const int col = it >> 3, kg = it & 7;
-                const double* c = reinterpret_cast<const double*>(cols[col]);
+            // ---- digits into the stage buffer (columns >= K stay zero): the 8 points of an
+            //      item are cut in lockstep, digit by digit (8 independent chains), and each
+            //      slice's 16-byte core-matrix row is stored as soon as it is complete
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int it = tid + r * TC_THREADS;
+                const int col = ((it >> 6) << 3) | (it & 7), kg = (it >> 3) & 7;
+                if (col >= K) continue;
                 const int e = s_e[col];
-                const long long pb = p0 + kg * 8;
-                unsigned w[TC_SLICES][4];
+                int lo[8], hi[8];
 #pragma unroll
-                for (int k = 0; k < 8; k += 2) {
-                    int d0[TC_SLICES], d1[TC_SLICES];
-                    const double x0 = (pb + k < p_hi) ? c[pb + k] : 0.0;
-                    const double x1 = (pb + k + 1 < p_hi) ? c[pb + k + 1] : 0.0;
-                    digits8(fixed56(x0, e), d0);
-                    digits8(fixed56(x1, e), d1);
-#pragma unroll
-                    for (int sl = 0; sl < TC_SLICES; ++sl) w[sl][k >> 1] = pack_bf16x2(d0[sl], d1[sl]);
+                for (int k = 0; k < 8; ++k) {
+                    const long long y = fixed56(xr[r][k], e);
+                    lo[k] = (int)(y & 0xFFFFFFFll);
+                    hi[k] = (int)(y >> 28);
                 }
-                const int g = col >> 3, rho = col & 7;
+                unsigned char* rowp = stage + ((col >> 3) * 8 + kg) * 128 + (col & 7) * 16;
 #pragma unroll
-                for (int sl = 0; sl < TC_SLICES; ++sl)
-                    *reinterpret_cast<uint4*>(stage + ((sl * 8 + g) * 8 + kg) * 128 + rho * 16) =
-                        make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+                for (int sl = TC_SLICES - 1; sl >= 0; --sl) {
+                    int d[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        int& v = (sl >= TC_SLICES / 2) ? lo[k] : hi[k];
+                        d[k] = ((v + 64) & 127) - 64;
+                        v = (v - d[k]) >> 7;
+                        if (sl == TC_SLICES / 2) hi[k] += lo[k];   // the carry out of the low half
+                    }
+                    *reinterpret_cast<uint4*>(rowp + sl * 8 * TC_SBO) =
+                        make_uint4(pack_bf16x2(d[0], d[1]), pack_bf16x2(d[2], d[3]), pack_bf16x2(d[4], d[5]),
+                                   pack_bf16x2(d[6], d[7]));
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
@@ -314,19 +326,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const unsigned sb = stage_s + q * TC_STAGE_BYTES;
-#pragma unroll 1
-                for (int k = 0; k < TC_PTS / 16; ++k) {
-                    bool fresh[TC_TILES];
+                const unsigned first = (nst == 0) ? 0u : 1u;   // 0: the window's first write of a tile
 #pragma unroll
-                    for (int cc = 0; cc < TC_TILES; ++cc) fresh[cc] = (nst == 0 && k == 0);
-#pragma unroll 1
+                for (int k = 0; k < TC_PTS / 16; ++k) {
+#pragma unroll
                     for (int sa = 0; sa < TC_SLICES; sa += 2) {   // A: slices sa, sa + 1 (0-based)
-                        for (int t = 0; sa + t < TC_TILES; ++t) {  // B: slice t; tile c0 = sa + t
+#pragma unroll
+                        for (int t = 0; t < TC_TILES; ++t) {      // B: slice t; tile c0 = sa + t
+                            if (sa + t >= TC_TILES) continue;
                             const int c0 = sa + t;
-                            const uint64_t ad = umma_desc(sb + (sa * 8) * TC_SBO + (2 * k) * TC_LBO);
-                            const uint64_t bdsc = umma_desc(sb + (t * 8) * TC_SBO + (2 * k) * TC_LBO);
-                            mma_bf16(tmem + (unsigned)(c0 * TC_N), ad, bdsc, fresh[c0] ? 0u : 1u);
-                            fresh[c0] = false;
+                            // the first pair into tile c0 in issue order is (sa = 0, t = c0) for
+                            // c0 < 8; it overwrites the tile at the window's first K-step
+                            const unsigned acc = (k == 0 && sa == 0) ? first : 1u;
+                            mma_bf16(tmem + (unsigned)(c0 * TC_N),
+                                     umma_desc(sb + (sa * 8) * TC_SBO + (2 * k) * TC_LBO),
+                                     umma_desc(sb + (t * 8) * TC_SBO + (2 * k) * TC_LBO), acc);
                         }
                     }
                 }
