@@ -593,7 +593,9 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
         o.zm = vload<T, W>(rowzm + x0);
         return o;
     };
-    // The stored perturbation at the W points from index i (FINE_MODE_IMPLICIT_PERT).
+    // The stored perturbation at the W points from index i (FINE_MODE_IMPLICIT_PERT).  It is
+    // loaded where the stencil uses it, not one plane ahead with the other owned-point
+    // inputs: its 3 W registers held across the march made the instantiation spill.
     auto load_pert = [&](int i) -> PertV<KT, W, PT> {
         PertV<KT, W, PT> o;
         if constexpr (PT) {
@@ -941,7 +943,6 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                       },
                       [&](int i) -> OwnFD<KT, W, PT> {
                           OwnFD<KT, W, PT> o;
-                          o.b = load_pert(i);
                           if (ff) o.f = vload<KT, W>(ff + i);
                           else {
 #pragma unroll
@@ -959,6 +960,8 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                           const auto q = nb7(rowc, rowzp, rowzm);
                           const VK chi = vload<float, W>(rowc + ring_lo + x0);
                           const VK clo = vload<float, W>(rowc + 2 * ring_lo + x0);
+                          const PertV<KT, W, PT> pbv = load_pert(i);
+                          (void)pbv;
                           VK fv = ow.f;
                           if (tdep) {
                               const KT fyz = ftk[n + yy] + ftk[2 * n + i / n2];
@@ -973,9 +976,9 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               KT ay = ky_x[e] + ky_z;
                               KT az = kz_x[e] + kz_y[k];
                               if constexpr (PT) {
-                                  ax += kp * ow.b.x.v[e];
-                                  ay += kp * ow.b.y.v[e];
-                                  az += kp * ow.b.z.v[e];
+                                  ax += kp * pbv.x.v[e];
+                                  ay += kp * pbv.y.v[e];
+                                  az += kp * pbv.z.v[e];
                               }
                               const KT dx = __fsub_rn(q.xp.v[e], q.xm.v[e]);
                               const KT dy = __fsub_rn(q.yp.v[e], q.ym.v[e]);
@@ -1063,12 +1066,12 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               for (int e = 0; e < W; ++e) o.v[e] = v.r.v[e] + bk * (v.p.v[e] - ok * v.v.v[e]);
                               return o;
                           },
-                          [&](int i) -> OwnH<KT, W, PT> { return {vload<KT, W>(rh + i), load_pert(i)}; },
+                          [&](int i) -> OwnH<KT, W, PT> { return {vload<KT, W>(rh + i), {}}; },
                           [&](int i, int k, int, const OwnH<KT, W, PT>& ow, const KT* rowc, const KT* rowzp,
                               const KT* rowzm) {
                               const VK& rhv = ow.h;
                               const auto q7 = nb7(rowc, rowzp, rowzm);
-                              const VK av = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm, ow.b);
+                              const VK av = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm, load_pert(i));
                               vstore(pn + i, q7.c);
                               vstore(vn + i, av);
 #pragma unroll
@@ -1108,11 +1111,11 @@ __global__ void __launch_bounds__(256, 2) fine_kernel(FineArgs a) {
                               for (int e = 0; e < W; ++e) o.v[e] = v.r.v[e] - al * v.v.v[e];
                               return o;
                           },
-                          [&](int i) -> PertV<KT, W, PT> { return load_pert(i); },
-                          [&](int i, int k, int, const PertV<KT, W, PT>& pb, const KT* rowc, const KT* rowzp,
+                          [&](int) -> NoOwn { return NoOwn{}; },
+                          [&](int i, int k, int, const NoOwn&, const KT* rowc, const KT* rowzp,
                               const KT* rowzm) {
                               const auto q7 = nb7(rowc, rowzp, rowzm);
-                              const VK tv = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm, pb);
+                              const VK tv = applyA(k, q7.c, q7.xp, q7.xm, q7.yp, q7.ym, q7.zp, q7.zm, load_pert(i));
                               vstore(t + i, tv);
 #pragma unroll
                               for (int e = 0; e < W; ++e) {
