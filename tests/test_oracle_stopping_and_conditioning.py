@@ -126,16 +126,44 @@ def test_pod_truncation_is_ill_conditioned_on_abc16():
     assert lam[3] / lam[0] < 1e-7 and lam[0] / (lam[3] - lam[4]) > 1e7
 
 
+def _recording_pod_dims():
+    """Wrap the oracle's pod_mode so that the POD dimension of every call is recorded."""
+    pod_mod = sys.modules["oracle.pod"]
+    par_mod = sys.modules["oracle.parareal"]
+    dims = []
+    orig = pod_mod.pod_mode
+
+    def rec(*args, **kw):
+        out = orig(*args, **kw)
+        dims.append(out[1])
+        return out
+    return dims, orig, rec, (pod_mod, par_mod)
+
+
 def test_rounding_level_gram_noise_moves_abc16_iterates_beyond_1e_12():
     # 1e-15 relative noise in the Gram matrices (FP64 rounding of sums over 4096 points)
     # changes the oracle's own iterates by more than 1e-12 already at k = 0 and by orders
     # of magnitude more at k = 1, where the augmentation normalises residuals as small as
     # 5e-9 ||U||.  No pair of FP64 implementations that round differently can therefore
-    # meet 1e-12 at every (k, n) of this workload.
+    # meet 1e-12 at every (k, n) of this workload.  Every discrete decision is the same in
+    # both runs (each POD dimension, each augment / skip), so running the oracle with the
+    # other side's decisions forced on it would not close the gap either: the kept
+    # subspaces themselves move (Davis-Kahan, previous test).
     w = pi.ABC_16
     prm = O.derive_params(w)
-    h = O.parareal(w, prm, k_max=1)
-    hp = _perturbed_gram_run(w, prm, 1, 1e-15)
+    dims, orig, rec, mods = _recording_pod_dims()
+    for m_ in mods:
+        m_.pod_mode = rec
+    try:
+        h = O.parareal(w, prm, k_max=1)
+        dims_ref = list(dims)
+        dims.clear()
+        hp = _perturbed_gram_run(w, prm, 1, 1e-15)
+    finally:
+        for m_ in mods:
+            m_.pod_mode = orig
+    assert dims == dims_ref and len(dims) > prm.N, (dims, dims_ref)
+    assert hp["aug"] == h["aug"] and hp["m1"] == h["m1"] and hp["m2"] == h["m2"]
     d0 = max(_norm_rel(hp["U"][0][n], h["U"][0][n]) for n in range(prm.N + 1))
     d1 = max(_norm_rel(hp["U"][1][n], h["U"][1][n]) for n in range(prm.N + 1))
     assert d0 > 1e-12, d0
