@@ -145,9 +145,10 @@ enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1, PR_METHOD_PAR
 /* Symmetric Gram kernels of the FP32 mode.  PR_GRAM_DF: double-float arithmetic on the
  * FP32 pipe (up to 54 columns; FP64 beyond).  PR_GRAM_TENSOR: the tensor cores, with the
  * values cut into error-free BF16 digits (FP64-accurate, see pr_op_gram; up to 64 columns,
- * double-float beyond).  PR_GRAM_AUTO: the tensor cores for 55..64 columns, where the
- * double-float kernel does not reach, double-float otherwise.  The FP64 mode always forms
- * its Grams in FP64. */
+ * double-float beyond).  PR_GRAM_AUTO: the tensor cores for windows of 24..32 columns
+ * (where the narrow tensor-core form is faster) and 55..64 columns (where the double-float
+ * kernel does not reach), double-float otherwise.  The FP64 mode always forms its Grams
+ * in FP64. */
 enum pr_gram_mode { PR_GRAM_AUTO = 0, PR_GRAM_DF = 1, PR_GRAM_TENSOR = 2 };
 
 /* Per-solve report (pr_solve).  Times are seconds measured with CUDA events. */
@@ -326,13 +327,18 @@ pr_status pr_op_pod(pr_ctx* ctx, const void* d_W, int w_f32, int n_cols, int B, 
 
 /* Gram matrices G_b = W_b^T W_b of B snapshot matrices, step 1 of POD_Mode (Algorithm 1)
  * (M = I).  d_W: B x n_cols x n^3 device doubles (column-major blocks as for pr_op_pod);
- * d_G: B x n_cols x n_cols device doubles (row-major, symmetric).  tensor = 1: on the
- * tensor cores (tcgen05.mma with BF16 operands and FP32 accumulation): each column is
- * aligned to its largest magnitude and cut into eight balanced base-128 integer digits,
- * which BF16 holds exactly; digit products are summed exactly in FP32 over 1024 points
- * and then added in FP64 with their power-of-two weights, so the result is FP64-accurate
- * (n_cols <= 64).  tensor = 0: FP64 arithmetic.  B <= n_sub + 1, n_cols <= the context's
- * largest POD window.  Synchronises. */
+ * d_G: B x n_cols x n_cols device doubles (row-major, symmetric).  tensor selects the
+ * arithmetic:
+ *   1: the tensor cores (tcgen05.mma, BF16 operands, FP32 accumulation; n_cols <= 64).
+ *      Each column is aligned to its largest magnitude and each value truncated to 56
+ *      bits and cut into eight balanced base-128 integer digits, which BF16 holds
+ *      exactly; digit products are summed exactly in FP32 over windows of points.  Up to
+ *      32 columns the windows are folded into 128-bit integers, so the result is the
+ *      digit sum rounded once to FP64 (bit-reproducible); 33..64 columns fold them into
+ *      FP64 every 1024 points.  Either way FP64-accurate.
+ *   2: double-float arithmetic on the FP32 pipe (the FP32 mode's default kernel).
+ *   0: FP64 arithmetic.
+ * B <= n_sub + 1, n_cols <= the context's largest POD window.  Synchronises. */
 pr_status pr_op_gram(pr_ctx* ctx, const double* d_W, int n_cols, int B, double* d_G, int tensor);
 
 /* One coarse update of eq. (formula4) on subinterval [t, t+DeltaT] with the augmented

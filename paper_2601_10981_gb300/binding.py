@@ -411,13 +411,15 @@ class Parareal:
                                         m.ctypes.data_as(_I)))
         return R, m
 
-    def op_gram(self, W, tensor: bool = True):
-        """G_b = W_b^T W_b of a (B, n_cols, n^3) float64 CUDA tensor; returns (B, n_cols, n_cols)."""
+    def op_gram(self, W, tensor: bool = True, df: bool = False):
+        """G_b = W_b^T W_b of a (B, n_cols, n^3) float64 CUDA tensor; returns (B, n_cols, n_cols).
+        tensor: tensor cores; else df: double-float on the FP32 pipe; else FP64."""
         torch = self.torch
         B, K = W.shape[0], W.shape[1]
         G = torch.empty((B, K, K), dtype=torch.float64, device=W.device)
+        mode = 1 if tensor else (2 if df else 0)
         self._check(self._lib.pr_op_gram(self.ctx, C.c_void_p(W.data_ptr()), K, B, C.c_void_p(G.data_ptr()),
-                                         1 if tensor else 0))
+                                         mode))
         return G
 
     def op_coarse_update(self, R, m: int, U, Uprev, F):

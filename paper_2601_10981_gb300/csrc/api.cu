@@ -403,8 +403,12 @@ cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32) {
     const int mode = c->o.gram_mode;
     const bool fits = c->fp32 && !in_f32 && ga.sym && ga.colblk == nullptr && ga.maxKA <= gram_tc_max_cols() &&
                       ga.B <= (c->wave > 0 ? c->wave : c->N) + 1;
-    const bool wide = ga.maxKA > 54;   // beyond the double-float kernel's 384 output tiles
-    if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && wide)))
+    // measured crossovers against the double-float kernel (64 items x 262,144 points): the
+    // narrow tensor form (<= 32 columns) wins from 24 columns (32: 3.8 vs 6.7 ms), the wide
+    // one (33..64) beyond the double-float kernel's 384 output tiles (55 columns)
+    const bool narrow = ga.maxKA >= 24 && ga.maxKA <= 32;
+    const bool wide = ga.maxKA > 54;
+    if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && (narrow || wide))))
         return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st);
     return launch_gram(ga, in_f32, in_f32, c->st);
 }
@@ -1814,7 +1818,8 @@ pr_status pr_op_gram(pr_ctx* c, const double* d_W, int n_cols, int B, double* d_
     if (!c || !d_W || !d_G || B < 1 || n_cols < 1) return PR_ERR_INVALID_ARG;
     const int bmax = (c->wave > 0 ? c->wave : c->N) + 1;   // partial sums: gram_part_doubles(Ng, bmax, ...)
     if (B > bmax || n_cols > c->maxK) return fail(c, PR_ERR_INVALID_ARG, "pr_op_gram: B or n_cols above the context's sizes");
-    if (tensor && n_cols > gram_tc_max_cols())
+    if (tensor < 0 || tensor > 2) return fail(c, PR_ERR_INVALID_ARG, "pr_op_gram: tensor must be 0, 1 or 2");
+    if (tensor == 1 && n_cols > gram_tc_max_cols())
         return fail(c, PR_ERR_INVALID_ARG, "pr_op_gram: the tensor-core Gram takes at most 64 columns");
     pr_status s = ensure_ws(c);
     if (s != PR_OK) return s;
@@ -1839,7 +1844,8 @@ pr_status pr_op_gram(pr_ctx* c, const double* d_W, int n_cols, int B, double* d_
     ga.G = d_G;
     ga.ldG = n_cols;
     ga.ldG_b = (long long)n_cols * n_cols;
-    if (tensor) PR_CUDA(launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st));
+    ga.df = (tensor == 2);
+    if (tensor == 1) PR_CUDA(launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st));
     else PR_CUDA(launch_gram(ga, false, false, c->st));
     return pr_sync(c);
 }

@@ -268,7 +268,8 @@ int gram_chunks(long long Ng);
 size_t gram_part_doubles(long long Ng, int B, int maxKA, int maxKB);
 cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t st);
 // Symmetric Gram W^T W of up to 64 FP64 columns on the tensor cores (tcgen05, error-free
-// BF16 digits, FP64-accurate; gram_tc.cu).  colmax: device scratch of B x ld (ld >= maxKA)
+// BF16 digits, FP64-accurate; gram_tc.cu; up to 32 columns the narrow, exactly summed
+// form when the partial buffer holds two chunks of the other Gram kernels per unit).  colmax: device scratch of B x ld (ld >= maxKA)
 // 64-bit words; err: device error flag (PR_ERR_TIMEOUT if an MMA completion wait times out).
 cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld, int* err, cudaStream_t st);
 int gram_tc_max_cols();

@@ -106,3 +106,134 @@ def test_fp32_mode_with_tensor_grams_against_oracle(gpu, wl):
             worst = max(worst, e / tol)
             assert e < tol, (k, n, e, env[k][n])
     print(f"{wl} FP32 mode, tensor-core Grams: worst error / tolerance {worst:.3f}")
+
+
+# ---- the narrow form (K <= 32): bit-exact against a digit-level emulation ----------------
+#
+# For K <= 32 columns the kernel sums the digit products exactly (128-bit integers) and
+# rounds once, so its result is a function of the inputs alone: each value truncated
+# toward zero to y = trunc(x 2^(56 - e)) (e = exponent of the column's largest magnitude
+# + 3), y cut into balanced base-128 digits D_0 (most significant) .. D_7, and
+#   G[i, j] = round( sum_{s, t: min(s, t) <= 3} 2^(-7 (s + t + 2)) sum_p D_s(p, i) D_t(p, j)
+#                    * 2^(e_i + e_j) ).
+# The emulation below computes that with Python integers (no code shared with the kernel).
+
+def _col_exp(x):
+    m = float(np.abs(x).max())
+    if m == 0.0:
+        return 0
+    return math.frexp(m)[1] - 1 + 3          # unbiased exponent of the maximum, + 3
+
+
+def _digits(x, e):
+    y = np.trunc(np.ldexp(x, 56 - e)).astype(np.int64)   # exact: |y| < 2^54
+    z = y + sum(64 << (7 * k) for k in range(8))
+    return np.stack([((z >> (7 * (7 - s))) & 127) - 64 for s in range(8)])   # D_s, s = 0 most significant
+
+
+def _emulated_gram(W):
+    from fractions import Fraction
+    K = W.shape[0]
+    es = [_col_exp(W[i]) for i in range(K)]
+    D = np.stack([_digits(W[i], es[i]) for i in range(K)], axis=1)   # (8, K, P)
+    G = np.zeros((K, K))
+    dots = {}
+    for s in range(8):
+        for t in range(8):
+            if min(s, t) <= 3:
+                dots[s, t] = D[s] @ D[t].T      # int64, exact (|sum| < P 2^12)
+    for i in range(K):
+        for j in range(i, K):
+            S = sum(int(dots[s, t][i, j]) << (7 * (14 - s - t)) for (s, t) in dots)
+            G[i, j] = G[j, i] = float(Fraction(S) * Fraction(2) ** (es[i] + es[j] - 112))
+    return G
+
+
+def _hard_columns(n, K, B, seed):
+    """Seeded smooth fields at scales 1e-30 .. 1e30 plus the awkward cases: a zero column,
+    exact zeros and negative zeros inside a column, subnormal entries inside a normal
+    column, a column spanning 25 orders of magnitude, a column with a single nonzero."""
+    rng = np.random.default_rng(seed)
+    Ng = n ** 3
+    W = np.empty((B, K, Ng))
+    for b in range(B):
+        for i in range(K):
+            f = pi.initial_state(n, seed=1000 * b + i + 7).reshape(-1)
+            W[b, i] = 10.0 ** rng.uniform(-30, 30) * (f + 1e-3 * rng.standard_normal(Ng))
+    W[0, 0, ::7] = 0.0
+    W[0, 0, 1::7] = -0.0
+    if K > 1:
+        W[0, 1] = 0.0
+    if K > 2:
+        W[0, 2, ::5] = 5e-320                                   # subnormals
+    if K > 3:
+        W[0, 3] *= 10.0 ** rng.uniform(-25, 0, Ng)              # wide dynamic range
+    if K > 4:
+        W[0, 4] = 0.0
+        W[0, 4, Ng // 2] = -3.0
+    return W
+
+
+@pytest.mark.parametrize("n,K,B", [
+    (8, 5, 1),      # 512 points: one unit of 8 stages
+    (10, 32, 2),    # 1,000 points: two units, the second ragged (488 = 7 x 64 + 40)
+    (16, 17, 3),    # 4,096 points: eight units an item, 17 of 32 columns
+    (72, 6, 1),     # 373,248 points: units of 5,832 points, two accumulation windows each
+])
+def test_narrow_tensor_gram_is_exactly_the_digit_sum(gpu, n, K, B):
+    bd, torch = gpu
+    w = pi.Workload("gram", n, pi.Flow("abc"), 0.05, 1.0, 4, 1e-3, n_snap=64, m_cap=32)
+    s = bd.Parareal.from_workload(w, precision=bd.PR_FP32)
+    W = _hard_columns(n, K, B, seed=n * K)
+    Wt = torch.from_numpy(W).to("cuda")
+    Gt = s.op_gram(Wt, tensor=True).cpu().numpy()
+    s.close()
+    for b in range(B):
+        Ge = _emulated_gram(W[b])
+        bad = np.argwhere(Gt[b].view(np.int64) != Ge.view(np.int64))
+        assert bad.size == 0, (b, bad[:4].tolist(), [(Gt[b][tuple(ij)], Ge[tuple(ij)]) for ij in bad[:4]])
+
+
+@pytest.mark.parametrize("n,K,B", [(12, 32, 2), (20, 24, 5)])
+def test_narrow_tensor_gram_within_the_fp64_bound(gpu, n, K, B):
+    """The narrow form against exactly rounded dot products, within the bound of the wide
+    test (its dropped digit pairs are a subset of the wide form's)."""
+    bd, torch = gpu
+    w = pi.Workload("gram", n, pi.Flow("abc"), 0.05, 1.0, 4, 1e-3, n_snap=64, m_cap=32)
+    s = bd.Parareal.from_workload(w, precision=bd.PR_FP32)
+    W = _columns(n, K, B, seed=K + 1)
+    Wt = torch.from_numpy(W).to("cuda")
+    Gt = s.op_gram(Wt, tensor=True).cpu().numpy()
+    s.close()
+    worst = 0.0
+    for b in range(B):
+        for i in range(K):
+            for j in range(i, K):
+                if (i * 7 + j * 13) % 3:
+                    continue
+                x, y = W[b, i], W[b, j]
+                ex = _exact_dot(x, y)
+                bound = 2.0 ** -50 * float(np.sum(np.abs(x * y)) + np.abs(x).max() * np.abs(y).sum()
+                                          + np.abs(y).max() * np.abs(x).sum()) + 1e-300
+                worst = max(worst, abs(Gt[b, i, j] - ex) / bound)
+    assert worst < 1.0, worst
+
+
+@pytest.mark.parametrize("K", [4, 24, 32])
+def test_double_float_gram_agrees(gpu, K):
+    """pr_op_gram's double-float kernel (tensor = 2, the FP32 mode's default) against the
+    tensor-core and FP64 kernels on the same columns: all three FP64-accurate."""
+    bd, torch = gpu
+    n, B = 16, 3
+    w = pi.Workload("gram", n, pi.Flow("abc"), 0.05, 1.0, 4, 1e-3, n_snap=64, m_cap=32)
+    s = bd.Parareal.from_workload(w, precision=bd.PR_FP32)
+    W = _columns(n, K, B, seed=K + 5)
+    Wt = torch.from_numpy(W).to("cuda")
+    Gd = s.op_gram(Wt, tensor=False, df=True).cpu().numpy()
+    Gt = s.op_gram(Wt, tensor=True).cpu().numpy()
+    G64 = s.op_gram(Wt, tensor=False).cpu().numpy()
+    s.close()
+    for b in range(B):
+        sc = np.abs(G64[b]).max()
+        assert np.abs(Gd[b] - G64[b]).max() < 1e-14 * sc
+        assert np.abs(Gt[b] - G64[b]).max() < 1e-14 * sc
