@@ -399,7 +399,10 @@ pr_status cols_contig(pr_ctx* c, const char* base, size_t bstride_bytes, const i
 // FP64-accurate; gram_tc.cu) for 55..64 columns, which the double-float kernel does not
 // take (gram_mode PR_GRAM_AUTO), for every width up to 64 (PR_GRAM_TENSOR), or never
 // (PR_GRAM_DF); every other Gram runs in double-float or FP64.
-cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32) {
+// k_exact: every item has maxKA columns (a snapshot window), not a cap on a POD dimension
+// that lives on the device; the automatic choice of the tensor cores needs the column
+// count (a Gram of 4 columns under a cap of 32 is faster in double-float).
+cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32, bool k_exact) {
     const int mode = c->o.gram_mode;
     const bool fits = c->fp32 && !in_f32 && ga.sym && ga.colblk == nullptr && ga.maxKA <= gram_tc_max_cols() &&
                       ga.B <= (c->wave > 0 ? c->wave : c->N) + 1;
@@ -408,14 +411,14 @@ cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32) {
     // one (33..64) beyond the double-float kernel's 384 output tiles (55 columns)
     const bool narrow = ga.maxKA >= 24 && ga.maxKA <= 32;
     const bool wide = ga.maxKA > 54;
-    if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && (narrow || wide))))
+    if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && k_exact && (narrow || wide))))
         return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st);
     return launch_gram(ga, in_f32, in_f32, c->st);
 }
 
 pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, bool in_f32, int cap,
                        int mmax, char* dest, size_t dest_bstride_elems, int* m_dest,
-                       bool ortho_blocks = false) {
+                       bool ortho_blocks = false, bool k_exact = true) {
     const bool f32 = false;  // bases and their Grams are FP64
     cudaStream_t st = c->st;
     // Gram W^T W
@@ -438,7 +441,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     ga.df = c->fp32;   // FP32 mode: double-float Grams and projections on the FP32 pipe
     // the bases leave Cholesky QR orthonormal to ~1e-15, far below the FP32 mode's accuracy
     ga.colblk = (c->fp32 && ortho_blocks && !in_f32) ? c->colblk : nullptr;
-    PR_CUDA(gram_auto(c, ga, in_f32));
+    PR_CUDA(gram_auto(c, ga, in_f32, k_exact));
     // eigenpairs + dimension + C = Y_m Lambda_m^{-1/2}
     EigArgs ea{};
     ea.G = c->gout;
@@ -487,7 +490,7 @@ pr_status pod_pipeline(pr_ctx* c, int B, int maxK, double gamma, double tau, boo
     gb.maxKB = mmax;
     gb.ldG = mmax;
     gb.ldG_b = (long long)mmax * mmax;
-    PR_CUDA(gram_auto(c, gb, f32));
+    PR_CUDA(gram_auto(c, gb, f32, false));   // m_dest columns per item, mmax a cap
     PR_CUDA(launch_chol_inv(c->gout, mmax, (long long)mmax * mmax, m_dest, mmax, B, c->X, mmax,
                             (long long)mmax * mmax, c->derr, st));
     TsmmArgs tb = ta;
@@ -719,7 +722,7 @@ pr_status level2_range(pr_ctx* c, int n_lo, int n_hi, char* R2, BlocksOf blocks)
     pr_status s = upload_blocks(c, bs, cs, 3, B2, c->colsA, c->KA, c->esz, c->colblk);
     if (s != PR_OK) return s;
     s = pod_pipeline(c, B2, c->w2, c->gamma3, c->tau, false, c->o.m_cap, c->mcap2, R2, (size_t)c->mcap2 * Ng,
-                     c->m2 + n_lo, true);
+                     c->m2 + n_lo, true, false);
     if (s != PR_OK) return s;
     return galerkin(c, R2, (size_t)c->mcap2 * Ng, c->m2 + n_lo, B2, c->mcap2,
                     c->Mr + (size_t)n_lo * c->mcap2 * c->mcap2, c->Lr + (size_t)n_lo * 3 * c->mcap2 * c->mcap2, true);

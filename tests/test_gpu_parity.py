@@ -424,9 +424,14 @@ def test_solve_stops_at_oracle_iteration(gpu, precision):
 @pytest.mark.parametrize("wl", list(WORKLOADS))
 def test_parareal_iterates_fp64(gpu, wl):
     """Whole iterations, FP64 mode: within max(1e-12, 10 x the oracle's own change under a
-    1e-13 relative perturbation of u0) at every (k, n).  The augmentation direction of
-    eqs. (eqaug)/(eq12) is fixed only to eps/(||d~||/||U||), and the sequential sweep
-    amplifies it, so on some workloads no two correct implementations agree to 1e-12."""
+    1e-13 relative perturbation of u0) at every (k, n), i.e. a flat 1e-12 wherever the
+    oracle's response stays below 1e-13.  Where it does not, an iteration is not a
+    well-conditioned function of its inputs: on the 16^3 ABC workload the sqrt-lambda
+    criterion keeps a mode with lambda_4 / lambda_1 = 2e-8 (the kept subspace moves by
+    ~5e7 x a Gram rounding error, already at k = 0), and the augmentation normalises
+    residuals of 5e-9 ||U|| at k = 1; rounding-level Gram noise moves the oracle's own
+    iterates past 1e-12 with every POD dimension and augment/skip decision unchanged
+    (test_oracle_stopping_and_conditioning.py)."""
     bd, torch = gpu
     w = WORKLOADS[wl]()
     prm = O.derive_params(w)
