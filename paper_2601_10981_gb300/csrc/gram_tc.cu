@@ -164,33 +164,49 @@ __device__ __forceinline__ unsigned pack_bf16x2(int a, int b) {
 
 // colmax[b * ld + i] = bit pattern of max_p |W_b[p, i]| (non-negative doubles order like
 // their bit patterns), by atomicMax from each CTA's chunk; the buffer starts at zero.
+// Four columns at a time (four independent loads in flight per thread), per-warp maxima
+// in shared memory, one barrier and one atomic per column and CTA.
 __global__ void __launch_bounds__(256) colmax_kernel(GramArgs a, long long CH, unsigned long long* colmax,
                                                      int ld) {
     const int b = blockIdx.y;
     const int K = a.KA[b];
     const long long p_lo = (long long)blockIdx.x * CH, p_hi = min(a.Ng, p_lo + CH);
     const void* const* cols = a.colsA + (size_t)b * a.ldcols;
-    __shared__ unsigned long long red[8];
-    for (int i = 0; i < K; ++i) {
-        const double* c = reinterpret_cast<const double*>(cols[i]);
-        unsigned long long m = 0ull;
+    __shared__ unsigned long long red[8][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < K; i0 += 4) {
+        const double* c[4];
+        unsigned long long m[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            c[j] = (i0 + j < K) ? reinterpret_cast<const double*>(cols[i0 + j]) : nullptr;
+            m[j] = 0ull;
+        }
         for (long long p = p_lo + threadIdx.x; p < p_hi; p += blockDim.x) {
-            const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(c[p]));
-            m = v > m ? v : m;
+            double v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = c[j] ? c[j][p] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long x = (unsigned long long)__double_as_longlong(fabs(v[j]));
+                m[j] = x > m[j] ? x : m[j];
+            }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
-            m = o > m ? o : m;
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, m[j], off);
+                m[j] = o > m[j] ? o : m[j];
+            }
+            if (lane == 0 && i0 + j < K) red[warp][i0 + j] = m[j];
         }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0ull;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = red[w] > t ? red[w] : t;
-            if (t) atomicMax(colmax + (size_t)b * ld + i, t);
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        unsigned long long t = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = red[w][threadIdx.x] > t ? red[w][threadIdx.x] : t;
+        if (t) atomicMax(colmax + (size_t)b * ld + threadIdx.x, t);
     }
 }
 
@@ -563,7 +579,6 @@ __device__ __forceinline__ bool mbar_wait_f(unsigned mbar, unsigned parity, vola
     *fail = 1;
     return false;
 }
-
 __device__ __forceinline__ void mbar_arrive(unsigned mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
