@@ -282,19 +282,23 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
     auto quad = [&](const float* pln, int col, int q) {
         return *reinterpret_cast<const ulonglong2*>(pln + col * GDF_LDP + ((q ^ ((col >> 3) & 1)) << 2));
     };
-    load(rawA, ncA, KA, colsA, p_lo);
-    if (!a.sym) load(rawB, ncB, KB, colsB, p_lo);
+    // the item's own column counts (the buffers are laid out for the launch's largest):
+    // a POD window under a cap of 48 columns that holds 12 costs 12 columns of copies and
+    // conversions, not 48 (the tiles only read columns < gdf_cols(K))
+    const int kA = gdf_cols(KA), kB = a.sym ? 0 : gdf_cols(KB);
+    load(rawA, kA, KA, colsA, p_lo);
+    if (!a.sym) load(rawB, kB, KB, colsB, p_lo);
     cp_async_commit();
     int nblk = 0;
     for (long long p0 = p_lo; p0 < p_hi; p0 += GDF_SUB) {
         cp_async_wait_all();
         __syncthreads();   // this block's rows landed; every thread is done with the planes
-        convert(rawA, sA, plA, ncA);
-        if (!a.sym) convert(rawB, sB, plB, ncB);
+        convert(rawA, sA, plA, kA);
+        if (!a.sym) convert(rawB, sB, plB, kB);
         __syncthreads();   // planes ready, raw buffers free
         if (p0 + GDF_SUB < p_hi) {
-            load(rawA, ncA, KA, colsA, p0 + GDF_SUB);
-            if (!a.sym) load(rawB, ncB, KB, colsB, p0 + GDF_SUB);
+            load(rawA, kA, KA, colsA, p0 + GDF_SUB);
+            if (!a.sym) load(rawB, kB, KB, colsB, p0 + GDF_SUB);
         }
         cp_async_commit();
         if (active) {
