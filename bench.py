@@ -430,14 +430,16 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def fine_bytes_per_dof_step(w_bytes: int, lin_iters: float, dM: int, has_f: bool) -> float:
+def fine_bytes_per_dof_step(w_bytes: int, lin_iters: float, dM: int, has_f: bool, has_pert: bool = False) -> float:
     """Algorithmic DRAM bytes of the fused fine sweep per grid point and fine step:
     setup reads the state (8 B: FP64, or the hi + lo float pair of the FP32 mode) and
     delta (w), writes the state (8 B), r and rhat (2w), reads f (w); each BiCGStab
     iteration streams 17 words (phase 1: r, p', v', rhat in, p, v out; phase 2: r, v in,
     t out; phase 3: delta, p, r, v, t, rhat in, delta, r out); one FP64 snapshot value
-    every dM steps."""
-    return 16 + 3 * w_bytes + (w_bytes if has_f else 0) + lin_iters * 17 * w_bytes + 8 / dM
+    every dM steps.  A stored velocity perturbation adds its three words at every stencil
+    march: the setup's and two per BiCGStab iteration."""
+    pert = 3 * w_bytes * (1 + 2 * lin_iters) if has_pert else 0.0
+    return 16 + 3 * w_bytes + (w_bytes if has_f else 0) + lin_iters * 17 * w_bytes + 8 / dM + pert
 
 
 def serving_sample(n_req: int, rate: float, t_scale: float, seed: int = 5):
@@ -598,7 +600,7 @@ def _large_leg(bd, config, torch, steps=2):
         lin_mean = float(tot.sum()) / (w.n_sub * s.S)
         t_ms, fine_ms, launches = _timed_iterations(s, s.stream, steps, 1, torch, wave=True)
         dofs = w.n_sub * s.S * w.Ng
-        bpd = fine_bytes_per_dof_step(4, lin_mean, s.dM, w.f_seed is not None)
+        bpd = fine_bytes_per_dof_step(4, lin_mean, s.dM, w.f_seed is not None, w.flow.pert_seed > 0)
         peak, _ = measured_peaks()
         ws_gib = s.workspace_bytes() / 2**30
         s.close()
@@ -695,7 +697,7 @@ def run_ours(args):
     e2e_val = ws * dofs_per_step / (e2e_ms * 1e-3) / 1e9
 
     wb = 4 if args.precision == "fp32" else 8
-    bpd = fine_bytes_per_dof_step(wb, lin_mean, s.dM, w.f_seed is not None)
+    bpd = fine_bytes_per_dof_step(wb, lin_mean, s.dM, w.f_seed is not None, w.flow.pert_seed > 0)
     achieved = bpd * dofs_per_step / (fine_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = recorded_traffic(args.precision) if args.config == "c2" and not args.subintervals else None

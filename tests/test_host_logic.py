@@ -51,6 +51,9 @@ def test_fine_traffic_model():
     # FP32: 16 + 12 + 8 (f) + 17*4*n_it + 4/dM
     assert bench.fine_bytes_per_dof_step(4, 3.0, 5, True) == 16 + 12 + 4 + 204 + 1.6
     assert bench.fine_bytes_per_dof_step(8, 2.0, 4, False) == 16 + 24 + 272 + 2
+    # a stored velocity perturbation: three words at the setup's stencil and at two per
+    # BiCGStab iteration
+    assert bench.fine_bytes_per_dof_step(4, 1.0, 41, False, True) == 16 + 12 + 68 + 8 / 41 + 36
 
 
 def test_clock_sampler_parses_reasons():
