@@ -445,8 +445,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
             for (int o = tid; o < K * K; o += TC_THREADS) {
                 const int i = o / K, j = o - i * K;
                 if (j < i) continue;
+                // chunk order (reproducible), loads in batches of 16 independent ones
+                const double* src = bpart + (size_t)i * a.maxKB + j;
                 double sum = 0.0;
-                for (int cc = 0; cc < chunks; ++cc) sum += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
+                int cc = 0;
+                for (; cc + 16 <= chunks; cc += 16) {
+                    double v[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = src[(size_t)(cc + e) * outsz];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) sum += v[e];
+                }
+                for (; cc < chunks; ++cc) sum += src[(size_t)cc * outsz];
                 Gb[(size_t)i * a.ldG + j] = sum;
                 Gb[(size_t)j * a.ldG + i] = sum;
             }

@@ -64,8 +64,19 @@ __device__ void gram_finish(const GramArgs& a, int b, int chunks, int KA, int KB
     for (int o = threadIdx.x; o < nout; o += blockDim.x) {
         int i, j;
         out_index(o, KA, KB, a.sym, i, j);
+        // in chunk order (reproducible), the loads in batches of 16 independent ones (a
+        // chain of dependent loads here held the item's last CTA for tens of microseconds)
+        const double* src = bpart + (size_t)i * a.maxKB + j;
         double s = 0.0;
-        for (int cc = 0; cc < chunks; ++cc) s += bpart[(size_t)cc * outsz + (size_t)i * a.maxKB + j];
+        int cc = 0;
+        for (; cc + 16 <= chunks; cc += 16) {
+            double v[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = src[(size_t)(cc + e) * outsz];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) s += v[e];
+        }
+        for (; cc < chunks; ++cc) s += src[(size_t)cc * outsz];
         Gb[(size_t)i * a.ldG + j] = s;
         if (a.sym) Gb[(size_t)j * a.ldG + i] = s;
     }
