@@ -358,11 +358,10 @@ pr_status pr_op_coarse_update(pr_ctx* ctx, const void* d_R, int m, const double*
  * it before returning.  A stored velocity perturbation (pr_flow.pert) lives in the
  * workspace: with one, bind the workspace and call pr_set_initial first
  * (PR_ERR_UNSUPPORTED otherwise).  The first call on a device looks up the array's device
- * address and keeps it for the life of the process; make that call before any stream
- * capture, and do not use the library across a cudaDeviceReset (the kept address would be
- * stale).  All calls share the array and leave the last call's contents; each call
- * rewrites what it reads, but calls that overlap on the GPU (different streams, no
- * ordering) race on it.  The paper has no counterpart: this is library plumbing. */
+ * address and keeps it for the life of the process; do not use the library across a
+ * cudaDeviceReset (the kept address would be stale).  All calls share the array and leave
+ * the last call's contents; each call rewrites what it reads, but calls that overlap on
+ * the GPU (different streams, no ordering) race on it.  The paper has no counterpart: this is library plumbing. */
 pr_status pr_op_apply_L_noalloc(pr_ctx* ctx, const double* d_in, double* d_out, int count,
                                 int transpose);
 

@@ -14,9 +14,8 @@
 // call rewrites all of it that it reads, so nothing needs clearing.  Two calls whose work
 // overlaps on the GPU (different streams, no ordering) race on it.  The device address of
 // the array is looked up with cudaGetSymbolAddress on the first call on each device, with
-// that device current, and kept for the life of the process; make that first call before
-// any stream capture, and do not use the library across a cudaDeviceReset, which would
-// leave the kept address stale.
+// that device current, and kept for the life of the process; do not use the library
+// across a cudaDeviceReset, which would leave the kept address stale.
 #include "pr_internal.cuh"
 
 #include <algorithm>
