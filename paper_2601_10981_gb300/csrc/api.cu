@@ -412,7 +412,7 @@ cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32, bool k_exact) 
     const bool narrow = ga.maxKA >= 24 && ga.maxKA <= 32;
     const bool wide = ga.maxKA > 54;
     if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && k_exact && (narrow || wide))))
-        return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st);
+        return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->o.spin_limit, c->st);
     return launch_gram(ga, in_f32, in_f32, c->st);
 }
 
@@ -1848,7 +1848,7 @@ pr_status pr_op_gram(pr_ctx* c, const double* d_W, int n_cols, int B, double* d_
     ga.ldG = n_cols;
     ga.ldG_b = (long long)n_cols * n_cols;
     ga.df = (tensor == 2);
-    if (tensor == 1) PR_CUDA(launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->st));
+    if (tensor == 1) PR_CUDA(launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->o.spin_limit, c->st));
     else PR_CUDA(launch_gram(ga, false, false, c->st));
     return pr_sync(c);
 }

@@ -94,9 +94,9 @@ __device__ __forceinline__ void mma_commit(unsigned mbar) {
 }
 
 // Bounded wait for phase `parity` of the mbarrier (non-blocking test, short sleeps: about
-// a second at most); false on time-out.
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
-    for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+// a second at most with the default limit); false on time-out.
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity, long long limit = TC_SPIN_LIMIT) {
+    for (long long it = 0; it <= limit; ++it) {
         unsigned ok = 0;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) colmax_kernel(GramArgs a, long long CH, u
 
 __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long long CH, int chunks,
                                                                 const unsigned long long* colmax, int ld,
-                                                                int* err) {
+                                                                int* err, long long limit) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long s_mbar[2];
     __shared__ unsigned s_tmem;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(GramArgs a, long
     // wait for the MMAs that read stage buffer q (all threads; one vote decides)
     auto wait_buf = [&](int q) -> bool {
         if (!pending[q]) return true;
-        const bool ok = mbar_wait(mbar0 + 8u * q, parity[q]);
+        const bool ok = mbar_wait(mbar0 + 8u * q, parity[q], limit);
         parity[q] ^= 1u;
         pending[q] = false;
         return __syncthreads_or(ok ? 0 : 1) == 0;
@@ -572,10 +572,10 @@ __device__ __forceinline__ void cut56(double x, int ce, unsigned& zl, unsigned& 
 
 // Bounded mbarrier wait that also gives up once another thread has recorded a failure.
 // try_wait suspends the thread (at most ~1 us a try, by its time hint) instead of
-// spinning, so waiting warps leave the issue slots to the others; 2^20 tries ~ 1 s.
-constexpr int TC_TRY_LIMIT = 1 << 20;
-__device__ __forceinline__ bool mbar_wait_f(unsigned mbar, unsigned parity, volatile int* fail) {
-    for (int it = 0; it < TC_TRY_LIMIT; ++it) {
+// spinning, so waiting warps leave the issue slots to the others; `limit` tries (the
+// context's spin limit, 2^22 ~ a few seconds by default; 0: one try).
+__device__ __forceinline__ bool mbar_wait_f(unsigned mbar, unsigned parity, volatile int* fail, long long limit) {
+    for (long long it = 0; it <= limit; ++it) {
         unsigned ok = 0;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n\t"
@@ -633,7 +633,7 @@ __device__ __forceinline__ double i128_to_double(__int128 S, int sc) {
 // 9 warps: three share one SM sub-partition's 16K registers, so at most 168 a thread
 __global__ void __launch_bounds__(N2_THREADS, 1) gram_tc32_kernel(GramArgs a, long long U, int chunks,
                                                                   const unsigned long long* colmax, int ld,
-                                                                  int* err) {
+                                                                  int* err, long long limit) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long s_bar[2 * N2_NS + 5];
     __shared__ unsigned s_tmem;
@@ -692,11 +692,11 @@ __global__ void __launch_bounds__(N2_THREADS, 1) gram_tc32_kernel(GramArgs a, lo
                 for (long long w0 = lo; w0 < hi; w0 += N2_WIN, ++gw) {
                     const long long w1 = min(hi, w0 + N2_WIN);
                     const int h = gw & 1;
-                    if (!bad && !mbar_wait_f(tempty0 + 8u * h, ((gw >> 1) & 1) ^ 1, &s_fail)) bad = true;
+                    if (!bad && !mbar_wait_f(tempty0 + 8u * h, ((gw >> 1) & 1) ^ 1, &s_fail, limit)) bad = true;
                     const unsigned td = tmem + (unsigned)(h * 256);
                     for (long long p0 = w0; p0 < w1; p0 += N2_PTS, ++gs) {
                         const int q = gs % N2_NS;
-                        if (!bad && !mbar_wait_f(full0 + 8u * q, (gs / N2_NS) & 1, &s_fail)) bad = true;
+                        if (!bad && !mbar_wait_f(full0 + 8u * q, (gs / N2_NS) & 1, &s_fail, limit)) bad = true;
                         if (!bad) {
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                             const unsigned sb = stage_s + q * N2_STAGE_BYTES;
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(N2_THREADS, 1) gram_tc32_kernel(GramArgs a, lo
 
         auto readback = [&]() {
             const int h = pw & 1;
-            if (!bad && !mbar_wait_f(tfull0 + 8u * h, (pw >> 1) & 1, &s_fail)) bad = true;
+            if (!bad && !mbar_wait_f(tfull0 + 8u * h, (pw >> 1) & 1, &s_fail, limit)) bad = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned base = tmem + ((unsigned)(32 * qd) << 16) + (unsigned)(h * 256 + 16 * ch);
             long long* hrow = sH + (qd * 32 + lane) * N2_XP + 16 * ch;
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(N2_THREADS, 1) gram_tc32_kernel(GramArgs a, lo
             if (P.p0 == P.lo)   // a new unit: this thread's column exponent
                 ce = col_exp(P.c ? colmax[(size_t)P.b * ld + col] : 0ull) + 1020;
             asm volatile("cp.async.wait_group %0;" ::"n"(N2_DEPTH) : "memory");   // this stage's copies
-            if (!bad && !mbar_wait_f(empty0 + 8u * q, eph, &s_fail)) bad = true;
+            if (!bad && !mbar_wait_f(empty0 + 8u * q, eph, &s_fail, limit)) bad = true;
             if (P.c) {
                 double xc[8];
                 const unsigned char* sp = stg + (size_t)slot * N2_STG_BYTES + (size_t)tid * 16;
@@ -941,7 +941,8 @@ __global__ void __launch_bounds__(N2_THREADS, 1) gram_tc32_kernel(GramArgs a, lo
 
 int gram_tc_max_cols() { return TC_N; }
 
-cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld, int* err, cudaStream_t st) {
+cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld, int* err, long long spin_limit,
+                           cudaStream_t st) {
     if (!a.sym || a.maxKA > TC_N || a.maxKA <= 0 || !colmax || !err || ld < a.maxKA) return cudaErrorInvalidValue;
     if (a.B <= 0) return cudaSuccess;
     // the chunks of the other Gram kernels, so that the partial buffer (gram_part_doubles)
@@ -972,12 +973,12 @@ cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld
                                  N2_SMEM);
         if (e != cudaSuccess) return e;
         const int grid2 = std::max(1, std::min(sms, a.B * chunks2));
-        gram_tc32_kernel<<<grid2, N2_THREADS, N2_SMEM, st>>>(a, U2, chunks2, colmax, ld, err);
+        gram_tc32_kernel<<<grid2, N2_THREADS, N2_SMEM, st>>>(a, U2, chunks2, colmax, ld, err, spin_limit);
         ++g_launch_count;
         return cudaGetLastError();
     }
     const int grid = std::max(1, std::min(sms, a.B * chunks));
-    gram_tc_kernel<<<grid, TC_THREADS, smem, st>>>(a, CH, chunks, colmax, ld, err);
+    gram_tc_kernel<<<grid, TC_THREADS, smem, st>>>(a, CH, chunks, colmax, ld, err, spin_limit);
     ++g_launch_count;
     return cudaGetLastError();
 }

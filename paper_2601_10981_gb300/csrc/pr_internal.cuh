@@ -270,8 +270,11 @@ cudaError_t launch_gram(const GramArgs& a, bool a_f32, bool b_f32, cudaStream_t 
 // Symmetric Gram W^T W of up to 64 FP64 columns on the tensor cores (tcgen05, error-free
 // BF16 digits, FP64-accurate; gram_tc.cu; up to 32 columns the narrow, exactly summed
 // form when the partial buffer holds two chunks of the other Gram kernels per unit).  colmax: device scratch of B x ld (ld >= maxKA)
-// 64-bit words; err: device error flag (PR_ERR_TIMEOUT if an MMA completion wait times out).
-cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld, int* err, cudaStream_t st);
+// 64-bit words; err: device error flag (PR_ERR_TIMEOUT if a wait on an mbarrier gives up
+// after spin_limit polls; the MMAs in flight are then waited for, with the default bound,
+// and the tensor memory freed).
+cudaError_t launch_gram_tc(const GramArgs& a, unsigned long long* colmax, int ld, int* err, long long spin_limit,
+                           cudaStream_t st);
 int gram_tc_max_cols();
 // M_b = I_{m[b]} for b < B (row stride ld, batch stride ld_b).
 cudaError_t launch_identity(double* M, int ld, long long ld_b, const int* m, int B, cudaStream_t st);

@@ -237,3 +237,28 @@ def test_double_float_gram_agrees(gpu, K):
         sc = np.abs(G64[b]).max()
         assert np.abs(Gd[b] - G64[b]).max() < 1e-14 * sc
         assert np.abs(Gt[b] - G64[b]).max() < 1e-14 * sc
+
+
+@pytest.mark.parametrize("K", [16, 40])
+def test_tensor_gram_wait_timeout_is_reported_and_the_device_stays_usable(gpu, K):
+    """Failure path of the tensor-core Grams (narrow form for 16 columns, wide for 40):
+    with a spin limit of 0 every mbarrier wait that is not already complete gives up at
+    once; the kernel records PR_ERR_TIMEOUT, waits (with its own bound) for the MMAs in
+    flight, frees its tensor memory and returns.  The host reads the status, and a fresh
+    context on the same device computes the Gram correctly afterwards."""
+    bd, torch = gpu
+    n, B = 16, 3
+    w = pi.Workload("gram", n, pi.Flow("abc"), 0.05, 1.0, 4, 1e-3, n_snap=64, m_cap=32)
+    W = _columns(n, K, B, seed=K + 9)
+    Wt = torch.from_numpy(W).to("cuda")
+    s = bd.Parareal.from_workload(w, precision=bd.PR_FP32, spin_limit=0)
+    with pytest.raises(bd.PRError) as ei:
+        s.op_gram(Wt, tensor=True)
+    assert ei.value.status == 6
+    s.close()
+    s2 = bd.Parareal.from_workload(w, precision=bd.PR_FP32)
+    Gt = s2.op_gram(Wt, tensor=True).cpu().numpy()
+    G64 = s2.op_gram(Wt, tensor=False).cpu().numpy()
+    s2.close()
+    for b in range(B):
+        assert np.abs(Gt[b] - G64[b]).max() < 1e-14 * np.abs(G64[b]).max()
