@@ -143,13 +143,14 @@ enum pr_fine { PR_FINE_IMPLICIT_EULER = 0, PR_FINE_RK4 = 1 };
 enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1, PR_METHOD_PARAREAL_II = 2 };
 
 /* Symmetric Gram kernels of the FP32 mode.  PR_GRAM_DF: double-float arithmetic on the
- * FP32 pipe (up to 54 columns; FP64 beyond).  PR_GRAM_TENSOR: the tensor cores, with the
- * values cut into error-free BF16 digits (FP64-accurate, see pr_op_gram; up to 64 columns,
- * double-float beyond).  PR_GRAM_AUTO: the tensor cores for snapshot windows of 24..32
- * columns (where the narrow tensor-core form is faster) and 55..64 columns (where the
- * double-float kernel does not reach), double-float otherwise (and for the Cholesky-QR
- * Grams, whose column counts are POD dimensions known only on the device).  The FP64
- * mode always forms its Grams in FP64. */
+ * FP32 pipe (up to 126 columns, windows wider than 54 columns in several passes over the
+ * data; FP64 beyond).  PR_GRAM_TENSOR: the tensor cores, with the values cut into
+ * error-free BF16 digits (FP64-accurate, see pr_op_gram; up to 64 columns, double-float
+ * beyond).  PR_GRAM_AUTO: the tensor cores for snapshot windows of 24..32 columns (where
+ * the narrow tensor-core form is faster) and 55..64 columns (where the double-float
+ * kernel would need two passes), double-float otherwise (and for the Cholesky-QR Grams,
+ * whose column counts are POD dimensions known only on the device).  The FP64 mode always
+ * forms its Grams in FP64. */
 enum pr_gram_mode { PR_GRAM_AUTO = 0, PR_GRAM_DF = 1, PR_GRAM_TENSOR = 2 };
 
 /* Per-solve report (pr_solve).  Times are seconds measured with CUDA events. */

@@ -408,7 +408,7 @@ cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32, bool k_exact) 
                       ga.B <= (c->wave > 0 ? c->wave : c->N) + 1;
     // measured crossovers against the double-float kernel (64 items x 262,144 points): the
     // narrow tensor form (<= 32 columns) wins from 24 columns (32: 3.8 vs 6.7 ms), the wide
-    // one (33..64) beyond the double-float kernel's 384 output tiles (55 columns)
+    // one (33..64) beyond the double-float kernel's 384 output tiles a pass (55 columns)
     const bool narrow = ga.maxKA >= 24 && ga.maxKA <= 32;
     const bool wide = ga.maxKA > 54;
     if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && k_exact && (narrow || wide))))

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_kernel(GramArgs a, long lon
 // level-2 2.37 -> 2.25 with 128 rows; a 160-thread level-1 Gram took 6.83 ms with 64 rows
 // and 7.00 with 128); a column plane holds SUB + 4 floats.
 constexpr int GDF_MAXTHR = 384;
+constexpr int GDF_MAXTILES = 2048;   // tiles of one item (2 x 2 each): up to 126 columns (sym)
 
 template <int SUB>
 __device__ __forceinline__ int gdf_pos(int col, int r) {
@@ -215,175 +216,187 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
     const void* const* colsB = (a.sym ? a.colsA : a.colsB) + (size_t)b * a.ldcols;
 
     const int nbA = (KA + 1) / 2, nbB = (KB + 1) / 2;
-    int ntiles = gdf_tiles(KA, KB, a.sym);
+    int ntiles_all = gdf_tiles(KA, KB, a.sym);
     const size_t outsz = (size_t)a.maxKA * a.maxKB;
     double* mypart = a.part + ((size_t)b * chunks + c) * outsz;
     // Blocks with orthonormal columns: a tile inside one diagonal block is the identity
     // (written here: 1 on the diagonal from chunk 0, 0 elsewhere); the remaining tiles
-    // are listed in order and shared out as usual.
-    __shared__ short s_tile[GDF_MAXTHR];
+    // are listed in order and shared out as usual.  The list is built nthr tiles a round.
+    __shared__ short s_tile[GDF_MAXTILES];
     __shared__ int s_wcnt[GDF_MAXTHR / 32 + 1];
     const bool compact = a.sym && a.colblk != nullptr;
     if (compact) {
         const int* blk = a.colblk + (size_t)b * a.ldcols;
-        bool need = false;
-        if (tid < ntiles) {
-            int bi, bj;
-            out_index(tid, nbA, nbB, true, bi, bj);
-            const int i0 = 2 * bi, j0 = 2 * bj, q = blk[i0];
-            const bool same = (i0 + 1 >= KA || blk[i0 + 1] == q) && blk[j0] == q && (j0 + 1 >= KA || blk[j0 + 1] == q);
-            need = !same;
-            if (same) {
-                for (int r = 0; r < 2; ++r)
-                    for (int s2 = 0; s2 < 2; ++s2) {
-                        const int i = i0 + r, j = j0 + s2;
-                        if (i < KA && j < KA && i <= j)
-                            mypart[(size_t)i * a.maxKB + j] = (i == j && c == 0) ? 1.0 : 0.0;
-                    }
+        int base = 0;
+        for (int t0 = 0; t0 < ntiles_all; t0 += nthr) {
+            const int t = t0 + tid;
+            bool need = false;
+            if (t < ntiles_all) {
+                int bi, bj;
+                out_index(t, nbA, nbB, true, bi, bj);
+                const int i0 = 2 * bi, j0 = 2 * bj, q = blk[i0];
+                const bool same =
+                    (i0 + 1 >= KA || blk[i0 + 1] == q) && blk[j0] == q && (j0 + 1 >= KA || blk[j0 + 1] == q);
+                need = !same;
+                if (same) {
+                    for (int r = 0; r < 2; ++r)
+                        for (int s2 = 0; s2 < 2; ++s2) {
+                            const int i = i0 + r, j = j0 + s2;
+                            if (i < KA && j < KA && i <= j)
+                                mypart[(size_t)i * a.maxKB + j] = (i == j && c == 0) ? 1.0 : 0.0;
+                        }
+                }
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, need);
+            const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = 0, tot = 0;
+            for (int w = 0; w < nw; ++w) {
+                const int cw = s_wcnt[w];
+                off += (w < warp) ? cw : 0;
+                tot += cw;
+            }
+            if (need) s_tile[base + off + __popc(bal & ((1u << lane) - 1u))] = (short)t;
+            base += tot;
+            __syncthreads();
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, need);
-        const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int cw = s_wcnt[w];
-            off += (w < warp) ? cw : 0;
-            tot += cw;
-        }
-        if (need) s_tile[off + __popc(bal & ((1u << lane) - 1u))] = (short)tid;
-        ntiles = tot;
-        __syncthreads();
+        ntiles_all = base;
     }
-    const int P = ntiles > 0 ? max(1, nthr / ntiles) : 1;
-    const int grp = ntiles > 0 ? tid / ntiles : P;
-    const bool active = grp < P;
-    int ti = 0, tj = 0;
-    if (active) {
-        int bi, bj;
-        const int t = tid - grp * ntiles;
-        out_index(compact ? (int)s_tile[t] : t, nbA, nbB, a.sym, bi, bj);
-        ti = 2 * bi;
-        tj = 2 * bj;
-    }
-    f2p sh[2][2], sl[2][2], Ah[2][2], Al[2][2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) sh[r][q] = sl[r][q] = Ah[r][q] = Al[r][q] = 0ull;
-    auto load = [&](double* raw, int ncols, int K, const void* const* cols, long long p0) {
-        for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
-            const int col = e / GDF_SUB, r = e - col * GDF_SUB;
-            const long long p = p0 + r;
-            const bool ok = col < K && p < p_hi;
-            const double* src = ok ? reinterpret_cast<const double*>(cols[col]) + p : reinterpret_cast<const double*>(a.part);
-            cp_async8(raw + e, src, ok ? 8 : 0);
-        }
-    };
-    auto convert = [&](const double* raw, float* dst, int pl, int ncols) {
-        for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
-            const int col = e / GDF_SUB, r = e - col * GDF_SUB;
-            const float2 v = d2df_bits(raw[e]);
-            const int o = gdf_pos<SUB>(col, r);
-            dst[o] = v.x;
-            dst[pl + o] = v.y;
-        }
-    };
-    auto quad = [&](const float* pln, int col, int q) {
-        return *reinterpret_cast<const ulonglong2*>(pln + col * GDF_LDP + ((q ^ ((col >> 3) & 1)) << 2));
-    };
-    // the item's own column counts (the buffers are laid out for the launch's largest):
-    // a POD window under a cap of 48 columns that holds 12 costs 12 columns of copies and
-    // conversions, not 48 (the tiles only read columns < gdf_cols(K))
-    const int kA = gdf_cols(KA), kB = a.sym ? 0 : gdf_cols(KB);
-    load(rawA, kA, KA, colsA, p_lo);
-    if (!a.sym) load(rawB, kB, KB, colsB, p_lo);
-    cp_async_commit();
-    int nblk = 0;
-    for (long long p0 = p_lo; p0 < p_hi; p0 += GDF_SUB) {
-        cp_async_wait_all();
-        __syncthreads();   // this block's rows landed; every thread is done with the planes
-        convert(rawA, sA, plA, kA);
-        if (!a.sym) convert(rawB, sB, plB, kB);
-        __syncthreads();   // planes ready, raw buffers free
-        if (p0 + GDF_SUB < p_hi) {
-            load(rawA, kA, KA, colsA, p0 + GDF_SUB);
-            if (!a.sym) load(rawB, kB, KB, colsB, p0 + GDF_SUB);
-        }
-        cp_async_commit();
+    // passes of at most nthr tiles (more than one only for items wider than the launch's
+    // threads cover; each pass streams the chunk again)
+    for (int t_base = 0; t_base < ntiles_all; t_base += nthr) {
+        const int ntiles = min(nthr, ntiles_all - t_base);
+        const int P = max(1, nthr / ntiles);
+        const int grp = tid / ntiles;
+        const bool active = grp < P;
+        int ti = 0, tj = 0;
         if (active) {
+            int bi, bj;
+            const int t = t_base + tid - grp * ntiles;
+            out_index(compact ? (int)s_tile[t] : t, nbA, nbB, a.sym, bi, bj);
+            ti = 2 * bi;
+            tj = 2 * bj;
+        }
+        f2p sh[2][2], sl[2][2], Ah[2][2], Al[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) sh[r][q] = sl[r][q] = Ah[r][q] = Al[r][q] = 0ull;
+        auto load = [&](double* raw, int ncols, int K, const void* const* cols, long long p0) {
+            for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
+                const int col = e / GDF_SUB, r = e - col * GDF_SUB;
+                const long long p = p0 + r;
+                const bool ok = col < K && p < p_hi;
+                const double* src = ok ? reinterpret_cast<const double*>(cols[col]) + p : reinterpret_cast<const double*>(a.part);
+                cp_async8(raw + e, src, ok ? 8 : 0);
+            }
+        };
+        auto convert = [&](const double* raw, float* dst, int pl, int ncols) {
+            for (int e = tid; e < ncols * GDF_SUB; e += nthr) {
+                const int col = e / GDF_SUB, r = e - col * GDF_SUB;
+                const float2 v = d2df_bits(raw[e]);
+                const int o = gdf_pos<SUB>(col, r);
+                dst[o] = v.x;
+                dst[pl + o] = v.y;
+            }
+        };
+        auto quad = [&](const float* pln, int col, int q) {
+            return *reinterpret_cast<const ulonglong2*>(pln + col * GDF_LDP + ((q ^ ((col >> 3) & 1)) << 2));
+        };
+        // the item's own column counts (the buffers are laid out for the launch's largest):
+        // a POD window under a cap of 48 columns that holds 12 costs 12 columns of copies and
+        // conversions, not 48 (the tiles only read columns < gdf_cols(K))
+        const int kA = gdf_cols(KA), kB = a.sym ? 0 : gdf_cols(KB);
+        load(rawA, kA, KA, colsA, p_lo);
+        if (!a.sym) load(rawB, kB, KB, colsB, p_lo);
+        cp_async_commit();
+        int nblk = 0;
+        for (long long p0 = p_lo; p0 < p_hi; p0 += GDF_SUB) {
+            cp_async_wait_all();
+            __syncthreads();   // this block's rows landed; every thread is done with the planes
+            convert(rawA, sA, plA, kA);
+            if (!a.sym) convert(rawB, sB, plB, kB);
+            __syncthreads();   // planes ready, raw buffers free
+            if (p0 + GDF_SUB < p_hi) {
+                load(rawA, kA, KA, colsA, p0 + GDF_SUB);
+                if (!a.sym) load(rawB, kB, KB, colsB, p0 + GDF_SUB);
+            }
+            cp_async_commit();
+            if (active) {
 #pragma unroll 1
-            for (int q = grp; q < GDF_SUB / 4; q += P) {
-                ulonglong2 bh[2], bl[2];
-#pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2) {
-                    bh[s2] = quad(sB, tj + s2, q);
-                    bl[s2] = quad(sB + plb, tj + s2, q);
-                }
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const ulonglong2 ah = quad(sA, ti + r, q), al = quad(sA + plA, ti + r, q);
-                    const f2p nx = neg2(ah.x), ny = neg2(ah.y);
+                for (int q = grp; q < GDF_SUB / 4; q += P) {
+                    ulonglong2 bh[2], bl[2];
 #pragma unroll
                     for (int s2 = 0; s2 < 2; ++s2) {
-                        df_mac2(sh[r][s2], sl[r][s2], ah.x, nx, al.x, bh[s2].x, bl[s2].x);
-                        df_mac2(sh[r][s2], sl[r][s2], ah.y, ny, al.y, bh[s2].y, bl[s2].y);
+                        bh[s2] = quad(sB, tj + s2, q);
+                        bl[s2] = quad(sB + plb, tj + s2, q);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const ulonglong2 ah = quad(sA, ti + r, q), al = quad(sA + plA, ti + r, q);
+                        const f2p nx = neg2(ah.x), ny = neg2(ah.y);
+#pragma unroll
+                        for (int s2 = 0; s2 < 2; ++s2) {
+                            df_mac2(sh[r][s2], sl[r][s2], ah.x, nx, al.x, bh[s2].x, bl[s2].x);
+                            df_mac2(sh[r][s2], sl[r][s2], ah.y, ny, al.y, bh[s2].y, bl[s2].y);
+                        }
                     }
                 }
             }
-        }
-        if (++nblk == P) {   // SUB rows a thread since the last fold
+            if (++nblk == P) {   // SUB rows a thread since the last fold
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2) {
-                    df_add2(Ah[r][s2], Al[r][s2], sh[r][s2], sl[r][s2]);
-                    sh[r][s2] = sl[r][s2] = 0ull;
-                }
-            nblk = 0;
-        }
-    }
-    cp_async_wait_all();   // the last (empty) group
-    double acc[2][2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2) {
-            df_add2(Ah[r][s2], Al[r][s2], sh[r][s2], sl[r][s2]);
-            const float2 h = upk2(Ah[r][s2]), l = upk2(Al[r][s2]);
-            acc[r][s2] = df_to_double(h.x, l.x) + df_to_double(h.y, l.y);   // even + odd rows
-        }
-    // groups > 0 hand their sums to group 0 through shared memory
-    double* sacc = reinterpret_cast<double*>(smem_raw);
-    if (P > 1) {
-        __syncthreads();
-        if (active && grp > 0) {
-            double* d = sacc + ((size_t)(grp - 1) * ntiles + (tid - grp * ntiles)) * 4;
-            d[0] = acc[0][0];
-            d[1] = acc[0][1];
-            d[2] = acc[1][0];
-            d[3] = acc[1][1];
-        }
-        __syncthreads();
-        if (active && grp == 0) {
-            for (int gg = 1; gg < P; ++gg) {
-                const double* d = sacc + ((size_t)(gg - 1) * ntiles + tid) * 4;
-                acc[0][0] += d[0];
-                acc[0][1] += d[1];
-                acc[1][0] += d[2];
-                acc[1][1] += d[3];
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        df_add2(Ah[r][s2], Al[r][s2], sh[r][s2], sl[r][s2]);
+                        sh[r][s2] = sl[r][s2] = 0ull;
+                    }
+                nblk = 0;
             }
         }
-    }
-    if (active && grp == 0) {
+        cp_async_wait_all();   // the last (empty) group
+        double acc[2][2];
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
-                const int i = ti + r, j = tj + s2;
-                if (i < KA && j < KB && (!a.sym || i <= j)) mypart[(size_t)i * a.maxKB + j] = acc[r][s2];
+                df_add2(Ah[r][s2], Al[r][s2], sh[r][s2], sl[r][s2]);
+                const float2 h = upk2(Ah[r][s2]), l = upk2(Al[r][s2]);
+                acc[r][s2] = df_to_double(h.x, l.x) + df_to_double(h.y, l.y);   // even + odd rows
             }
+        // groups > 0 hand their sums to group 0 through shared memory
+        double* sacc = reinterpret_cast<double*>(smem_raw);
+        if (P > 1) {
+            __syncthreads();
+            if (active && grp > 0) {
+                double* d = sacc + ((size_t)(grp - 1) * ntiles + (tid - grp * ntiles)) * 4;
+                d[0] = acc[0][0];
+                d[1] = acc[0][1];
+                d[2] = acc[1][0];
+                d[3] = acc[1][1];
+            }
+            __syncthreads();
+            if (active && grp == 0) {
+                for (int gg = 1; gg < P; ++gg) {
+                    const double* d = sacc + ((size_t)(gg - 1) * ntiles + tid) * 4;
+                    acc[0][0] += d[0];
+                    acc[0][1] += d[1];
+                    acc[1][0] += d[2];
+                    acc[1][1] += d[3];
+                }
+            }
+        }
+        if (active && grp == 0) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const int i = ti + r, j = tj + s2;
+                    if (i < KA && j < KB && (!a.sym || i <= j)) mypart[(size_t)i * a.maxKB + j] = acc[r][s2];
+                }
+        }
+        __syncthreads();   // the group sums are read: the buffers are free for the next pass
     }
     gram_finish(a, b, chunks, KA, KB, nout);
 }
@@ -394,7 +407,8 @@ __global__ void __launch_bounds__(GDF_MAXTHR, 2) gram_df_kernel(GramArgs a, long
 // 6.60 ms on the 64^3 workload); 0 when the df kernel does not apply.
 static int gram_df_threads(const GramArgs& a) {
     const int tiles = gdf_tiles(a.maxKA, a.maxKB, a.sym);
-    if (tiles <= 0 || tiles > GDF_MAXTHR) return 0;
+    if (tiles <= 0 || tiles > GDF_MAXTILES) return 0;
+    if (tiles > GDF_MAXTHR) return GDF_MAXTHR;   // wider items take several passes
     const int P = (tiles > 128 && 2 * tiles <= GDF_MAXTHR) ? 2 : std::max(1, 256 / tiles);
     return (tiles * P + 31) / 32 * 32;
 }

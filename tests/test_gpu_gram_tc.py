@@ -219,10 +219,12 @@ def test_narrow_tensor_gram_within_the_fp64_bound(gpu, n, K, B):
     assert worst < 1.0, worst
 
 
-@pytest.mark.parametrize("K", [4, 24, 32])
+@pytest.mark.parametrize("K", [4, 24, 32, 60, 96])
 def test_double_float_gram_agrees(gpu, K):
     """pr_op_gram's double-float kernel (tensor = 2, the FP32 mode's default) against the
-    tensor-core and FP64 kernels on the same columns: all three FP64-accurate."""
+    tensor-core (up to 64 columns) and FP64 kernels on the same columns: all FP64-accurate.
+    60 and 96 columns (465 and 1176 output tiles) exceed the kernel's 384 threads and take
+    two and four passes over each chunk."""
     bd, torch = gpu
     n, B = 16, 3
     w = pi.Workload("gram", n, pi.Flow("abc"), 0.05, 1.0, 4, 1e-3, n_snap=64, m_cap=32)
@@ -230,13 +232,15 @@ def test_double_float_gram_agrees(gpu, K):
     W = _columns(n, K, B, seed=K + 5)
     Wt = torch.from_numpy(W).to("cuda")
     Gd = s.op_gram(Wt, tensor=False, df=True).cpu().numpy()
-    Gt = s.op_gram(Wt, tensor=True).cpu().numpy()
+    Gt = s.op_gram(Wt, tensor=True).cpu().numpy() if K <= 64 else None
     G64 = s.op_gram(Wt, tensor=False).cpu().numpy()
     s.close()
     for b in range(B):
         sc = np.abs(G64[b]).max()
         assert np.abs(Gd[b] - G64[b]).max() < 1e-14 * sc
-        assert np.abs(Gt[b] - G64[b]).max() < 1e-14 * sc
+        assert np.array_equal(Gd[b], Gd[b].T)
+        if Gt is not None:
+            assert np.abs(Gt[b] - G64[b]).max() < 1e-14 * sc
 
 
 @pytest.mark.parametrize("K", [16, 40])
