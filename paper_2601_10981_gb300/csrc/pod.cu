@@ -680,6 +680,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
     int* pq = perm + Kp;                         // [Kp/2][2]: the round's pairs
     __shared__ double red[32];
     __shared__ int s_stop;
+    __shared__ double s_prev;   // ||off||_F^2 before the previous sweep
     const double* Gb = a.G + (size_t)b * a.ldG_b;
     for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) {
         const int i = e / Kp, j = e - i * Kp;
@@ -721,9 +722,14 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_pod_kernel(EigArgs a) {
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) st += red[w];
             // converged when the off-diagonal part is at the rounding level of the Gram
             // matrix itself, ||off||_F <= K eps ||A||_F: a tighter bound sits below the
-            // noise of the rotations (fused multiply-adds) and would never be met
+            // noise of the rotations (fused multiply-adds) and would never be met.  The
+            // rotations' own noise can also sit just above that bound, so a sweep that no
+            // longer cuts ||off|| four-fold within 16 times of it ends the iteration too
+            // (past the quadratic phase further sweeps only reshuffle rounding noise)
             const double tolK = (double)K * 2.220446049250313e-16;
-            s_stop = (offsum <= tolK * tolK * st) || st == 0.0;
+            const bool stalled = sweep > 0 && offsum <= 256.0 * tolK * tolK * st && offsum * 16.0 >= s_prev;
+            s_stop = (offsum <= tolK * tolK * st) || st == 0.0 || stalled;
+            s_prev = offsum;
         }
         __syncthreads();
         if (s_stop) break;
