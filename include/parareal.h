@@ -146,7 +146,7 @@ enum pr_method { PR_METHOD_ADAPTIVE = 0, PR_METHOD_PARAREAL_I = 1, PR_METHOD_PAR
  * FP32 pipe (up to 126 columns, windows wider than 54 columns in several passes over the
  * data; FP64 beyond).  PR_GRAM_TENSOR: the tensor cores, with the values cut into
  * error-free BF16 digits (FP64-accurate, see pr_op_gram; up to 64 columns, double-float
- * beyond).  PR_GRAM_AUTO: the tensor cores for snapshot windows of 24..32 columns (where
+ * beyond).  PR_GRAM_AUTO: the tensor cores for snapshot windows of 20..32 columns (where
  * the narrow tensor-core form is faster) and 55..64 columns (where the double-float
  * kernel would need two passes), double-float otherwise (and for the Cholesky-QR Grams,
  * whose column counts are POD dimensions known only on the device).  The FP64 mode always

@@ -406,10 +406,11 @@ cudaError_t gram_auto(pr_ctx* c, const GramArgs& ga, bool in_f32, bool k_exact) 
     const int mode = c->o.gram_mode;
     const bool fits = c->fp32 && !in_f32 && ga.sym && ga.colblk == nullptr && ga.maxKA <= gram_tc_max_cols() &&
                       ga.B <= (c->wave > 0 ? c->wave : c->N) + 1;
-    // measured crossovers against the double-float kernel (64 items x 262,144 points): the
-    // narrow tensor form (<= 32 columns) wins from 24 columns (32: 3.8 vs 6.7 ms), the wide
-    // one (33..64) beyond the double-float kernel's 384 output tiles a pass (55 columns)
-    const bool narrow = ga.maxKA >= 24 && ga.maxKA <= 32;
+    // measured crossovers against the double-float kernel (64 items x 262,144 points, wall
+    // time incl. the column-maximum pass): the narrow tensor form (<= 32 columns) wins from
+    // 20 columns (20: 2.7 vs 3.0 ms, 32: 3.3 vs 6.9 ms; 16: 2.1 vs 1.9), the wide one
+    // (33..64) beyond the double-float kernel's 384 output tiles a pass (55 columns)
+    const bool narrow = ga.maxKA >= 20 && ga.maxKA <= 32;
     const bool wide = ga.maxKA > 54;
     if (fits && (mode == PR_GRAM_TENSOR || (mode == PR_GRAM_AUTO && k_exact && (narrow || wide))))
         return launch_gram_tc(ga, c->colmax, gram_tc_max_cols(), c->derr, c->o.spin_limit, c->st);

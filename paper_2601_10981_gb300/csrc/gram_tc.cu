@@ -164,8 +164,15 @@ __device__ __forceinline__ unsigned pack_bf16x2(int a, int b) {
 
 // colmax[b * ld + i] = bit pattern of max_p |W_b[p, i]| (non-negative doubles order like
 // their bit patterns), by atomicMax from each CTA's chunk; the buffer starts at zero.
-// Four columns at a time (four independent loads in flight per thread), per-warp maxima
-// in shared memory, one barrier and one atomic per column and CTA.
+// Eight columns at a time, two points a load where the columns are 16-byte aligned (eight
+// independent 16-byte loads in flight per thread), per-warp maxima in shared memory, one
+// barrier and one atomic per column and CTA.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsigned long long y) {
+    return x > y ? x : y;
+}
 __global__ void __launch_bounds__(256) colmax_kernel(GramArgs a, long long CH, unsigned long long* colmax,
                                                      int ld) {
     const int b = blockIdx.y;
@@ -174,38 +181,42 @@ __global__ void __launch_bounds__(256) colmax_kernel(GramArgs a, long long CH, u
     const void* const* cols = a.colsA + (size_t)b * a.ldcols;
     __shared__ unsigned long long red[8][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i0 = 0; i0 < K; i0 += 4) {
-        const double* c[4];
-        unsigned long long m[4];
+    for (int i0 = 0; i0 < K; i0 += 8) {
+        const double* c[8];
+        unsigned long long m[8];
+        bool al = (p_lo & 1) == 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            c[j] = (i0 + j < K) ? reinterpret_cast<const double*>(cols[i0 + j]) : nullptr;
+        for (int j = 0; j < 8; ++j) {   // columns past K read column i0 again (never stored)
+            c[j] = reinterpret_cast<const double*>(cols[i0 + j < K ? i0 + j : i0]);
             m[j] = 0ull;
+            al = al && ((reinterpret_cast<uintptr_t>(c[j]) & 15u) == 0);
         }
-        for (long long p = p_lo + threadIdx.x; p < p_hi; p += blockDim.x) {
-            double v[4];
+        long long p = p_lo + (al ? 2 * (long long)threadIdx.x : (long long)threadIdx.x);
+        if (al) {
+            for (; p + 1 < p_hi; p += 2 * (long long)blockDim.x) {
+                double2 v[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = c[j] ? c[j][p] : 0.0;
+                for (int j = 0; j < 8; ++j) v[j] = *reinterpret_cast<const double2*>(c[j] + p);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const unsigned long long x = (unsigned long long)__double_as_longlong(fabs(v[j]));
-                m[j] = x > m[j] ? x : m[j];
+                for (int j = 0; j < 8; ++j) m[j] = umax64(m[j], umax64(abs_bits(v[j].x), abs_bits(v[j].y)));
             }
         }
+        // the remaining single points (an odd tail, or every point of unaligned columns)
+        for (; p < p_hi; p += (al ? 2 * (long long)blockDim.x : (long long)blockDim.x)) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 8; ++j) m[j] = umax64(m[j], abs_bits(c[j][p]));
+        }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, m[j], off);
-                m[j] = o > m[j] ? o : m[j];
-            }
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) m[j] = umax64(m[j], __shfl_xor_sync(0xffffffffu, m[j], off));
             if (lane == 0 && i0 + j < K) red[warp][i0 + j] = m[j];
         }
     }
     __syncthreads();
     if (threadIdx.x < K) {
         unsigned long long t = 0ull;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = red[w][threadIdx.x] > t ? red[w][threadIdx.x] : t;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = umax64(t, red[w][threadIdx.x]);
         if (t) atomicMax(colmax + (size_t)b * ld + threadIdx.x, t);
     }
 }
@@ -573,8 +584,14 @@ __device__ __forceinline__ void cut56(double x, int ce, unsigned& zl, unsigned& 
 // Bounded mbarrier wait that also gives up once another thread has recorded a failure.
 // try_wait suspends the thread (at most ~1 us a try, by its time hint) instead of
 // spinning, so waiting warps leave the issue slots to the others; `limit` tries (the
-// context's spin limit, 2^22 ~ a few seconds by default; 0: one try).
+// context's spin limit, 2^22 ~ a few seconds by default).  limit 0: one non-blocking
+// test, so that a wait not already complete gives up at once.
 __device__ __forceinline__ bool mbar_wait_f(unsigned mbar, unsigned parity, volatile int* fail, long long limit) {
+    if (limit == 0) {
+        if (mbar_wait(mbar, parity, 0)) return true;
+        *fail = 1;
+        return false;
+    }
     for (long long it = 0; it <= limit; ++it) {
         unsigned ok = 0;
         asm volatile(

@@ -176,6 +176,7 @@ def _hard_columns(n, K, B, seed):
 
 @pytest.mark.parametrize("n,K,B", [
     (8, 5, 1),      # 512 points: one unit of 8 stages
+    (9, 7, 2),      # 729 points (odd): odd columns only 8-byte aligned, a 25-point tail
     (10, 32, 2),    # 1,000 points: two units, the second ragged (488 = 7 x 64 + 40)
     (16, 17, 3),    # 4,096 points: eight units an item, 17 of 32 columns
     (72, 6, 1),     # 373,248 points: units of 5,832 points, two accumulation windows each
