@@ -102,7 +102,8 @@ typedef struct pr_opts {
                                0: every co-resident CTA slot over the subintervals        */
     int ctas_per_sm;        /* resident CTAs per SM for the fine sweep; 0: occupancy max  */
     long long spin_limit;   /* polls of an in-kernel barrier or mbarrier before
-                               PR_ERR_TIMEOUT (default 1<<22, a few seconds)              */
+                               PR_ERR_TIMEOUT (default 1<<22, a few seconds; 0: one
+                               non-blocking check, so a wait not already complete fails) */
     int method;             /* enum pr_method; default PR_METHOD_ADAPTIVE                 */
     int fine;               /* enum pr_fine; default PR_FINE_IMPLICIT_EULER               */
     int wave;               /* adaptive method only.  0 (default): pr_fine_sweep covers all
