@@ -311,6 +311,14 @@ long long pr_launch_count(void);
 pr_status pr_op_apply_L(pr_ctx* ctx, const double* d_in, double* d_out, int count,
                         int transpose);
 
+/* out = L_h u as the FP32 mode's Galerkin projection forms it (Algorithm 2, the reduced
+ * operator R^T L R): the stencil weights and values split into float pairs and summed with
+ * error-free products and TwoSums on the FP32 pipe, within ~1e-14 of the sum of the seven
+ * terms' magnitudes at each point (pr_op_apply_L computes the same operator in FP64).
+ * d_in, d_out: count x n^3 device doubles.  Steady flows only (PR_ERR_UNSUPPORTED for a
+ * time-dependent one).  Synchronises the context stream. */
+pr_status pr_op_apply_L_df(pr_ctx* ctx, const double* d_in, double* d_out, int count);
+
 /* Fine propagator on B independent states: d_out[b] = F(t0, t0 + steps*dt, d_in[b]) with
  * snapshots of the states at steps 0, dM, ... (n_snap of them; d_snap may be NULL when
  * n_snap = 0).  d_in, d_out: B x n^3 doubles.  d_snap: B x n_snap x n^3 doubles (snapshots

@@ -106,6 +106,7 @@ _SIGS = {
     "pr_get_snapshots": (C.c_int, [_P, C.c_int, _P]),
     "pr_get_basis": (C.c_int, [_P, C.c_int, C.c_int, _P, _I]),
     "pr_op_apply_L": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
+    "pr_op_apply_L_df": (C.c_int, [_P, _P, _P, C.c_int]),
     "pr_op_fine": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int]),
     "pr_op_pod": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _P, _I]),
     "pr_op_coarse_update": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, _P]),
@@ -380,11 +381,17 @@ class Parareal:
         return G.value, ms.value
 
     # ------------------------------------------------------------------ single ops
-    def op_apply_L(self, u, transpose: bool = False):
-        """u: torch float64 tensor (count, n, n, n) on the GPU."""
+    def op_apply_L(self, u, transpose: bool = False, df: bool = False):
+        """u: torch float64 tensor (count, n, n, n) on the GPU.  df: the double-float form
+        of the FP32 mode's Galerkin projection (pr_op_apply_L_df; L only, not L^T)."""
         out = self.torch.empty_like(u)
         count = u.shape[0] if u.dim() == 4 else 1
-        self._check(self._lib.pr_op_apply_L(self.ctx, _tptr(u), _tptr(out), count, int(transpose)))
+        if df:
+            if transpose:
+                raise ValueError("the double-float operator form has no transpose")
+            self._check(self._lib.pr_op_apply_L_df(self.ctx, _tptr(u), _tptr(out), count))
+        else:
+            self._check(self._lib.pr_op_apply_L(self.ctx, _tptr(u), _tptr(out), count, int(transpose)))
         return out
 
     def op_fine(self, u, steps: int, dM: int = 1, n_snap: int = 0, t0: float = 0.0):

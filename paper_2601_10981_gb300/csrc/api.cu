@@ -1783,6 +1783,27 @@ pr_status pr_op_apply_L(pr_ctx* c, const double* d_in, double* d_out, int count,
     return PR_OK;
 }
 
+pr_status pr_op_apply_L_df(pr_ctx* c, const double* d_in, double* d_out, int count) {
+    if (!c || !d_in || !d_out || count < 0) return PR_ERR_INVALID_ARG;
+    if (c->tdep) return fail(c, PR_ERR_UNSUPPORTED, "pr_op_apply_L_df: time-dependent flows need a time");
+    pr_status s = ensure_ws(c);
+    if (s != PR_OK) return s;
+    Grid g = grid_of(c);
+    for (int c0 = 0; c0 < count; c0 += c->N + 1) {
+        const int B = std::min(count - c0, c->N + 1);
+        std::vector<const void*> in(B), out(B);
+        for (int b = 0; b < B; ++b) {
+            in[b] = d_in + (size_t)(c0 + b) * c->Ng;
+            out[b] = d_out + (size_t)(c0 + b) * c->Ng;
+        }
+        PR_CUDA(cudaMemcpyAsync(c->colsA, in.data(), sizeof(void*) * B, cudaMemcpyHostToDevice, c->st));
+        PR_CUDA(cudaMemcpyAsync(c->colsB, out.data(), sizeof(void*) * B, cudaMemcpyHostToDevice, c->st));
+        PR_CUDA(launch_apply_L_df(g, c->colsA, (void* const*)c->colsB, c->ones, 1, 1, B, c->st));
+        PR_CUDA(cudaStreamSynchronize(c->st));
+    }
+    return PR_OK;
+}
+
 pr_status pr_op_fine(pr_ctx* c, const double* d_in, double* d_out, void* d_snap, int B, double t0,
                      int steps, int dM, int n_snap) {
     if (!c || !d_in || !d_out || B < 1 || B > c->N || steps < 1) return PR_ERR_INVALID_ARG;

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import pr_inputs as pi
-from oracle.discretisation import Operator
+from oracle.discretisation import AXES, Operator
 
 pytestmark = pytest.mark.gpu
 
@@ -95,6 +95,38 @@ def test_apply_L_matches_oracle(gpu, flow, n):
         for i in range(2):
             ref = op.LT(us[i], 0.0) if transpose else op.L(us[i], 0.0)
             assert rel(out[i], ref) < 1e-13
+
+
+@pytest.mark.parametrize("flow", [pi.Flow("abc", A=1.0, B=0.7, C=1.3), pi.Flow("kolmogorov", k=3)])
+@pytest.mark.parametrize("n", [8, 12, 16, 40])
+def test_apply_L_double_float_matches_oracle(gpu, flow, n):
+    """pr_op_apply_L_df, the operator form of the FP32 mode's Galerkin projection, against
+    the oracle's FP64 operator point by point: within 2^-42 of the sum of the seven
+    stencil terms' magnitudes at the point (each term's float-pair split and error-free
+    product keep ~2^-47 of it).  One thread a point in blocks of 256: 8^3 = two blocks of
+    four z-planes, 12^3 = 1,728 points (blocks straddle rows and planes, the last one
+    ragged), 16^3 = one z-plane a block, 40^3 = rows of 40 points.  The third field has a
+    large mean, so the Laplacian's terms cancel to ~1e-4 of their magnitudes."""
+    bd, torch = gpu
+    eps = 0.037
+    w = pi.Workload("op", n, flow, eps, 1.0, 2, 1e-3, n_snap=8, m_cap=8)
+    s = solver(bd, w, precision=bd.PR_FP32)
+    u0 = pi.initial_state(n, seed=3)
+    us = np.stack([u0, pi.initial_state(n, seed=7), 100.0 + u0])
+    out = s.op_apply_L(dev(torch, us), df=True).cpu().numpy()
+    s.close()
+    op = Operator(O.Grid(n), flow, eps)
+    h = O.Grid(n).h
+    vel = op.vel(0.0)
+    for i in range(len(us)):
+        u = us[i]
+        ref = op.L(u, 0.0)
+        mag = 6.0 * eps / h ** 2 * np.abs(u)
+        for axis, b in zip(AXES, vel):
+            mag = mag + np.abs(b / (2.0 * h) - eps / h ** 2) * np.abs(np.roll(u, -1, axis=axis))
+            mag = mag + np.abs(-b / (2.0 * h) - eps / h ** 2) * np.abs(np.roll(u, +1, axis=axis))
+        err = np.abs(out[i] - ref)
+        assert np.all(err <= 2.0 ** -42 * mag + 1e-300), (i, float((err / mag).max()))
 
 
 # ---------------------------------------------------------------------- fine propagator
